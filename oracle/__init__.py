@@ -1,0 +1,252 @@
+"""CPU oracle for the compressed and sieved BFS -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never loads it, and shares no code with it.
+
+Each function follows a passage of the paper:
+
+* :func:`csr` -- the adjacency the search runs on (Sec. VII-A), tuples
+  symmetrised with self-loops kept twice and duplicates kept.
+* :func:`bfs_levels` -- BFS hop distances (Sec. II), -1 when unreachable.
+* :func:`parents` -- the deterministic parent: the smallest neighbour on the
+  previous level (the paper's (select,max) semiring of Sec. III-A picks the
+  largest; ``use_max=True`` gives that reading).
+* :func:`directory` / :func:`cross_directory` -- directory vectors V_{i,j}
+  (Eq. 4) and the cross directory (Eq. 5).
+* :func:`wah_encode` / :func:`wah_decode` -- the WAH code of Sec. IV, Table 3.
+* :func:`dist_bfs` -- Algorithms 1, 2, 3 (BIT, WAH, DIR-WAH) on a simulated
+  p x p grid, with every exchanged buffer recorded.
+* :func:`level_exchange` -- the exchanged buffers for one given frontier.
+
+Every function is pinned by ``tests/test_oracle_*.py`` against worked examples
+printed in the paper, brute force and invariants; none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PLAIN, COMPRESS, COMPRESS_SIEVE = 0, 1, 2
+
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_ptr = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (plain C11, portable)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            sig = {
+                "oracle_csr_size": (_i64, [_i64, _int]),
+                "oracle_csr": (_int, [_i64, _i64, _ptr, _ptr, _int, _ptr, _ptr]),
+                "oracle_bfs_levels": (_i64, [_i64, _ptr, _ptr, ctypes.c_int32, _ptr]),
+                "oracle_parents": (None, [_i64, _ptr, _ptr, _ptr, ctypes.c_int32, _int, _ptr]),
+                "oracle_range_begin": (_i64, [_i64, _int, _int]),
+                "oracle_range_len": (_i64, [_i64, _int, _int]),
+                "oracle_directory": (None, [_i64, _int, _ptr, _ptr, _int, _int, _ptr]),
+                "oracle_cross_directory": (None, [_i64, _int, _ptr, _ptr, _ptr]),
+                "oracle_wah_encode": (_i64, [_ptr, _i64, _int, _int, _ptr]),
+                "oracle_wah_decode": (_int, [_ptr, _i64, _i64, _int, _int, _ptr]),
+                "oracle_dist_bfs": (_i64, [_i64, _int, _ptr, _ptr, ctypes.c_int32, _int, _int, _int,
+                                           _ptr, _ptr, _ptr, _i64, _ptr, _i64]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class CSR:
+    """Plain CSR by source vertex: ``row_ptr`` (int64, n+1) and ``col`` (int32)."""
+
+    def __init__(self, n: int, row_ptr: np.ndarray, col: np.ndarray):
+        self.n, self.row_ptr, self.col = n, row_ptr, col
+
+    def degree(self) -> np.ndarray:
+        return np.diff(self.row_ptr)
+
+
+def csr(n: int, src: np.ndarray, dst: np.ndarray, symmetrize: bool = True) -> CSR:
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    m = len(src)
+    lib = _load()
+    row_ptr = np.empty(n + 1, dtype=np.int64)
+    col = np.empty(max(1, lib.oracle_csr_size(m, int(symmetrize))), dtype=np.int32)
+    rc = lib.oracle_csr(n, m, _p(src), _p(dst), int(symmetrize), _p(row_ptr), _p(col))
+    if rc != 0:
+        raise ValueError("oracle_csr: vertex id out of range")
+    return CSR(n, row_ptr, col[: lib.oracle_csr_size(m, int(symmetrize))])
+
+
+def bfs_levels(g: CSR, root: int) -> np.ndarray:
+    level = np.empty(g.n, dtype=np.int32)
+    rc = _load().oracle_bfs_levels(g.n, _p(g.row_ptr), _p(g.col), root, _p(level))
+    if rc < 0:
+        raise ValueError("oracle_bfs_levels: bad root")
+    return level
+
+
+def parents(g: CSR, level: np.ndarray, root: int, use_max: bool = False) -> np.ndarray:
+    level = np.ascontiguousarray(level, dtype=np.int32)
+    parent = np.empty(g.n, dtype=np.int32)
+    _load().oracle_parents(g.n, _p(g.row_ptr), _p(g.col), _p(level), root, int(use_max), _p(parent))
+    return parent
+
+
+def bfs(g: CSR, root: int, use_max: bool = False):
+    """``(level, parent)`` by the plain definition."""
+    level = bfs_levels(g, root)
+    return level, parents(g, level, root, use_max)
+
+
+def range_begin(n: int, p: int, b: int) -> int:
+    return int(_load().oracle_range_begin(n, p, b))
+
+
+def range_len(n: int, p: int, b: int) -> int:
+    return int(_load().oracle_range_len(n, p, b))
+
+
+def directory(g: CSR, p: int, i: int, j: int) -> np.ndarray:
+    """V_{i,j} as 0/1 bytes of length range_len(j)."""
+    out = np.empty(max(1, range_len(g.n, p, j)), dtype=np.uint8)
+    _load().oracle_directory(g.n, p, _p(g.row_ptr), _p(g.col), i, j, _p(out))
+    return out[: range_len(g.n, p, j)]
+
+
+def cross_directory(g: CSR, p: int) -> np.ndarray:
+    """``D[i, u]`` = bit of u in V_{i, range(u)}; shape (p, n), 0/1 bytes."""
+    out = np.empty((p, g.n), dtype=np.uint8)
+    _load().oracle_cross_directory(g.n, p, _p(g.row_ptr), _p(g.col), _p(out))
+    return out
+
+
+def wah_encode(bits: np.ndarray, w: int = 32, fill_bit: bool = True) -> np.ndarray:
+    """WAH words (as uint64 values) of a 0/1 byte array."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    nbits = len(bits)
+    out = np.empty(nbits // (w - 1) + 2, dtype=np.uint64)
+    nw = _load().oracle_wah_encode(_p(bits) if nbits else 0, nbits, w, int(fill_bit), _p(out))
+    return out[:nw].copy()
+
+
+def wah_decode(words: np.ndarray, nbits: int, w: int = 32, fill_bit: bool = True):
+    """0/1 byte array, or ``None`` if the stream is malformed."""
+    words = np.ascontiguousarray(words, dtype=np.uint64)
+    bits = np.zeros(max(1, nbits), dtype=np.uint8)
+    rc = _load().oracle_wah_decode(_p(words) if len(words) else 0, len(words), nbits, w,
+                                   int(fill_bit), _p(bits))
+    return None if rc != 0 else bits[:nbits]
+
+
+def dist_bfs(g: CSR, p: int, root: int, mode: int = COMPRESS_SIEVE, w: int = 32,
+             use_max: bool = False, trace: bool = False, max_levels: int = 256,
+             trace_cap: int | None = None):
+    """Algorithm 1/2/3 on a simulated p x p grid.
+
+    Returns ``(level, parent, trace)``; ``trace`` is a list (one entry per
+    exchange, i.e. per BFS level that had a nonempty frontier) of lists of
+    word arrays, indexed by slot: ``i*p + j`` for DIR-WAH (stream from source
+    range j to block-row i), ``j`` for WAH.  ``None`` unless ``trace``.
+    """
+    lib = _load()
+    level = np.empty(g.n, dtype=np.int32)
+    parent = np.empty(g.n, dtype=np.int32)
+    slots = p * p if mode == COMPRESS_SIEVE else (p if mode == COMPRESS else 0)
+    if trace and slots:
+        if trace_cap is None:
+            trace_cap = max_levels * (slots * 2 + (g.n * (p if mode == COMPRESS_SIEVE else 1)) // (w - 1) + 8)
+        words = np.empty(trace_cap, dtype=np.uint64)
+        counts = np.zeros(max_levels * slots, dtype=np.int64)
+        wp, cp = _p(words), _p(counts)
+    else:
+        words = counts = None
+        wp = cp = 0
+        trace_cap = 0
+    rc = lib.oracle_dist_bfs(g.n, p, _p(g.row_ptr), _p(g.col), root, mode, w, int(use_max),
+                             _p(level), _p(parent), wp, trace_cap, cp, max_levels)
+    if rc < 0:
+        raise ValueError(f"oracle_dist_bfs failed ({rc})")
+    tr = None
+    if trace and slots:
+        tr, off = [], 0
+        for k in range(min(rc, max_levels)):
+            lv = []
+            for s in range(slots):
+                c = int(counts[k * slots + s])
+                lv.append(words[off: off + c].copy())
+                off += c
+            tr.append(lv)
+    return level, parent, tr
+
+
+def level_exchange(g: CSR, p: int, frontier: np.ndarray, mode: int = COMPRESS_SIEVE, w: int = 32,
+                   D: np.ndarray | None = None):
+    """The buffers exchanged for one frontier (0/1 bytes of length n).
+
+    DIR-WAH: slot ``i*p + j`` = WAH(f_j (.) V_{i,j});  WAH: slot ``j`` = WAH(f_j).
+    Returns ``(streams, sieved_counts)`` where ``sieved_counts[s]`` is the
+    number of set bits in the encoded slice.
+    """
+    n = g.n
+    frontier = np.ascontiguousarray(frontier, dtype=np.uint8)
+    if mode == COMPRESS_SIEVE and D is None:
+        D = cross_directory(g, p)
+    streams, counts = [], []
+    if mode == COMPRESS_SIEVE:
+        for i in range(p):
+            for j in range(p):
+                b, ln = range_begin(n, p, j), range_len(n, p, j)
+                sl = frontier[b: b + ln] & D[i, b: b + ln]
+                streams.append(wah_encode(sl, w))
+                counts.append(int(sl.sum()))
+    elif mode == COMPRESS:
+        for j in range(p):
+            b, ln = range_begin(n, p, j), range_len(n, p, j)
+            sl = frontier[b: b + ln]
+            streams.append(wah_encode(sl, w))
+            counts.append(int(sl.sum()))
+    return streams, counts
+
+
+def pack_bits(bits: np.ndarray) -> np.ndarray:
+    """0/1 bytes -> little-endian bit-packed uint32 words (bit q of word k = bits[32k+q])."""
+    bits = np.asarray(bits, dtype=np.uint8)
+    pad = (-len(bits)) % 32
+    b = np.concatenate([bits, np.zeros(pad, dtype=np.uint8)]) if pad else bits
+    return np.packbits(b, bitorder="little").view(np.uint32).copy() if len(b) else np.zeros(0, np.uint32)
+
+
+def unpack_bits(words: np.ndarray, nbits: int) -> np.ndarray:
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    return np.unpackbits(w.view(np.uint8), bitorder="little")[:nbits].copy()

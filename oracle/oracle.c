@@ -1,0 +1,370 @@
+/*
+ * oracle.c -- plain, slow, single-threaded CPU reference for the compressed
+ * and sieved level-synchronous BFS.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the bench's
+ * CPU-baseline leg may load this code.  It shares no code, header, table or
+ * helper with the CUDA library, and neither side includes the other.
+ *
+ * What each function follows:
+ *   oracle_csr            -- the adjacency the search runs on (Sec. VII-A): one
+ *                            directed entry per tuple and, when symmetrising,
+ *                            the reverse entry too (a self-loop gives two).
+ *   oracle_bfs_levels     -- BFS as defined in Sec. II: hop distance from the
+ *                            source; unreachable vertices get -1.
+ *   oracle_parents        -- deterministic parent: the smallest (or, for the
+ *                            paper's (select,max) semiring of Sec. III-A, the
+ *                            largest) neighbour on the previous level.
+ *   oracle_directory      -- directory vector V_{i,j} of Eq. 4: bit k set iff
+ *                            column k of block A_{i,j} holds a nonzero.
+ *   oracle_wah_encode/_decode -- word-aligned hybrid code of Sec. IV, Table 3:
+ *                            literal / fill / active words over (w-1)-bit groups.
+ *   oracle_dist_bfs       -- Algorithms 1, 2 and 3 (BIT, WAH, DIR-WAH) run on a
+ *                            simulated p x p grid, step by step in the paper's
+ *                            order, recording every exchanged buffer.
+ *
+ * Bitmaps are held one byte per bit (0 or 1) so every step reads as its
+ * definition.  Vertex ranges: range b of a p-way split of n vertices is
+ * [b*nb, min(n, (b+1)*nb)) with nb = ceil(n/p) (Eq. 1-2).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ CSR -- */
+
+/* Count the directed entries first: returns the number of entries the CSR
+ * will hold (m, or 2m when symmetrising). */
+int64_t oracle_csr_size(int64_t m, int symmetrize) { return symmetrize ? 2 * m : m; }
+
+/* Build CSR by source vertex.  Entries keep tuple order inside each row.
+ * row_ptr has n+1 entries; col has oracle_csr_size(m, symmetrize) entries.
+ * Returns 0, or -1 if a tuple names a vertex outside [0, n). */
+int oracle_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, int symmetrize,
+               int64_t *row_ptr, int32_t *col)
+{
+    for (int64_t e = 0; e < m; ++e)
+        if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return -1;
+    for (int64_t v = 0; v <= n; ++v) row_ptr[v] = 0;
+    for (int64_t e = 0; e < m; ++e) {
+        row_ptr[src[e] + 1] += 1;
+        if (symmetrize) row_ptr[dst[e] + 1] += 1;
+    }
+    for (int64_t v = 0; v < n; ++v) row_ptr[v + 1] += row_ptr[v];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!fill) return -2;
+    for (int64_t v = 0; v < n; ++v) fill[v] = row_ptr[v];
+    for (int64_t e = 0; e < m; ++e) {
+        col[fill[src[e]]++] = dst[e];
+        if (symmetrize) col[fill[dst[e]]++] = src[e];
+    }
+    free(fill);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ BFS -- */
+
+/* level[v] = hop distance from root following CSR entries u -> v, or -1.
+ * Returns the number of reached vertices, or -1 for a bad root. */
+int64_t oracle_bfs_levels(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t root,
+                          int32_t *level)
+{
+    if (root < 0 || root >= n) return -1;
+    for (int64_t v = 0; v < n; ++v) level[v] = -1;
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!queue) return -2;
+    int64_t head = 0, tail = 0;
+    level[root] = 0;
+    queue[tail++] = root;
+    while (head < tail) {
+        int32_t u = queue[head++];
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            int32_t v = col[e];
+            if (level[v] < 0) {
+                level[v] = level[u] + 1;
+                queue[tail++] = v;
+            }
+        }
+    }
+    free(queue);
+    return tail;
+}
+
+/* Parent of every reached v != root: the smallest (use_max = 0) or largest
+ * (use_max = 1) u with an entry u -> v and level[u] = level[v] - 1.
+ * parent[root] = root; unreached vertices get -1. */
+void oracle_parents(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *level,
+                    int32_t root, int use_max, int32_t *parent)
+{
+    for (int64_t v = 0; v < n; ++v) parent[v] = -1;
+    for (int64_t u = 0; u < n; ++u) {
+        if (level[u] < 0) continue;
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            int32_t v = col[e];
+            if (v == root || level[v] != level[u] + 1) continue;
+            if (parent[v] < 0 || (!use_max && u < parent[v]) || (use_max && u > parent[v]))
+                parent[v] = (int32_t)u;
+        }
+    }
+    if (root >= 0 && root < n) parent[root] = root;
+}
+
+/* ------------------------------------------------------------ partition -- */
+
+static int64_t range_size(int64_t n, int p) { return (n + p - 1) / p; }
+
+static int64_t range_begin(int64_t n, int p, int b)
+{
+    int64_t x = (int64_t)b * range_size(n, p);
+    return x < n ? x : n;
+}
+
+static int64_t range_end(int64_t n, int p, int b) { return range_begin(n, p, b + 1); }
+
+int64_t oracle_range_begin(int64_t n, int p, int b) { return range_begin(n, p, b); }
+int64_t oracle_range_len(int64_t n, int p, int b) { return range_end(n, p, b) - range_begin(n, p, b); }
+
+/* ------------------------------------------------------------ directory -- */
+
+/* Eq. 4: V_{i,j}[k] = 1 iff column k of A_{i,j} has a nonzero, i.e. the
+ * source u = begin(j) + k has at least one entry u -> v with v in range i.
+ * V receives range_len(j) bytes. */
+void oracle_directory(int64_t n, int p, const int64_t *row_ptr, const int32_t *col, int i, int j,
+                      uint8_t *V)
+{
+    const int64_t jb = range_begin(n, p, j), je = range_end(n, p, j);
+    const int64_t ib = range_begin(n, p, i), ie = range_end(n, p, i);
+    for (int64_t u = jb; u < je; ++u) {
+        uint8_t bit = 0;
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+            if (col[e] >= ib && col[e] < ie) { bit = 1; break; }
+        V[u - jb] = bit;
+    }
+}
+
+/* Cross directory (Eq. 5) of every processor at once: D[i*n + u] = V_{i,j}[u - begin(j)]
+ * for the source range j holding u.  Built in one pass over the entries (every
+ * entry u -> v marks column u of the block in block-row range(v)); the same
+ * definition as oracle_directory, reached a different way.  D has p*n bytes. */
+void oracle_cross_directory(int64_t n, int p, const int64_t *row_ptr, const int32_t *col, uint8_t *D)
+{
+    const int64_t nb = range_size(n, p);
+    memset(D, 0, (size_t)n * (size_t)p);
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+            D[(size_t)(col[e] / nb) * (size_t)n + (size_t)u] = 1;
+}
+
+/* ------------------------------------------------------------------ WAH -- */
+
+/*
+ * Word-aligned hybrid code with w-bit words (Sec. IV, Table 3).
+ *   The bitmap is cut into groups of g = w-1 bits; the first bit of a group
+ *   is the most significant of its g payload bits.
+ *   Literal word: top bit 0, the g payload bits.
+ *   Fill word:    top bit 1; with fill_bit, bit w-2 holds the fill value and
+ *                 bits 0..w-3 the run length in groups; without it (the
+ *                 paper's 4-bit example, whose fill words carry no value
+ *                 bit) only zero runs are fills and bits 0..w-2 hold the
+ *                 run length.
+ *                 An all-zero group (or, with fill_bit, an all-one group) is
+ *                 always written as a fill; adjacent equal fills merge up to
+ *                 the largest length the count field holds.
+ *   Active word:  present iff nbits mod g != 0; holds the r = nbits mod g
+ *                 trailing bits right-aligned, first bit highest.
+ * Returns the number of words written to out (at most nbits/g + 1).
+ */
+int64_t oracle_wah_encode(const uint8_t *bits, int64_t nbits, int w, int fill_bit, uint64_t *out)
+{
+    const int g = w - 1;
+    const uint64_t top = 1ULL << (w - 1);
+    const uint64_t ones = (g >= 64) ? ~0ULL : ((1ULL << g) - 1ULL);
+    const int count_bits = fill_bit ? w - 2 : w - 1;
+    const uint64_t max_count = (1ULL << count_bits) - 1ULL;
+    const int64_t full = nbits / g;
+    const int64_t r = nbits % g;
+    int64_t nw = 0;
+    int last_fill = -1;     /* fill value of out[nw-1] if it is a fill word, else -1 */
+    for (int64_t k = 0; k < full; ++k) {
+        uint64_t x = 0;
+        for (int b = 0; b < g; ++b) x = (x << 1) | (uint64_t)(bits[k * g + b] & 1);
+        int fill_value = -1;
+        if (x == 0) fill_value = 0;
+        else if (fill_bit && x == ones) fill_value = 1;
+        if (fill_value < 0) {
+            out[nw++] = x;
+            last_fill = -1;
+            continue;
+        }
+        if (last_fill == fill_value && (out[nw - 1] & max_count) < max_count) {
+            out[nw - 1] += 1;
+        } else {
+            uint64_t word = top | 1ULL;
+            if (fill_bit && fill_value) word |= 1ULL << (w - 2);
+            out[nw++] = word;
+            last_fill = fill_value;
+        }
+    }
+    if (r > 0) {
+        uint64_t x = 0;
+        for (int64_t b = 0; b < r; ++b) x = (x << 1) | (uint64_t)(bits[full * g + b] & 1);
+        out[nw++] = x;
+    }
+    return nw;
+}
+
+/* Inverse of oracle_wah_encode.  Accepts any well-formed stream (canonical
+ * or not).  Returns 0, or -1 if the stream is malformed: a fill of length 0,
+ * a literal with the top bit set, groups beyond nbits, a missing or oversized
+ * active word, or trailing words. */
+int oracle_wah_decode(const uint64_t *words, int64_t nwords, int64_t nbits, int w, int fill_bit,
+                      uint8_t *bits)
+{
+    const int g = w - 1;
+    const uint64_t top = 1ULL << (w - 1);
+    const int count_bits = fill_bit ? w - 2 : w - 1;
+    const uint64_t count_mask = (1ULL << count_bits) - 1ULL;
+    const int64_t full = nbits / g;
+    const int64_t r = nbits % g;
+    int64_t pos = 0;     /* groups written */
+    int64_t k = 0;       /* words read */
+    while (pos < full) {
+        if (k >= nwords) return -1;
+        uint64_t word = words[k++];
+        if (w < 64 && (word >> w) != 0) return -1;
+        if (word & top) {
+            uint64_t len = word & count_mask;
+            int value = fill_bit ? (int)((word >> (w - 2)) & 1ULL) : 0;
+            if (len == 0 || (int64_t)len > full - pos) return -1;
+            for (uint64_t q = 0; q < len; ++q, ++pos)
+                for (int b = 0; b < g; ++b) bits[pos * g + b] = (uint8_t)value;
+        } else {
+            for (int b = 0; b < g; ++b) bits[pos * g + b] = (uint8_t)((word >> (g - 1 - b)) & 1ULL);
+            ++pos;
+        }
+    }
+    if (r > 0) {
+        if (k >= nwords) return -1;
+        uint64_t word = words[k++];
+        if ((word >> r) != 0) return -1;
+        for (int64_t b = 0; b < r; ++b) bits[full * g + b] = (uint8_t)((word >> (r - 1 - b)) & 1ULL);
+    }
+    return k == nwords ? 0 : -1;
+}
+
+/* ------------------------------------------- Algorithms 1-3 on a p x p grid -- */
+
+/*
+ * Distributed BFS on a simulated p x p grid, one processor P_i per vertex
+ * range i (paper indices shifted to start at 0).  mode 0 = BIT (Alg. 1),
+ * 1 = WAH (Alg. 2), 2 = DIR-WAH (Alg. 3).  Each level:
+ *   t_i = sum_j A_{i,j} (x) f_{i,j}   over the (select, min|max) semiring, so
+ *         t_i[v] carries the chosen parent of v;
+ *   t_i = t_i (.) not(pi_i);  pi_i = pi_i + t_i;  f_i = t_i;
+ * then the exchange of the new f:
+ *   BIT:     f = Allgatherv(f_i)                       (raw bitmaps)
+ *   WAH:     f' = Allgatherv(Compress(f_i)); f = Uncompress(f')
+ *   DIR-WAH: f_{i,j} = f_i (.) V_{j,i}; f'_{i,j} = Compress(f_{i,j});
+ *            g'_i = Alltoallv(f'_i); f_{i,j} = Uncompress(g'_{i,j})
+ * The exchange before level 0 carries f = {root}.
+ *
+ * Trace (optional, trace_counts != NULL): the exchanged buffers of the
+ * exchange that feeds level k are recorded as
+ *   WAH:     one stream per source range j, slot s = j        (p slots)
+ *   DIR-WAH: stream "from range j to block-row i", slot s = i*p + j  (p*p slots)
+ * trace_counts[k * slots + s] = word count; the words are appended to
+ * trace_words in (k, s) order (trace_cap words available).
+ *
+ * Outputs level[] and parent[] (length n).  Returns the number of levels
+ * traced (the number of exchanges), -1 on a bad argument, -2 if the trace
+ * does not fit, -3 on a decode failure (cannot happen for encoder output).
+ */
+int64_t oracle_dist_bfs(int64_t n, int p, const int64_t *row_ptr, const int32_t *col, int32_t root,
+                        int mode, int w, int use_max, int32_t *level, int32_t *parent,
+                        uint64_t *trace_words, int64_t trace_cap, int64_t *trace_counts,
+                        int64_t max_levels)
+{
+    if (n <= 0 || p <= 0 || p > n || root < 0 || root >= n || mode < 0 || mode > 2) return -1;
+    const int64_t nb = range_size(n, p);
+    uint8_t *f = (uint8_t *)calloc((size_t)n, 1);        /* current frontier, all ranges */
+    uint8_t *pi = (uint8_t *)calloc((size_t)n, 1);       /* visited */
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);   /* semiring value, -1 = zero */
+    uint8_t *recv = (uint8_t *)calloc((size_t)n * (size_t)p, 1);   /* f_{i,j} as received by P_i */
+    uint8_t *slice = (uint8_t *)malloc((size_t)nb + 1);
+    uint8_t *dec = (uint8_t *)malloc((size_t)nb + 1);
+    uint64_t *words = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nb + 2));
+    uint8_t *D = (mode == 2) ? (uint8_t *)malloc((size_t)n * (size_t)p) : NULL;
+    if (!f || !pi || !t || !recv || !slice || !dec || !words || (mode == 2 && !D)) {
+        free(f); free(pi); free(t); free(recv); free(slice); free(dec); free(words); free(D);
+        return -1;
+    }
+    /* Alg. 3 line 2: initialise the cross directories (static for the graph) */
+    if (mode == 2) oracle_cross_directory(n, p, row_ptr, col, D);
+    /* recv[i*n + u] = bit u of the frontier as P_i holds it after the exchange */
+    for (int64_t v = 0; v < n; ++v) { level[v] = -1; parent[v] = -1; }
+    level[root] = 0; parent[root] = root;
+    f[root] = 1; pi[root] = 1;
+    const int64_t slots = (mode == 2) ? (int64_t)p * p : (mode == 1 ? p : 0);
+    int64_t k = 0, used = 0, rc = 0;
+    for (;;) {
+        /* ---- exchange of f (the frontier of level k) ---- */
+        int64_t fsize = 0;
+        for (int64_t v = 0; v < n; ++v) fsize += f[v];
+        if (fsize == 0) break;
+        for (int i = 0; i < p; ++i) {
+            for (int j = 0; j < p; ++j) {
+                const int64_t jb = range_begin(n, p, j), jl = range_end(n, p, j) - jb;
+                uint8_t *dst = recv + (size_t)i * (size_t)n + (size_t)jb;
+                if (mode == 0) {                                   /* BIT: raw bitmap */
+                    memcpy(dst, f + jb, (size_t)jl);
+                    continue;
+                }
+                if (mode == 1 && i > 0) {                          /* WAH: one stream per j, */
+                    memcpy(dst, recv + (size_t)jb, (size_t)jl);    /* everyone gets the same */
+                    continue;
+                }
+                if (mode == 2) {                                   /* sieve: f_j (.) V_{i,j} */
+                    const uint8_t *Vij = D + (size_t)i * (size_t)n + (size_t)jb;
+                    for (int64_t q = 0; q < jl; ++q) slice[q] = (uint8_t)(f[jb + q] & Vij[q]);
+                } else {
+                    for (int64_t q = 0; q < jl; ++q) slice[q] = f[jb + q];
+                }
+                int64_t nw = oracle_wah_encode(slice, jl, w, 1, words);
+                if (trace_counts && k < max_levels) {
+                    const int64_t s = (mode == 2) ? (int64_t)i * p + j : j;
+                    trace_counts[k * slots + s] = nw;
+                    if (used + nw > trace_cap) { rc = -2; goto done; }
+                    memcpy(trace_words + used, words, sizeof(uint64_t) * (size_t)nw);
+                    used += nw;
+                }
+                if (oracle_wah_decode(words, nw, jl, w, 1, dec) != 0) { rc = -3; goto done; }
+                memcpy(dst, dec, (size_t)jl);
+            }
+        }
+        /* ---- t_i = sum_j A_{i,j} (x) f_{i,j} over (select, min|max) ---- */
+        for (int64_t v = 0; v < n; ++v) t[v] = -1;
+        for (int i = 0; i < p; ++i) {
+            const int64_t ib = range_begin(n, p, i), ie = range_end(n, p, i);
+            const uint8_t *fi = recv + (size_t)i * (size_t)n;
+            for (int64_t u = 0; u < n; ++u) {
+                if (!fi[u]) continue;
+                for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                    int32_t v = col[e];
+                    if (v < ib || v >= ie) continue;
+                    if (t[v] < 0 || (!use_max && u < t[v]) || (use_max && u > t[v])) t[v] = (int32_t)u;
+                }
+            }
+        }
+        /* ---- t = t (.) not(pi); pi = pi + t; f = t ---- */
+        for (int64_t v = 0; v < n; ++v) {
+            if (pi[v]) t[v] = -1;
+            f[v] = (uint8_t)(t[v] >= 0);
+            if (f[v]) { pi[v] = 1; level[v] = (int32_t)(k + 1); parent[v] = t[v]; }
+        }
+        ++k;
+    }
+    rc = k;
+done:
+    free(f); free(pi); free(t); free(recv); free(slice); free(dec); free(words); free(D);
+    return rc;
+}
