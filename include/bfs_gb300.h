@@ -1,0 +1,231 @@
+/*
+ * bfs_gb300.h -- C ABI of the compressed and sieved level-synchronous BFS on
+ * one GB300 (sm_103a).
+ *
+ * The method (Lv, Tan, Chen, Sun, "Compression and Sieve: Reducing
+ * Communication in Parallel Breadth First Search on Distributed Memory
+ * Systems"): BFS as a boolean sparse matrix-vector product per level
+ * (Sec. III-A, Alg. 1); the adjacency matrix split into a p x p grid of blocks
+ * A_{i,j} (Eq. 1-3); the frontier exchanged between block-rows compressed
+ * with the word-aligned hybrid code (Sec. IV, Table 3, Alg. 2) after being
+ * sieved by the cross directory V_{i,j} (Eq. 4-5, Sec. V-B, Alg. 3).  On one
+ * GPU the p x p processor grid is a virtual grid of blocks in HBM and every
+ * exchanged message is a per-block buffer in HBM.
+ *
+ * Conventions for every entry point:
+ *   - Errors are returned as a bfs_status; nothing throws across the ABI and
+ *     outputs are unspecified when the status is not BFS_OK.  A one-line
+ *     description of the last error of the calling thread is available from
+ *     bfs_last_error().
+ *   - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).  Work
+ *     is ordered on that stream; entry points that must report a result to the
+ *     host (a status from the device, a size) synchronise that stream and say so.
+ *   - Device pointers are CUDA device allocations of the current device.  Where
+ *     an argument says "host or device", the library asks the CUDA runtime which
+ *     it is and copies host data itself.
+ *   - Vertex ids are int32 in [0, n), 1 <= n <= 2^31 - 1.
+ *   - Every wait inside the library is bounded; no call blocks forever.
+ *
+ * Citations name the paper's sections, equations, algorithms and tables.
+ */
+#ifndef BFS_GB300_H
+#define BFS_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BFS_API __attribute__((visibility("default")))
+#else
+#define BFS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bfs_graph *bfs_graph_t;
+
+typedef enum {
+    BFS_OK = 0,
+    BFS_ERR_INVALID_ARG = 1,    /* an argument is out of range or inconsistent */
+    BFS_ERR_OUT_OF_MEMORY = 2,  /* a device or host allocation failed */
+    BFS_ERR_CUDA = 3,           /* a CUDA runtime call failed (see bfs_last_error) */
+    BFS_ERR_TIMEOUT = 4,        /* a bounded wait ran out */
+    BFS_ERR_CORRUPT = 5,        /* a compressed stream is malformed */
+    BFS_ERR_BUSY = 6,           /* the object is in use by another call */
+    BFS_ERR_NOT_FOUND = 7       /* an id or ticket is unknown */
+} bfs_status;
+
+/* Frontier exchange of each level (the three algorithms of Table 5). */
+enum {
+    BFS_MODE_PLAIN = 0,          /* BIT, Alg. 1: raw bitmap frontier */
+    BFS_MODE_COMPRESS = 1,       /* WAH, Alg. 2: one WAH stream per source range */
+    BFS_MODE_COMPRESS_SIEVE = 2  /* DIR-WAH, Alg. 3: one WAH stream per (source range j,
+                                    block-row i) holding f_j sieved by V_{i,j} */
+};
+
+typedef struct {
+    int32_t grid_r;          /* virtual grid rows p (destination ranges); 1 <= p <= min(n, 1024) */
+    int32_t grid_c;          /* virtual grid columns; must equal grid_r (square grid, Eq. 1-2) */
+    int32_t mode;            /* BFS_MODE_* */
+    int32_t wah_word_bits;   /* 32 (31-bit groups, Table 3) or 64 (63-bit groups) */
+    int32_t autotune;        /* reserved, 0 */
+    int32_t debug_checks;    /* 1: kernels verify internal invariants and report
+                                BFS_ERR_CORRUPT instead of continuing */
+} bfs_options;
+
+/* Fill `opt` with the defaults: 1 x 1 grid, BFS_MODE_COMPRESS_SIEVE, 32-bit words. */
+BFS_API void bfs_options_default(bfs_options *opt);
+
+/* Human-readable name of a status ("BFS_OK", ...). Never NULL. */
+BFS_API const char *bfs_status_string(bfs_status s);
+
+/* Copy the calling thread's last error message (NUL-terminated, truncated to
+ * `len` bytes) into `buf`.  Returns the status of that error. */
+BFS_API bfs_status bfs_last_error(char *buf, int64_t len);
+
+/*
+ * Build a graph from n_edges directed tuples (src[e], dst[e]) (Sec. VII-A:
+ * the tuples of the generated edge list, multi-edges and self-loops kept).
+ * With `symmetrize` != 0 every tuple also adds the reverse entry dst -> src
+ * (a self-loop therefore adds two entries), giving the undirected graph the
+ * paper searches.  src/dst may be host or device pointers; they are copied and
+ * the caller keeps ownership.  The build lays the entries out on the device as
+ * the p x p grid of blocks A_{i,j} (block-row i = destination range i, block
+ * column j = source range j; range b = [b*ceil(n/p), min(n, (b+1)*ceil(n/p)))),
+ * each block stored column-compressed over its nonempty source columns with
+ * the directory vector V_{i,j} of Eq. 4 as the column index.  The graph owns
+ * all of its device memory.  Synchronises `cuda_stream`.
+ * Errors: BFS_ERR_INVALID_ARG for n outside [1, 2^31-1], n_edges < 0, an id
+ * outside [0, n), a bad option; BFS_ERR_OUT_OF_MEMORY; BFS_ERR_CUDA.
+ */
+BFS_API bfs_status bfs_graph_create_edges(int64_t n_vertices, int64_t n_edges, const int32_t *src,
+                                  const int32_t *dst, int32_t symmetrize, const bfs_options *opt,
+                                  void *cuda_stream, bfs_graph_t *out);
+
+/*
+ * Build a graph from a CSR adjacency: row_ptr[n+1] (int64, row_ptr[0] = 0,
+ * nondecreasing) and col[row_ptr[n]] (int32), entry u -> col[e] for e in
+ * [row_ptr[u], row_ptr[u+1]).  No symmetrisation.  Host or device pointers,
+ * copied.  Same layout, ownership and errors as bfs_graph_create_edges.
+ */
+BFS_API bfs_status bfs_graph_create_csr(int64_t n_vertices, const int64_t *row_ptr, const int32_t *col,
+                                const bfs_options *opt, void *cuda_stream, bfs_graph_t *out);
+
+/* Free the graph and all of its device memory.  NULL is accepted. */
+BFS_API bfs_status bfs_graph_destroy(bfs_graph_t g);
+
+/* Device bytes held by the graph (layout plus per-search workspace). */
+BFS_API bfs_status bfs_graph_footprint(bfs_graph_t g, int64_t *bytes);
+
+typedef struct {
+    int64_t n_vertices;
+    int64_t n_entries;       /* directed adjacency entries */
+    int32_t p;               /* grid is p x p */
+    int32_t mode;
+    int32_t wah_word_bits;
+    int32_t reserved;
+    int64_t range_size;      /* ceil(n / p) */
+    int64_t nonempty_columns;/* sum over blocks of |V_{i,j}| (set directory bits) */
+} bfs_graph_info_t;
+
+BFS_API bfs_status bfs_graph_info(bfs_graph_t g, bfs_graph_info_t *info);
+
+/* Switch the exchange mode and WAH word width of later searches (the layout
+ * serves all three algorithms of Table 5).  Not safe while a search on `g`
+ * is running. */
+BFS_API bfs_status bfs_graph_set_mode(bfs_graph_t g, int32_t mode, int32_t wah_word_bits);
+
+/*
+ * Copy the directory vector V_{i,j} (Eq. 4: bit k set iff source column
+ * begin(j)+k of block A_{i,j} has an entry) into `out_words` (device,
+ * ceil(range_len(j)/32) uint32 words, bit k = bit k%32 of word k/32).
+ * Ordered on `cuda_stream`.
+ */
+BFS_API bfs_status bfs_graph_directory(bfs_graph_t g, int32_t i, int32_t j, uint32_t *out_words,
+                               void *cuda_stream);
+
+/* Per-level counters of one search (Table 6 phase labels for the timers). */
+typedef struct {
+    int64_t frontier_vertices;   /* |f_k| of the frontier exchanged for level k */
+    int64_t exchanged_vertices;  /* set bits carried by the exchange (after the sieve);
+                                    PLAIN/COMPRESS: p * |f_k| */
+    int64_t column_hits;         /* (vertex, block) pairs with a nonempty column, the
+                                    work items of the expansion */
+    int64_t raw_bytes;           /* bytes of the raw bitmap exchange: p slices of each range */
+    int64_t wah_bytes;           /* bytes of the compressed streams (0 in PLAIN mode) */
+    int64_t edges_scanned;       /* adjacency entries read by the expansion */
+    float ms_compress_sieve;     /* sieve + compress + decompress kernels */
+    float ms_communication;      /* exchange: size scan (and packing when traced) */
+    float ms_traversing;         /* expansion (the local SpMV) */
+    float ms_reducing;           /* mask, visited update, level writeback, frontier count */
+} bfs_level_stats;
+
+typedef struct {
+    int32_t capacity_levels;     /* entries of `levels` (and rows of trace_counts) */
+    int32_t n_levels;            /* out: exchanges performed (= BFS depth + 1 when reached set > 1) */
+    int32_t timing;              /* 1: fill the ms_* fields with CUDA-event times */
+    int32_t reserved;
+    bfs_level_stats *levels;     /* host array of capacity_levels entries, or NULL */
+    /* Optional exchange trace (device pointers, or NULL): for each exchange k,
+     * the streams of all slots packed back to back in slot order (slot = i*p + j
+     * in COMPRESS_SIEVE mode, j in COMPRESS mode) -- the receive buffer g' of
+     * Alg. 3 -- with each 32-bit WAH word as one uint32 and each 64-bit word as
+     * two uint32 (low half first). trace_counts[k*slots + s] = words in slot s. */
+    uint32_t *trace_words;
+    int64_t trace_capacity;      /* uint32 elements available in trace_words */
+    int64_t *trace_counts;       /* device, capacity_levels * slots entries */
+    int64_t trace_used;          /* out: uint32 elements written */
+} bfs_run_stats;
+
+/*
+ * One breadth-first search from `root` (Alg. 1, 2 or 3 per the graph's mode).
+ * Outputs, length n: level[v] = hop distance from root (root 0, unreached -1);
+ * parent[v] = the smallest neighbour u of v with level[u] = level[v] - 1
+ * (root: root; unreached: -1).  parent/level may both be device pointers (the
+ * search stays on the device and is ordered on `cuda_stream`; the call returns
+ * once the last level is known, so it synchronises the stream once per level)
+ * or both host pointers (results are copied back before returning).
+ * `stats` may be NULL.
+ * Errors: BFS_ERR_INVALID_ARG (root out of range, trace too small),
+ * BFS_ERR_BUSY (another search on this graph is running), BFS_ERR_CORRUPT
+ * (debug checks found a broken invariant), BFS_ERR_CUDA.
+ */
+BFS_API bfs_status bfs_run(bfs_graph_t g, int32_t root, int32_t *parent, int32_t *level,
+                   bfs_run_stats *stats, void *cuda_stream);
+
+/*
+ * WAH-encode one bitmap (Sec. IV, Table 3) on the device.
+ *   bits: device, bit b of the bitmap = bit b%32 of bits[b/32], nbits >= 0
+ *         bits; the array must hold ceil(nbits/32) + 2 words (the encoder
+ *         reads up to two words past the end and ignores them).
+ *   word_bits: 32 or 64.  Words are (word_bits-1)-bit groups, first bit of a
+ *         group most significant; literal top bit 0; fill top bit 1, next bit
+ *         the fill value, the rest the run length in groups; an all-0 or all-1
+ *         group is always a fill and equal fills merge; an active word holds the
+ *         nbits mod (word_bits-1) trailing bits right-aligned, first bit highest.
+ *   words: device output, capacity_words words of word_bits bits; at most
+ *         floor(nbits/(word_bits-1)) + 1 are written.
+ *   nwords: device int64, receives the word count.
+ * Uses scratch memory allocated on `cuda_stream` (stream-ordered allocator).
+ * Errors: BFS_ERR_INVALID_ARG (bad width, capacity below the bound above).
+ */
+BFS_API bfs_status bfs_wah_encode(const uint32_t *bits, int64_t nbits, int32_t word_bits, void *words,
+                          int64_t capacity_words, int64_t *nwords, void *cuda_stream);
+
+/*
+ * Decode a WAH stream (the inverse of bfs_wah_encode; accepts non-canonical
+ * but well-formed streams) into `bits` (device, ceil(nbits/32) words, bits past
+ * nbits in the last word are cleared).  Synchronises `cuda_stream` to report
+ * the result.  Errors: BFS_ERR_CORRUPT if the stream is malformed (a fill of
+ * length 0, groups past nbits, a missing or oversized active word, trailing
+ * words); `bits` is then unspecified.  BFS_ERR_INVALID_ARG for a bad width.
+ */
+BFS_API bfs_status bfs_wah_decode(const void *words, int64_t nwords, int64_t nbits, int32_t word_bits,
+                          uint32_t *bits, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFS_GB300_H */

@@ -1,0 +1,154 @@
+// internal.h -- host-side structures shared by the translation units of
+// libbfs_gb300 (graph layout, search workspace, error reporting, launchers).
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "bfs_gb300.h"
+
+namespace bfsgb {
+
+// ---------------------------------------------------------------- errors --
+bfs_status set_error(bfs_status s, const char* fmt, ...);
+bfs_status cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+#define BFS_CUDA_TRY(expr)                                                        \
+    do {                                                                          \
+        cudaError_t e__ = (expr);                                                 \
+        if (e__ != cudaSuccess) return ::bfsgb::cuda_error(e__, #expr, __FILE__, __LINE__); \
+    } while (0)
+
+#define BFS_TRY(expr)                                                             \
+    do {                                                                          \
+        bfs_status s__ = (expr);                                                  \
+        if (s__ != BFS_OK) return s__;                                            \
+    } while (0)
+
+// Kind of pointer the caller handed over.
+bool is_device_pointer(const void* p);
+
+// ---------------------------------------------------------- device arrays --
+// Owning device buffer (cudaMalloc / cudaFree).
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    bfs_status alloc(size_t nbytes);
+    void release();
+    template <typename T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// ------------------------------------------------------------ the layout --
+// Blocks b = i*p + j: block-row i = destinations in range i, block column j =
+// sources in range j.  Per block: directory V_{i,j} (range_len(j) bits, padded
+// to dir_stride uint32 words), rank[w] = set directory bits before word w,
+// cp = nnzc_b + 1 block-local offsets into the block's part of ir, ir = global
+// destination ids, block after block, column after column.
+struct Layout {
+    int64_t n = 0;          // vertices
+    int p = 1;              // grid p x p
+    int64_t nb = 0;         // range size ceil(n/p)
+    int64_t nnz = 0;        // directed entries
+    int64_t dir_stride = 0; // uint32 words per block directory (padded)
+    int64_t nnzc_total = 0; // nonempty columns over all blocks
+    DevBuf dir, rank, cp, ir, cp_base_d, ir_base_d;
+    std::vector<int64_t> cp_base, ir_base, nnzc, nnz_b;   // host copies, p*p
+    int64_t range_begin(int b) const { int64_t x = (int64_t)b * nb; return x < n ? x : n; }
+    int64_t range_len(int b) const { return range_begin(b + 1) - range_begin(b); }
+};
+
+// Work item of the expansion: source u with its column of one block.
+struct __align__(16) Item {
+    int32_t u;
+    uint32_t len;
+    int64_t begin;
+};
+
+// Device counters of one search (uint64 slots).
+enum Counter : int {
+    C_NEXT_COUNT = 0,    // vertices in the next frontier
+    C_UNITS,             // work units of the expansion (WAH chunks)
+    C_ITEMS,             // decoded (vertex, block) items
+    C_HITS,              // items with a nonempty column
+    C_EDGES,             // adjacency entries scanned
+    C_ERROR,             // nonzero: an invariant failed (code)
+    C_TRACE_USED,        // uint32 elements of the trace written so far
+    C_WAH_WORDS,         // words of all streams of this level
+    C_EXCHANGED,         // set bits carried by the exchange
+    C_NUM
+};
+
+// Per-search workspace (owned by the graph, reused by every search).
+struct Workspace {
+    int64_t bm_words = 0;       // uint32 words of an n-bit bitmap (padded)
+    int64_t fsum_len = 0;       // bytes of the frontier summary (1 per 1024 bits)
+    int64_t slot_cap = 0;       // words (of the WAH width) per exchange slot
+    int64_t chunk_words = 0;    // words per expansion chunk of a stream
+    int64_t chunks_per_slot = 0;
+    int slots = 0;              // exchange slots of the current mode
+    int wah_bits = 0;
+    int mode = -1;
+    DevBuf pi, fa, fb, fsum, xbuf, xcount, chunk_base, units, counters;
+    DevBuf tmp_parent, tmp_level;      // for searches with host outputs
+    uint64_t* h_counters = nullptr;    // pinned mirror of the counters
+    cudaEvent_t ev[8] = {};
+    bool events = false;
+};
+
+}  // namespace bfsgb
+
+struct bfs_graph {
+    bfsgb::Layout L;
+    bfsgb::Workspace W;
+    int mode = BFS_MODE_COMPRESS_SIEVE;
+    int wah_bits = 32;
+    int debug_checks = 0;
+    int device = 0;
+    std::atomic<int> busy{0};
+    std::mutex mu;
+};
+
+namespace bfsgb {
+
+// graph_build.cu
+bfs_status build_layout(bfs_graph* g, int64_t n, int64_t m, const int32_t* d_src,
+                        const int32_t* d_dst, int symmetrize, cudaStream_t st);
+bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st);
+void free_workspace(bfs_graph* g);
+
+// wah.cu
+struct EncodeArgs {
+    const uint32_t* frontier;   // bitmap read by the encoder
+    const uint32_t* dir;        // directories (sieve) or nullptr
+    int64_t dir_stride;
+    int p;
+    int64_t nb, n;
+    int sieve;                  // 1: slot s = i*p + j sieved by V_{i,j}; 0: slot = j
+    int nslots;
+    const uint8_t* fsum;        // frontier summary or nullptr
+    void* out;
+    int64_t slot_cap;
+    int64_t* counts;
+};
+bfs_status launch_wah_encode(const EncodeArgs& a, int wah_bits, cudaStream_t st);
+
+struct DecodeArgs {             // standalone decode into a bitmap
+    const void* words;
+    int64_t nwords;
+    int64_t nbits;
+    uint32_t* bits;
+    unsigned long long* err;
+};
+bfs_status launch_wah_decode_bitmap(const DecodeArgs& a, int wah_bits, cudaStream_t st);
+
+}  // namespace bfsgb

@@ -1,0 +1,351 @@
+// wah.cu -- WAH compress (Sec. IV, Table 3; Alg. 2 line 7, Alg. 3 line 10),
+// fused with the cross-directory sieve (Alg. 3 line 9), and the standalone
+// codec entry points of the C ABI.
+//
+// Encoder: one CTA per exchange slot walks the slot's groups in tiles of
+// kTile groups.  Inside a tile every thread classifies kK consecutive groups
+// (all-zero / all-one / literal); a block scan of "head" flags (a literal, or
+// a group whose type differs from its predecessor) gives every word its index,
+// and a block max-scan of head positions gives every group the start of its
+// run, so the group that ends a fill run writes the merged fill word.  The open
+// run, the word count and the previous type carry from tile to tile.  Tiles
+// whose frontier bits are all zero (frontier summary: one byte per 1024 bits)
+// are skipped without loading a word.
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+#include "wah.cuh"
+
+namespace bfsgb {
+namespace {
+
+constexpr int kNT = 256;          // threads per encoder CTA
+constexpr int kK = 4;             // groups per thread per tile
+constexpr int kTile = kNT * kK;   // groups per tile
+
+struct SlotGeom {
+    int64_t src0;      // first bitmap bit of the slot's source range
+    int64_t nbits;     // bits in the slot
+    const uint32_t* dirb;   // directory of the slot's block, or nullptr
+};
+
+__device__ __forceinline__ SlotGeom slot_geom(const EncodeArgs& a, int s) {
+    const int j = a.sieve ? (s % a.p) : s;
+    int64_t b0 = (int64_t)j * a.nb, b1 = b0 + a.nb;
+    if (b0 > a.n) b0 = a.n;
+    if (b1 > a.n) b1 = a.n;
+    SlotGeom g;
+    g.src0 = b0;
+    g.nbits = b1 - b0;
+    g.dirb = a.sieve ? a.dir + (int64_t)s * a.dir_stride : nullptr;
+    return g;
+}
+
+template <typename W>
+__device__ __forceinline__ W load_group(const EncodeArgs& a, const SlotGeom& sg, int64_t g) {
+    W x = Wah<W>::group(a.frontier, (uint64_t)(sg.src0 + g * Wah<W>::GB));
+    if (sg.dirb && x) x &= Wah<W>::group(sg.dirb, (uint64_t)(g * Wah<W>::GB));
+    return x;
+}
+
+template <typename W>
+__global__ void __launch_bounds__(kNT) wah_encode_kernel(EncodeArgs a, unsigned long long* setbits) {
+    using T = Wah<W>;
+    constexpr int GB = T::GB;
+    const int s = blockIdx.x;
+    const SlotGeom sg = slot_geom(a, s);
+    const int64_t G = sg.nbits / GB;
+    const int r = (int)(sg.nbits % GB);
+    W* out = static_cast<W*>(a.out) + (int64_t)s * a.slot_cap;
+
+    __shared__ int64_t sm64[kNT / 32 + 1];
+    __shared__ unsigned long long smu[kNT / 32 + 1];
+    __shared__ uint8_t sm_first[kNT], sm_last[kNT];
+    __shared__ int sm_flag;
+    __shared__ int sm_next_type;
+    __shared__ int sm_carry_type;
+    __shared__ int64_t sm_carry_start;
+
+    int64_t nw = 0;            // words assigned so far (the open run's word included)
+    int prev_type = -1;        // type of the group before the tile (-1: none)
+    int64_t run_start = 0;     // start group of the run holding the group before the tile
+    unsigned long long ones = 0;
+
+    for (int64_t tb = 0; tb < G; tb += kTile) {
+        const int64_t tend = (tb + kTile < G) ? tb + kTile : G;
+        // ---- zero skip from the frontier summary ----
+        if (a.fsum) {
+            if (threadIdx.x < 32) {
+                const int64_t lo = sg.src0 + tb * GB, hi = sg.src0 + tend * GB;   // [lo, hi)
+                const int64_t q0 = lo >> 10, q1 = (hi - 1) >> 10;
+                bool any = false;
+                for (int64_t q = q0 + lane_id(); q <= q1; q += 32) any |= (a.fsum[q] != 0);
+                any = __any_sync(0xffffffffu, any);
+                if (threadIdx.x == 0) sm_flag = any ? 1 : 0;
+            }
+            __syncthreads();
+            const int any = sm_flag;
+            __syncthreads();
+            if (!any) {
+                if (prev_type != G_ZERO) { nw += 1; run_start = tb; prev_type = G_ZERO; }
+                if (tend == G && threadIdx.x == 0) out[nw - 1] = fill_word<W>(G_ZERO, (uint64_t)(G - run_start));
+                continue;
+            }
+        }
+        // ---- classify this thread's groups ----
+        const int64_t g0 = tb + (int64_t)threadIdx.x * kK;
+        W x[kK];
+        int ty[kK];
+#pragma unroll
+        for (int k = 0; k < kK; ++k) {
+            const int64_t g = g0 + k;
+            if (g < tend) {
+                x[k] = load_group<W>(a, sg, g);
+                ty[k] = group_type<W>(x[k]);
+                ones += (unsigned long long)T::popc(x[k]);
+            } else {
+                x[k] = W(0);
+                ty[k] = G_NONE;
+            }
+        }
+        sm_first[threadIdx.x] = (uint8_t)ty[0];
+        sm_last[threadIdx.x] = (uint8_t)ty[kK - 1];
+        if (threadIdx.x == 0) sm_next_type = (tend < G) ? group_type<W>(load_group<W>(a, sg, tend)) : G_NONE;
+        __syncthreads();
+        const int prev0 = (threadIdx.x == 0) ? prev_type : (int)sm_last[threadIdx.x - 1];
+        // heads and last head position of this thread
+        bool h[kK];
+        int hc = 0;
+        int64_t lastpos = -1;
+        int pt = prev0;
+#pragma unroll
+        for (int k = 0; k < kK; ++k) {
+            h[k] = (ty[k] != G_NONE) && (ty[k] == G_LIT || ty[k] != pt);
+            if (h[k]) { ++hc; lastpos = g0 + k; }
+            pt = ty[k];
+        }
+        int64_t tot_h;
+        const int64_t excl_h = block_excl_scan<kNT>((int64_t)hc, (int64_t)0, OpSum(), sm64, &tot_h);
+        int64_t dummy;
+        const int64_t excl_pos = block_excl_scan<kNT>(lastpos, (int64_t)-1, OpMax(), sm64, &dummy);
+        // ---- write literals and the fill words of runs that end here ----
+        int64_t cur_start = excl_pos > run_start ? excl_pos : run_start;
+        int64_t widx = nw + excl_h - 1;
+#pragma unroll
+        for (int k = 0; k < kK; ++k) {
+            const int64_t g = g0 + k;
+            if (ty[k] == G_NONE) break;
+            if (h[k]) { cur_start = g; ++widx; }
+            int nt;
+            if (k + 1 < kK) nt = ty[k + 1];
+            else nt = (threadIdx.x + 1 < kNT) ? (int)sm_first[threadIdx.x + 1] : G_NONE;
+            if (g + 1 == tend) nt = sm_next_type;
+            if (ty[k] == G_LIT) {
+                out[widx] = T::to_payload(x[k]);
+            } else if (nt != ty[k]) {
+                out[widx] = fill_word<W>(ty[k], (uint64_t)(g - cur_start + 1));
+            }
+            if (g + 1 == tend) { sm_carry_type = ty[k]; sm_carry_start = cur_start; }
+        }
+        __syncthreads();
+        nw += tot_h;
+        prev_type = sm_carry_type;
+        run_start = sm_carry_start;
+        __syncthreads();
+    }
+    if (setbits) {
+        unsigned long long tot;
+        block_excl_scan<kNT>(ones, 0ull, OpSum(), smu, &tot);
+        if (threadIdx.x == 0 && tot) atomicAdd(setbits, tot);
+    }
+    if (threadIdx.x == 0) {
+        int64_t total = nw;
+        if (r > 0) {
+            const uint64_t pos = (uint64_t)(sg.src0 + G * GB);
+            W y = T::tail(a.frontier, pos, r);
+            if (sg.dirb && y) y &= T::tail(sg.dirb, (uint64_t)(G * GB), r);
+            if (setbits && y) atomicAdd(setbits, (unsigned long long)T::popc(y));
+            out[total++] = T::to_active(y, r);
+        }
+        a.counts[s] = total;
+    }
+}
+
+// ------------------------------------------------------- standalone decode --
+// One CTA walks the stream in tiles of kNT words (one per thread), scanning run
+// lengths to place each word, and ORs the decoded groups into the zeroed
+// output.  Malformed streams set *err.
+template <typename W>
+__global__ void __launch_bounds__(kNT) wah_decode_bitmap_kernel(DecodeArgs a) {
+    using T = Wah<W>;
+    constexpr int GB = T::GB;
+    const W* in = static_cast<const W*>(a.words);
+    const int64_t G = a.nbits / GB;
+    const int r = (int)(a.nbits % GB);
+    __shared__ unsigned long long smu[kNT / 32 + 1];
+    unsigned long long gpos = 0;     // groups consumed before the tile
+    for (int64_t wb = 0; wb < a.nwords; wb += kNT) {
+        const int64_t x = wb + threadIdx.x;
+        const bool valid = x < a.nwords;
+        const W y = valid ? in[x] : W(0);
+        const unsigned long long len = valid ? (unsigned long long)word_groups<W>(y) : 0ull;
+        unsigned long long tot;
+        const unsigned long long gs = gpos + block_excl_scan<kNT>(len, 0ull, OpSum(), smu, &tot);
+        if (valid) {
+            bool bad = false;
+            if (gs < (unsigned long long)G) {
+                if (is_fill<W>(y)) {
+                    if (len == 0 || gs + len > (unsigned long long)G) bad = true;
+                    else if (y & T::VAL) {
+                        // set bits [gs*GB, (gs+len)*GB)
+                        const uint64_t b0 = gs * GB, b1 = (gs + len) * GB;
+                        uint64_t b = b0;
+                        while (b < b1) {
+                            const uint64_t w = b >> 5;
+                            const uint32_t lo = (uint32_t)(b & 31);
+                            const uint64_t take = (b1 - b < 32 - lo) ? b1 - b : 32 - lo;
+                            const uint32_t mask = (take == 32) ? 0xffffffffu : (((1u << take) - 1u) << lo);
+                            if (mask == 0xffffffffu) a.bits[w] = mask;
+                            else atomicOr(a.bits + w, mask);
+                            b += take;
+                        }
+                    }
+                } else {
+                    const W v = T::from_payload(y);
+                    const uint64_t b0 = gs * GB;
+                    // OR the GB bits at b0 (may touch three 32-bit words)
+                    for (int q = 0; q < GB; q += 32) {
+                        const uint64_t bq = b0 + q;
+                        const int nbit = (GB - q < 32) ? GB - q : 32;
+                        uint32_t part = (uint32_t)(v >> q);
+                        if (nbit < 32) part &= (1u << nbit) - 1u;
+                        if (!part) continue;
+                        const uint64_t w = bq >> 5;
+                        const uint32_t sh = (uint32_t)(bq & 31);
+                        atomicOr(a.bits + w, part << sh);
+                        if (sh && (part >> (32 - sh))) atomicOr(a.bits + w + 1, part >> (32 - sh));
+                    }
+                }
+            } else if (gs == (unsigned long long)G && r > 0 && x == a.nwords - 1) {
+                if ((y >> r) != W(0)) bad = true;
+                else {
+                    const W v = T::from_active(y, r);
+                    const uint64_t b0 = gs * GB;
+                    for (int q = 0; q < r; q += 32) {
+                        const uint64_t bq = b0 + q;
+                        const int nbit = (r - q < 32) ? r - q : 32;
+                        uint32_t part = (uint32_t)(v >> q);
+                        if (nbit < 32) part &= (1u << nbit) - 1u;
+                        if (!part) continue;
+                        const uint64_t w = bq >> 5;
+                        const uint32_t sh = (uint32_t)(bq & 31);
+                        atomicOr(a.bits + w, part << sh);
+                        if (sh && (part >> (32 - sh))) atomicOr(a.bits + w + 1, part >> (32 - sh));
+                    }
+                }
+            } else {
+                bad = true;           // word past the groups, or misplaced active word
+            }
+            if (bad) atomicOr(a.err, 1ull);
+        }
+        gpos += tot;
+    }
+    if (threadIdx.x == 0 && gpos != (unsigned long long)G + (r > 0 ? 1ull : 0ull)) atomicOr(a.err, 1ull);
+}
+
+}  // namespace
+
+bfs_status launch_wah_encode(const EncodeArgs& a, int wah_bits, cudaStream_t st) {
+    if (a.nslots <= 0) return BFS_OK;
+    if (wah_bits == 32)
+        wah_encode_kernel<uint32_t><<<a.nslots, kNT, 0, st>>>(a, nullptr);
+    else
+        wah_encode_kernel<unsigned long long><<<a.nslots, kNT, 0, st>>>(a, nullptr);
+    BFS_CUDA_TRY(cudaGetLastError());
+    return BFS_OK;
+}
+
+bfs_status launch_wah_encode_counted(const EncodeArgs& a, int wah_bits, unsigned long long* setbits,
+                                     cudaStream_t st) {
+    if (a.nslots <= 0) return BFS_OK;
+    if (wah_bits == 32)
+        wah_encode_kernel<uint32_t><<<a.nslots, kNT, 0, st>>>(a, setbits);
+    else
+        wah_encode_kernel<unsigned long long><<<a.nslots, kNT, 0, st>>>(a, setbits);
+    BFS_CUDA_TRY(cudaGetLastError());
+    return BFS_OK;
+}
+
+bfs_status launch_wah_decode_bitmap(const DecodeArgs& a, int wah_bits, cudaStream_t st) {
+    if (wah_bits == 32)
+        wah_decode_bitmap_kernel<uint32_t><<<1, kNT, 0, st>>>(a);
+    else
+        wah_decode_bitmap_kernel<unsigned long long><<<1, kNT, 0, st>>>(a);
+    BFS_CUDA_TRY(cudaGetLastError());
+    return BFS_OK;
+}
+
+}  // namespace bfsgb
+
+using namespace bfsgb;
+
+extern "C" {
+
+bfs_status bfs_wah_encode(const uint32_t* bits, int64_t nbits, int32_t word_bits, void* words,
+                          int64_t capacity_words, int64_t* nwords, void* stream) {
+    if (word_bits != 32 && word_bits != 64) return set_error(BFS_ERR_INVALID_ARG, "word_bits must be 32 or 64");
+    if (nbits < 0 || !nwords || (nbits > 0 && (!bits || !words)))
+        return set_error(BFS_ERR_INVALID_ARG, "bad encode arguments");
+    const int64_t bound = nbits / (word_bits - 1) + 1;
+    if (capacity_words < bound)
+        return set_error(BFS_ERR_INVALID_ARG, "capacity %lld below the bound %lld", (long long)capacity_words, (long long)bound);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    EncodeArgs a;
+    memset(&a, 0, sizeof(a));
+    a.frontier = bits;
+    a.p = 1;
+    a.nb = nbits;
+    a.n = nbits;
+    a.sieve = 0;
+    a.nslots = 1;
+    a.out = words;
+    a.slot_cap = capacity_words;
+    a.counts = nwords;
+    if (nbits == 0) {
+        BFS_CUDA_TRY(cudaMemsetAsync(nwords, 0, sizeof(int64_t), st));
+        return BFS_OK;
+    }
+    return launch_wah_encode(a, word_bits, st);
+}
+
+bfs_status bfs_wah_decode(const void* words, int64_t nwords, int64_t nbits, int32_t word_bits, uint32_t* bits,
+                          void* stream) {
+    if (word_bits != 32 && word_bits != 64) return set_error(BFS_ERR_INVALID_ARG, "word_bits must be 32 or 64");
+    if (nbits < 0 || nwords < 0 || (nwords > 0 && !words) || (nbits > 0 && !bits))
+        return set_error(BFS_ERR_INVALID_ARG, "bad decode arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t out_words = (nbits + 31) / 32;
+    DevBuf err, pad;
+    BFS_TRY(err.alloc(sizeof(unsigned long long)));
+    BFS_CUDA_TRY(cudaMemsetAsync(err.ptr, 0, sizeof(unsigned long long), st));
+    // the kernel may OR into the word after the last one: decode into a padded copy
+    BFS_TRY(pad.alloc(sizeof(uint32_t) * (out_words + 2)));
+    BFS_CUDA_TRY(cudaMemsetAsync(pad.ptr, 0, pad.bytes, st));
+    DecodeArgs a;
+    a.words = words;
+    a.nwords = nwords;
+    a.nbits = nbits;
+    a.bits = pad.as<uint32_t>();
+    a.err = err.as<unsigned long long>();
+    BFS_TRY(launch_wah_decode_bitmap(a, word_bits, st));
+    unsigned long long h_err = 0;
+    BFS_CUDA_TRY(cudaMemcpyAsync(&h_err, err.ptr, sizeof(h_err), cudaMemcpyDeviceToHost, st));
+    if (out_words > 0)
+        BFS_CUDA_TRY(cudaMemcpyAsync(bits, pad.ptr, sizeof(uint32_t) * out_words, cudaMemcpyDeviceToDevice, st));
+    BFS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_err) return set_error(BFS_ERR_CORRUPT, "malformed WAH stream");
+    return BFS_OK;
+}
+
+}  // extern "C"

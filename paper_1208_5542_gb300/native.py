@@ -1,0 +1,102 @@
+"""ctypes binding of libbfs_gb300.so -- argument marshalling only.
+
+Every step of the search runs in the CUDA library; this module only loads it
+and declares the C signatures of ``include/bfs_gb300.h``.  Importing it fails
+loudly when the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libbfs_gb300.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "bfs_gb300.h")
+
+_lock = threading.Lock()
+_lib = None
+
+i32, i64, u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+vp = ctypes.c_void_p
+P = ctypes.POINTER
+
+STATUS = ["BFS_OK", "BFS_ERR_INVALID_ARG", "BFS_ERR_OUT_OF_MEMORY", "BFS_ERR_CUDA", "BFS_ERR_TIMEOUT",
+          "BFS_ERR_CORRUPT", "BFS_ERR_BUSY", "BFS_ERR_NOT_FOUND"]
+MODE_PLAIN, MODE_COMPRESS, MODE_COMPRESS_SIEVE = 0, 1, 2
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("grid_r", i32), ("grid_c", i32), ("mode", i32), ("wah_word_bits", i32),
+                ("autotune", i32), ("debug_checks", i32)]
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n_vertices", i64), ("n_entries", i64), ("p", i32), ("mode", i32), ("wah_word_bits", i32),
+                ("reserved", i32), ("range_size", i64), ("nonempty_columns", i64)]
+
+
+class LevelStats(ctypes.Structure):
+    _fields_ = [("frontier_vertices", i64), ("exchanged_vertices", i64), ("column_hits", i64),
+                ("raw_bytes", i64), ("wah_bytes", i64), ("edges_scanned", i64),
+                ("ms_compress_sieve", ctypes.c_float), ("ms_communication", ctypes.c_float),
+                ("ms_traversing", ctypes.c_float), ("ms_reducing", ctypes.c_float)]
+
+
+class RunStats(ctypes.Structure):
+    _fields_ = [("capacity_levels", i32), ("n_levels", i32), ("timing", i32), ("reserved", i32),
+                ("levels", P(LevelStats)), ("trace_words", vp), ("trace_capacity", i64),
+                ("trace_counts", vp), ("trace_used", i64)]
+
+
+_SIGS = {
+    "bfs_options_default": (None, [P(Options)]),
+    "bfs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "bfs_last_error": (ctypes.c_int, [ctypes.c_char_p, i64]),
+    "bfs_graph_create_edges": (ctypes.c_int, [i64, i64, vp, vp, i32, P(Options), vp, P(vp)]),
+    "bfs_graph_create_csr": (ctypes.c_int, [i64, vp, vp, P(Options), vp, P(vp)]),
+    "bfs_graph_destroy": (ctypes.c_int, [vp]),
+    "bfs_graph_footprint": (ctypes.c_int, [vp, P(i64)]),
+    "bfs_graph_info": (ctypes.c_int, [vp, P(GraphInfo)]),
+    "bfs_graph_set_mode": (ctypes.c_int, [vp, i32, i32]),
+    "bfs_graph_directory": (ctypes.c_int, [vp, i32, i32, vp, vp]),
+    "bfs_run": (ctypes.c_int, [vp, i32, vp, vp, P(RunStats), vp]),
+    "bfs_wah_encode": (ctypes.c_int, [vp, i64, i32, vp, i64, vp, vp]),
+    "bfs_wah_decode": (ctypes.c_int, [vp, i64, i64, i32, vp, vp]),
+}
+
+
+class BfsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS[status] if 0 <= status < len(STATUS) else status}: {msg}")
+        self.status = status
+
+
+def header_symbols() -> list[str]:
+    """Names of the entry points declared in include/bfs_gb300.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^BFS_API\s+[\w\s\*]*?\b(bfs_\w+)\s*\(", text, flags=re.M)))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with paper_1208_5542_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int):
+    if status != 0:
+        buf = ctypes.create_string_buffer(512)
+        lib().bfs_last_error(buf, 512)
+        raise BfsError(status, buf.value.decode(errors="replace"))

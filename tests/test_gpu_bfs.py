@@ -1,0 +1,207 @@
+"""Parity of the CUDA search with the CPU oracle (levels, parents and every exchanged buffer)."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen
+import oracle
+from tests.golden_io import bfs_example
+
+pytestmark = pytest.mark.gpu
+
+MODES = {"plain": 0, "compress": 1, "sieve": 2}
+ORACLE_MODE = {0: oracle.PLAIN, 1: oracle.COMPRESS, 2: oracle.COMPRESS_SIEVE}
+
+
+def _lib():
+    from paper_1208_5542_gb300 import bfs
+    from paper_1208_5542_gb300 import build
+    build.build()
+    return bfs
+
+
+def _run(g, root, **kw):
+    parent, level, st = g.run(root, **kw)
+    torch.cuda.synchronize()
+    return parent.cpu().numpy(), level.cpu().numpy(), st
+
+
+def _unpack_trace(st, wah_bits):
+    """GPU trace -> list (per exchange) of lists (per slot) of word values."""
+    words = st.trace_words[: st.trace_used].cpu().numpy().view(np.uint32)
+    counts = st.trace_counts.cpu().numpy()
+    per = wah_bits // 32
+    out, off = [], 0
+    for k in range(counts.shape[0]):
+        lv = []
+        for c in counts[k]:
+            c = int(c)
+            seg = words[off: off + c * per]
+            if per == 2:
+                seg = seg[0::2].astype(np.uint64) | (seg[1::2].astype(np.uint64) << np.uint64(32))
+            lv.append(seg.astype(np.uint64))
+            off += c * per
+        out.append(lv)
+    return out
+
+
+def _check_trace(gpu_tr, ora_tr):
+    assert len(gpu_tr) == len(ora_tr)
+    for k, (a, b) in enumerate(zip(gpu_tr, ora_tr)):
+        assert len(a) == len(b)
+        for s, (x, y) in enumerate(zip(a, b)):
+            assert len(x) == len(y) and (x == y).all(), f"exchange {k}, slot {s}: {x[:8]} vs {y[:8]}"
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("p", [1, 2, 4])
+@pytest.mark.parametrize("wah", [32, 64])
+def test_paper_example(mode, p, wah):
+    bfs = _lib()
+    d = bfs_example()
+    g = bfs.Graph.from_edges(d["n"], d["src"], d["dst"], p=p, mode=mode, wah_bits=wah)
+    parent, level, st = _run(g, d["root"], stats=True, trace_capacity=4096)
+    assert level.tolist() == d["levels"]
+    assert parent.tolist() == d["parents_min"]
+    if mode:
+        go = oracle.csr(d["n"], d["src"], d["dst"])
+        _, _, tr = oracle.dist_bfs(go, p, d["root"], mode=ORACLE_MODE[mode], w=wah, trace=True)
+        _check_trace(_unpack_trace(st, wah), tr)
+
+
+def test_directories_match_eq4():
+    bfs = _lib()
+    n, src, dst = graphgen.edges(11, 16)
+    go = oracle.csr(n, src, dst)
+    for p in (1, 3, 8):
+        g = bfs.Graph.from_edges(n, src, dst, p=p)
+        assert g.nonempty_columns == int(oracle.cross_directory(go, p).sum())
+        for i in range(p):
+            for j in range(p):
+                want = oracle.pack_bits(oracle.directory(go, p, i, j))
+                got = g.directory(i, j).cpu().numpy().view(np.uint32)
+                assert (got == want).all(), (p, i, j)
+
+
+def test_scale12_plain_2x2_sixteen_roots():
+    """The scale-12 Kronecker graph, 2x2 grid, no compression or sieve, 16 seeded roots."""
+    bfs = _lib()
+    n, src, dst = graphgen.edges(12, 16)
+    go = oracle.csr(n, src, dst)
+    g = bfs.Graph.from_edges(n, src, dst, p=2, mode=0)
+    roots = graphgen.pick_roots(n, src, dst, 16)
+    assert len(roots) == 16
+    for r in roots:
+        lv, pa = oracle.bfs(go, int(r))
+        parent, level, _ = _run(g, int(r))
+        assert (level == lv).all() and (parent == pa).all()
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("p,wah", [(2, 32), (4, 64), (8, 32), (5, 32)])
+def test_kronecker_traces_bit_exact(mode, p, wah):
+    bfs = _lib()
+    n, src, dst = graphgen.edges(14, 16)
+    go = oracle.csr(n, src, dst)
+    g = bfs.Graph.from_edges(n, src, dst, p=p, mode=mode, wah_bits=wah)
+    for r in graphgen.pick_roots(n, src, dst, 3):
+        lv, pa, tr = oracle.dist_bfs(go, p, int(r), mode=ORACLE_MODE[mode], w=wah, trace=True)
+        parent, level, st = _run(g, int(r), stats=True, trace_capacity=1 << 22)
+        assert (level == lv).all() and (parent == pa).all()
+        _check_trace(_unpack_trace(st, wah), tr)
+        # per-level statistics agree with the oracle's streams
+        for k, ls in enumerate(st.levels):
+            assert ls["frontier_vertices"] == int((lv == k).sum())
+            assert ls["wah_bytes"] == sum(len(x) for x in tr[k]) * wah // 8
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_ragged_ranges_directed_and_multi_tile(mode):
+    """n not a multiple of p (ragged last range, unaligned slices), no symmetrisation,
+    ranges long enough for several encoder tiles and expansion chunks."""
+    bfs = _lib()
+    n = 100_003
+    src, dst = graphgen.random_edges(n, 400_000, 11)
+    go = oracle.csr(n, src, dst, symmetrize=False)
+    for p in (3, 7):
+        g = bfs.Graph.from_edges(n, src, dst, symmetrize=False, p=p, mode=mode)
+        for r in (0, 77_777, n - 1):
+            lv, pa = oracle.bfs(go, r)
+            parent, level, _ = _run(g, r)
+            assert (level == lv).all() and (parent == pa).all()
+
+
+def test_dense_frontier_one_fills():
+    """Root 0 reaches 1..3999 (a contiguous dense frontier), each of which reaches
+    one vertex of 4000..7999: the level-1 streams hold all-one groups (1-fills)."""
+    bfs = _lib()
+    mid = np.arange(1, 4000)
+    src = np.concatenate([np.zeros(len(mid), np.int64), mid]).astype(np.int32)
+    dst = np.concatenate([mid, 4000 + (mid * 7) % 4000]).astype(np.int32)
+    n = 8000
+    go = oracle.csr(n, src, dst)
+    for mode in (1, 2):
+        for p in (1, 2):
+            g = bfs.Graph.from_edges(n, src, dst, p=p, mode=mode)
+            lv, pa, tr = oracle.dist_bfs(go, p, 0, mode=ORACLE_MODE[mode], trace=True)
+            parent, level, st = _run(g, 0, stats=True, trace_capacity=1 << 20)
+            assert (level == lv).all() and (parent == pa).all()
+            got = _unpack_trace(st, 32)
+            _check_trace(got, tr)
+            one_fills = sum(int(((w >> np.uint64(30)) == 3).sum()) for lvl in got for w in lvl if len(w))
+            assert one_fills > 0
+
+
+def test_isolated_root_single_vertex_and_empty_graph():
+    bfs = _lib()
+    g = bfs.Graph.from_edges(1, np.zeros(0, np.int32), np.zeros(0, np.int32), p=1)
+    parent, level, _ = _run(g, 0)
+    assert parent.tolist() == [0] and level.tolist() == [0]
+    src = np.array([0, 1, 5], np.int32)
+    dst = np.array([1, 2, 5], np.int32)
+    for mode in (0, 1, 2):
+        g = bfs.Graph.from_edges(6, src, dst, p=3, mode=mode)
+        parent, level, _ = _run(g, 5)
+        assert level.tolist() == [-1, -1, -1, -1, -1, 0]
+        assert parent.tolist() == [-1, -1, -1, -1, -1, 5]
+        parent, level, _ = _run(g, 3)
+        assert level.tolist() == [-1, -1, -1, 0, -1, -1]
+
+
+def test_from_csr_and_host_outputs():
+    bfs = _lib()
+    n, src, dst = graphgen.edges(12, 8)
+    go = oracle.csr(n, src, dst)
+    g = bfs.Graph.from_csr(n, go.row_ptr, go.col, p=4)
+    r = int(graphgen.pick_roots(n, src, dst, 1)[0])
+    lv, pa = oracle.bfs(go, r)
+    par = np.empty(n, np.int32)
+    lev = np.empty(n, np.int32)
+    g.run(r, parent=par, level=lev)
+    assert (lev == lv).all() and (par == pa).all()
+
+
+def test_bad_arguments_are_reported():
+    bfs = _lib()
+    from paper_1208_5542_gb300.native import BfsError
+    with pytest.raises(BfsError, match="INVALID_ARG"):
+        bfs.Graph.from_edges(10, np.array([0, 11], np.int32), np.array([1, 2], np.int32))
+    with pytest.raises(BfsError, match="INVALID_ARG"):
+        bfs.Graph.from_edges(10, np.array([0], np.int32), np.array([1], np.int32), p=11)
+    g = bfs.Graph.from_edges(10, np.array([0], np.int32), np.array([1], np.int32), p=2)
+    with pytest.raises(BfsError, match="INVALID_ARG"):
+        g.run(10)
+    with pytest.raises(BfsError, match="INVALID_ARG"):
+        g.set_mode(3)
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_scale20_grid8(mode):
+    bfs = _lib()
+    n, src, dst = graphgen.edges(20, 16)
+    go = oracle.csr(n, src, dst)
+    g = bfs.Graph.from_edges(n, src, dst, p=8, mode=mode)
+    for r in graphgen.pick_roots(n, src, dst, 2):
+        lv, pa = oracle.bfs(go, int(r))
+        parent, level, _ = _run(g, int(r))
+        assert (level == lv).all() and (parent == pa).all()
