@@ -1,0 +1,457 @@
+#!/usr/bin/env python3
+"""Harmonic-mean GTEPS of the compressed + sieved BFS on one GB300 (and N replicas).
+
+One step = one breadth-first search from each of the workload's roots (64 by
+default) on the resident graph, with the L2 flushed (a 256 MiB write) before
+every search.  TEPS_r = m_r / t_r, where m_r is the number of input tuples in
+the component reached from root r (self-loops and duplicates counted, Sec.
+VII-A) and t_r the CUDA-event time of search r; the reported value is the
+harmonic mean N_roots / sum_r (1 / TEPS_r).  The same graph is then searched
+with the raw-bitmap exchange (BIT, Alg. 1) for the comparison.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload s22|s26|s26er|s20|s12]
+  python bench.py --impl reference      # the CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank searches its own replica of the graph from
+its own seeded roots (weak scaling, no data-path collective); rank 0 prints the
+JSON line with the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (scale, edgefactor, grid p, kind, roots, description)
+    "s12": (12, 16, 2, 0, 16, "kronecker-s12-ef16-grid2x2"),
+    "s20": (20, 16, 8, 0, 64, "kronecker-s20-ef16-grid8x8"),
+    "s22": (22, 16, 8, 0, 64, "kronecker-s22-ef16-grid8x8"),
+    "s26": (26, 16, 16, 0, 64, "kronecker-s26-ef16-grid16x16"),
+    "s26er": (26, 16, 16, 1, 64, "erdos-renyi-s26-ef16-grid16x16"),
+}
+METRIC = "harmonic-mean GTEPS on 1 GB300 (compressed+sieved vs plain GPU BFS) at bit-exact levels"
+MODE_NAMES = {0: "plain", 1: "compress", 2: "compress_sieve"}
+KERNEL_SOURCES = ["paper_1208_5542_gb300/csrc/bfs_level.cu", "paper_1208_5542_gb300/csrc/wah.cuh",
+                  "paper_1208_5542_gb300/csrc/common.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="s22", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", type=int, default=2, help="0 plain, 1 compress, 2 compress+sieve")
+    ap.add_argument("--wah-bits", type=int, default=32)
+    ap.add_argument("--roots", type=int, default=0, help="override the number of roots")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile-run", action="store_true",
+                    help="build the graph and run one search per mode, untimed (for ncu)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers --
+def kernel_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(workload, mode_name):
+    """Per-launch DRAM bytes of the expansion kernel from the committed ncu summary,
+    or None if none was taken for this workload or the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+    except OSError:
+        return None
+    ent = data.get(f"{workload}:{mode_name}")
+    if not ent or ent.get("kernel_hash") != kernel_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def hm_gteps(m, t):
+    """Harmonic mean of m_r / t_r in GTEPS (t in seconds)."""
+    s = sum(tr / mr for mr, tr in zip(m, t) if mr > 0)
+    n = sum(1 for mr in m if mr > 0)
+    return (n / s) / 1e9 if s > 0 else 0.0
+
+
+# ---------------------------------------------------------- reference arm --
+def run_reference(args):
+    """The CPU oracle, as it stands, on the host cores (one core)."""
+    import numpy as np  # noqa: F401
+
+    import graphgen
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    scale, ef, p, kind, nroots, desc = WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    n, src, dst = graphgen.edges(scale, ef, kind=kind)
+    roots = graphgen.pick_roots(n, src, dst, nroots, seed=7)
+    deg = graphgen.degrees(n, src, dst)
+    g = oracle.csr(n, src, dst)
+    ms, ts = [], []
+    k = 0
+    total_steps = args.warmup + args.steps
+    step_times = []
+    for step in range(total_steps):
+        r = int(roots[k % len(roots)])
+        k += 1
+        t0 = time.perf_counter()
+        level, parent = oracle.bfs(g, r)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            ms.append(graphgen.traversed_tuples(deg, level))
+            ts.append(dt)
+            step_times.append(dt)
+    value = hm_gteps(ms, ts)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(step_times) / len(step_times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": desc, "scale": scale, "edgefactor": ef, "grid": f"{p}x{p}", "roots": nroots,
+                   "step": "one search (plain single-threaded CPU oracle: queue BFS + smallest-parent pass)"},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} roots of the {nroots}, one per step"},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- our arm --
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import graphgen
+    from paper_1208_5542_gb300 import build as libbuild
+    from paper_1208_5542_gb300 import bfs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        libbuild.build()
+    if world > 1:
+        dist.barrier()
+
+    scale, ef, p, kind, nroots, desc = WORKLOADS[args.workload]
+    if args.roots:
+        nroots = args.roots
+    t_setup = time.perf_counter()
+    n, src, dst = graphgen.edges(scale, ef, kind=kind)
+    roots = graphgen.pick_roots(n, src, dst, nroots, seed=7 + 1000 * rank)
+    g = bfs.Graph.from_edges(n, src, dst, p=p, mode=args.mode, wah_bits=args.wah_bits)
+    src_d = torch.from_numpy(src).to(dev)
+    dst_d = torch.from_numpy(dst).to(dev)
+    deg = (torch.bincount(src_d.long(), minlength=n) + torch.bincount(dst_d.long(), minlength=n))
+    setup_s = time.perf_counter() - t_setup
+    stream = torch.cuda.current_stream()
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    level = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    if args.profile_run:
+        for mode in (args.mode, 0):
+            g.set_mode(mode, args.wah_bits)
+            g.run(int(roots[0]), parent, level)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": True, "workload": desc}))
+        return
+
+    def step(record=False):
+        """One search per root; returns per-root device times (s), m_r, and stats."""
+        times, ms_, sts = [], [], []
+        for r in roots:
+            flush.fill_(1)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            _, _, st = g.run(int(r), parent, level, stats=record, timing=record, stream=stream)
+            ev1.record(stream)
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1) / 1e3)
+            ms_.append(int((deg * (level >= 0)).sum().item()) // 2)
+            sts.append(st)
+        return times, ms_, sts
+
+    def timed(mode):
+        g.set_mode(mode, args.wah_bits)
+        for _ in range(args.warmup):
+            step()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        per_root = [[] for _ in roots]
+        all_stats = []
+        wall0 = time.perf_counter()
+        m_r = None
+        for _ in range(args.steps):
+            t, m_r, sts = step(record=True)
+            for i, x in enumerate(t):
+                per_root[i].append(x)
+            all_stats.append(sts)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        wall = time.perf_counter() - wall0
+        t_mean = [sum(x) / len(x) for x in per_root]
+        return t_mean, m_r, all_stats, wall
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_cs, m_r, stats_cs, wall_cs = timed(args.mode)
+    clk = clocks.stop()
+
+    # whole-job value: roots of all ranks over the slowest rank's sum of t_r/m_r
+    inv = sum(t / m for t, m in zip(t_cs, m_r) if m > 0)
+    ms_step = 1e3 * sum(t_cs)
+    if world > 1:
+        x = torch.tensor([inv, ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        inv, ms_step = float(x[0]), float(x[1])
+    total_roots = len(roots) * world
+    value = (total_roots / inv) / 1e9 if inv > 0 else 0.0
+
+    # roofline of the expansion kernel (algorithmic bytes per launch / event time per launch)
+    ex_bytes = ex_ms = 0.0
+    launches = 0
+    levels_tot = 0
+    per_level = {}
+    for sts in stats_cs:
+        for st in sts:
+            levels_tot += st.n_levels
+            for k, ls in enumerate(st.levels):
+                wah_read = ls["wah_bytes"]
+                discovered = st.levels[k + 1]["frontier_vertices"] if k + 1 < len(st.levels) else 0
+                # entries read (4 B) + rank word and column-pointer pair per item (12 B)
+                # + streams decoded + one parent word per discovered vertex
+                ex_bytes += 4 * ls["edges_scanned"] + 12 * ls["column_hits"] + wah_read + 4 * discovered
+                ex_ms += ls["ms_traversing"]
+                launches += 1
+                agg = per_level.setdefault(k, {"frontier": 0, "exchanged": 0, "raw_bytes": 0, "wah_bytes": 0,
+                                                "hits": 0, "n": 0})
+                agg["frontier"] += ls["frontier_vertices"]
+                agg["exchanged"] += ls["exchanged_vertices"]
+                agg["raw_bytes"] += ls["raw_bytes"]
+                agg["wah_bytes"] += ls["wah_bytes"]
+                agg["hits"] += ls["column_hits"]
+                agg["n"] += 1
+    launches_per_bfs = {0: 3, 1: 5, 2: 5}[args.mode]
+    gpu_launches = sum(2 + launches_per_bfs * st.n_levels for sts in stats_cs for st in sts)
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = (ex_bytes / launches) / (ex_ms / launches / 1e3) / 1e9 if launches and ex_ms > 0 else 0.0
+    traffic = ncu_traffic(args.workload, MODE_NAMES[args.mode])
+    exch = []
+    for k in sorted(per_level):
+        a = per_level[k]
+        f = a["frontier"] / a["n"]
+        exch.append({"level": k, "frontier": round(f, 1),
+                     "wah_over_raw": round(a["wah_bytes"] / a["raw_bytes"], 6) if a["raw_bytes"] else None,
+                     "sieve_drop": round(1 - a["exchanged"] / (p * a["frontier"]), 4) if a["frontier"] else None})
+
+    # phase breakdown (Table 6 labels), summed over the timed searches
+    phases = {"compression_sieve": 0.0, "communication": 0.0, "traversing": 0.0, "reducing": 0.0}
+    for sts in stats_cs:
+        for st in sts:
+            for ls in st.levels:
+                phases["compression_sieve"] += ls["ms_compress_sieve"]
+                phases["communication"] += ls["ms_communication"]
+                phases["traversing"] += ls["ms_traversing"]
+                phases["reducing"] += ls["ms_reducing"]
+    nsearch = sum(len(s) for s in stats_cs)
+    phases = {k: round(v / nsearch, 4) for k, v in phases.items()}
+
+    # validation: BFS-tree invariants and the smallest-parent rule for every root
+    # (torch over the edge list), bit-exact oracle comparison on the CPU-baseline sample
+    g.set_mode(args.mode, args.wah_bits)
+    invariant_ok = 0
+    for r in roots:
+        g.run(int(r), parent, level, stream=stream)
+        lv = level.long()
+        pa = parent.long()
+        u, v = src_d.long(), dst_d.long()
+        r = int(r)
+        ok = bool(lv[r] == 0) and bool(pa[r] == r)
+        lu, lvv = lv[u], lv[v]
+        ok &= not bool(((lu >= 0) ^ (lvv >= 0)).any())
+        both = (lu >= 0) & (lvv >= 0)
+        ok &= not bool(((lu - lvv).abs()[both] > 1).any())
+        best = torch.full((n,), 2**62, dtype=torch.int64, device=dev)
+        m1 = (lvv == lu + 1) & (lu >= 0)
+        best.scatter_reduce_(0, v[m1], u[m1], reduce="amin")
+        m2 = (lu == lvv + 1) & (lvv >= 0)
+        best.scatter_reduce_(0, u[m2], v[m2], reduce="amin")
+        reached = (lv > 0)
+        ok &= bool((pa[reached] == best[reached]).all())
+        ok &= bool((pa[lv < 0] == -1).all())
+        invariant_ok += int(ok)
+
+    # PLAIN (BIT, Alg. 1) on the same graph
+    plain = None
+    if not args.no_plain and args.mode != 0:
+        t_pl, m_pl, stats_pl, _ = timed(0)
+        plain = {"value": hm_gteps(m_pl, t_pl), "ms_per_step": round(1e3 * sum(t_pl), 3)}
+        g.set_mode(args.mode, args.wah_bits)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.empty(n, dtype=torch.int32).pin_memory()
+        hl = torch.empty(n, dtype=torch.int32).pin_memory()
+        ts_e2e, m_e2e = [], []
+        for r in roots:
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.run(int(r), hp, hl, stream=stream)
+            ts_e2e.append(time.perf_counter() - t0)
+            m_e2e.append(int(deg[torch.from_numpy(hl.numpy() >= 0).to(dev)].sum().item()) // 2)
+        e2e = {"value": hm_gteps(m_e2e, ts_e2e), "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(roots),
+               "d2h_bytes_per_step": 8 * n * len(roots)}
+
+    # CPU oracle on the host cores, bounded sample (rank 0, N = 1 only)
+    cpu = None
+    oracle_exact = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        go = oracle.csr(n, src, dst)
+        m_c, t_c = [], []
+        oracle_exact = 0
+        t_start = time.perf_counter()
+        for r in roots:
+            t0 = time.perf_counter()
+            lv_o, pa_o = oracle.bfs(go, int(r))
+            t_c.append(time.perf_counter() - t0)
+            m_c.append(int(deg[torch.from_numpy(lv_o >= 0).to(dev)].sum().item()) // 2)
+            g.run(int(r), parent, level, stream=stream)
+            oracle_exact += int(bool((level.cpu().numpy() == lv_o).all() and (parent.cpu().numpy() == pa_o).all()))
+            if time.perf_counter() - t_start > args.cpu_seconds:
+                break
+        cpu = {"value": hm_gteps(m_c, t_c), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"{len(t_c)} of the {len(roots)} roots (single-threaded queue BFS + smallest-parent pass)"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": desc + f"-{MODE_NAMES[args.mode]}-{len(roots)}roots", "scale": scale,
+                   "edgefactor": ef, "vertices": n, "tuples": int(len(src)), "grid": f"{p}x{p}",
+                   "mode": MODE_NAMES[args.mode], "wah_word_bits": args.wah_bits, "roots": len(roots),
+                   "step": "one search per root", "l2": "flushed (256 MiB write) before every search",
+                   "parallelism": f"replicas x{world}"},
+        "plain_gpu": plain,
+        "roofline": {"kernel": ("expand_wah" if args.mode else "expand_plain") + " + expand_pieces", "bound": "hbm",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4) if peak else None,
+                     "peak_source": peak_src, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": round(ex_bytes / launches) if launches else 0,
+                     "avg_launch_ms": round(ex_ms / launches, 5) if launches else 0, "launches": launches},
+        "phases_ms_per_search": phases,
+        "exchange_per_level": exch,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": gpu_launches,
+        "validation": {"invariant_and_min_parent_roots": invariant_ok, "roots": len(roots),
+                       "oracle_bit_exact_roots": oracle_exact},
+        "setup_s": round(setup_s, 2), "timed_wall_s": round(wall_cs, 3),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -68,6 +68,8 @@ struct LevelArgs {
     int64_t* chunk_base;
     int64_t chunks_per_slot;
     Unit* units;
+    Item* pieces;
+    int64_t piece_cap;
     unsigned long long* ctr;
     int sieve;                // 1: DIR-WAH streams (no directory test at the receiver)
     int nstreams;
@@ -78,56 +80,95 @@ __device__ __forceinline__ int64_t range_begin(const LevelArgs& a, int64_t b) {
     return x < a.n ? x : a.n;
 }
 
-// Visit entry u -> v of the expansion.
+// Visit entry u -> v of the expansion: if v was not visited before this
+// level, lower parent[v] to u and set t[v].  Both updates are reductions whose
+// results are not used (fire-and-forget at L2); the only dependent load is the
+// visited word, read through the read-only path (pi does not change during the
+// expansion).
 __device__ __forceinline__ void visit(const LevelArgs& a, int32_t v, int32_t u) {
     const uint32_t w = (uint32_t)v >> 5;
     const uint32_t m = 1u << ((uint32_t)v & 31u);
-    if (__ldg(a.pi + w) & m) return;                        // visited before this level
-    unsigned int* pp = reinterpret_cast<unsigned int*>(a.parent) + v;
-    if ((unsigned int)u < __ldcg(pp)) atomicMin(pp, (unsigned int)u);   // -1 is the largest unsigned
-    if (!(__ldcg(a.t + w) & m)) atomicOr(a.t + w, m);
+    if (__ldg(a.pi + w) & m) return;
+    atomicMin(reinterpret_cast<unsigned int*>(a.parent) + v, (unsigned int)u);   // -1 is the largest unsigned
+    atomicOr(a.t + w, m);
 }
 
-// Shared state of one expansion round: up to kNT items, one per thread.
-struct RoundSmem {
-    int32_t u[kNT];
-    int64_t begin[kNT];
-    uint32_t incl[kNT];
-    unsigned long long red[kNT / 32 + 1];
+constexpr uint32_t kHub = 1024;     // columns longer than this are cut into pieces
+constexpr uint32_t kPiece = 1024;   // entries per piece
+
+// Expand one item per lane (u, offset of its column in ir, length; length 0 =
+// none).  Columns longer than kHub go to the piece list; the rest are expanded
+// by the warp with a load-balanced search over the lanes' entry counts, so
+// every lane reads one entry per step and a step covers 32 consecutive entries
+// of the concatenated columns.
+__device__ __forceinline__ void warp_expand(const LevelArgs& a, int32_t u, int64_t beg, uint32_t len,
+                                            unsigned long long& edges, unsigned long long& hits) {
+    const uint32_t lane = lane_id();
+    hits += (len > 0);
+    if (__any_sync(0xffffffffu, len > kHub)) {
+        if (len > kHub) {
+            const uint32_t np = (len + kPiece - 1) / kPiece;
+            const unsigned long long base = atomicAdd(a.ctr + C_PIECES, (unsigned long long)np);
+            if (base + np <= (unsigned long long)a.piece_cap) {
+                for (uint32_t k = 0; k < np; ++k) {
+                    Item it;
+                    it.u = u;
+                    it.len = (len - k * kPiece < kPiece) ? len - k * kPiece : kPiece;
+                    it.begin = beg + (int64_t)k * kPiece;
+                    a.pieces[base + k] = it;
+                }
+            } else {
+                atomicOr(a.ctr + C_ERROR, 8ull);        // piece list overflow (cannot happen by the bound)
+            }
+            len = 0;
+        }
+    }
+    const uint32_t incl = warp_incl_sum(len);
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t excl = incl - len;
+    edges += len;
+    for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        // owner: the first lane whose inclusive count exceeds e
+        int lo = 0, hi = 31;
+#pragma unroll
+        for (int step = 0; step < 5; ++step) {
+            const int mid = (lo + hi) >> 1;
+            const uint32_t im = __shfl_sync(0xffffffffu, incl, mid);
+            if (im > e) hi = mid; else lo = mid + 1;
+        }
+        const int o = lo;
+        const int64_t ob = __shfl_sync(0xffffffffu, beg, o);
+        const uint32_t oe = __shfl_sync(0xffffffffu, excl, o);
+        const int32_t ou = __shfl_sync(0xffffffffu, u, o);
+        if (e < total) {
+            const int32_t v = __ldg(a.ir + ob + (int64_t)(e - oe));
+            visit(a, v, ou);
+        }
+    }
+}
+
+// Column of source u_local in block b: (offset into ir, len); len 0 if empty.
+struct BlockView {
+    const uint32_t* dir;
+    const uint32_t* rank;
+    const uint32_t* cp;
+    int64_t ir0;
 };
 
-// Expand the round's items (thread t holds item (u, begin, len); len 0 = none)
-// with a block-level load-balanced search over their entries.
-__device__ __forceinline__ void expand_round(const LevelArgs& a, RoundSmem& S, int32_t u, int64_t begin,
-                                             uint32_t len) {
-    const int hits = __syncthreads_count(len > 0);
-    unsigned long long tot;
-    const unsigned long long excl = block_excl_scan<kNT>((unsigned long long)len, 0ull, OpSum(), S.red, &tot);
-    if (threadIdx.x == 0 && hits) atomicAdd(a.ctr + C_HITS, (unsigned long long)hits);
-    S.u[threadIdx.x] = u;
-    S.begin[threadIdx.x] = begin;
-    S.incl[threadIdx.x] = (uint32_t)(excl + len);
-    __syncthreads();
-    const uint64_t E = tot;
-    for (uint64_t e = threadIdx.x; e < E; e += kNT) {
-        // first k with incl[k] > e
-        int lo = 0, hi = kNT - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if ((uint64_t)S.incl[mid] > e) hi = mid; else lo = mid + 1;
-        }
-        const uint64_t start = lo ? S.incl[lo - 1] : 0u;
-        const int32_t v = __ldg(a.ir + S.begin[lo] + (int64_t)(e - start));
-        visit(a, v, S.u[lo]);
-    }
-    if (threadIdx.x == 0 && E) atomicAdd(a.ctr + C_EDGES, (unsigned long long)E);
-    __syncthreads();
+__device__ __forceinline__ BlockView block_view(const LevelArgs& a, int64_t b) {
+    BlockView bv;
+    bv.dir = a.dir + b * a.dir_stride;
+    bv.rank = a.rank + b * a.dir_stride;
+    bv.cp = a.cp + __ldg(a.cp_base + b);
+    bv.ir0 = __ldg(a.ir_base + b);
+    return bv;
 }
 
-// Column of source u_local in block b: (begin, len) into ir; len 0 if empty.
-__device__ __forceinline__ void column_of(const LevelArgs& a, int64_t b, int64_t ul, bool test_dir,
+__device__ __forceinline__ void column_of(const LevelArgs& a, const BlockView& bv, int64_t ul, bool test_dir,
                                           int64_t* begin, uint32_t* len) {
-    const uint32_t dw = __ldg(a.dir + b * a.dir_stride + (ul >> 5));
+    const uint32_t dw = __ldg(bv.dir + (ul >> 5));
+    const uint32_t rk = __ldg(bv.rank + (ul >> 5));
     const uint32_t bit = 1u << (ul & 31);
     if (!(dw & bit)) {                  // empty column: nothing to expand
         *begin = 0;
@@ -135,22 +176,54 @@ __device__ __forceinline__ void column_of(const LevelArgs& a, int64_t b, int64_t
         if (!test_dir) atomicOr(a.ctr + C_ERROR, 4ull);   // a sieved vertex must have a column
         return;
     }
-    const uint32_t c = __ldg(a.rank + b * a.dir_stride + (ul >> 5)) + __popc(dw & (bit - 1u));
-    const int64_t cb = __ldg(a.cp_base + b);
-    const uint32_t c0 = __ldg(a.cp + cb + c), c1 = __ldg(a.cp + cb + c + 1);
-    *begin = __ldg(a.ir_base + b) + c0;
+    const uint32_t c = rk + __popc(dw & (bit - 1u));
+    const uint32_t c0 = __ldg(bv.cp + c), c1 = __ldg(bv.cp + c + 1);
+    *begin = bv.ir0 + c0;
     *len = c1 - c0;
 }
 
+__device__ __forceinline__ void flush_counts(const LevelArgs& a, unsigned long long edges, unsigned long long hits) {
+    edges = warp_sum(edges);
+    hits = warp_sum(hits);
+    if (lane_id() == 0) {
+        if (edges) atomicAdd(a.ctr + C_EDGES, edges);
+        if (hits) atomicAdd(a.ctr + C_HITS, hits);
+    }
+}
+
+// Pieces of long columns: one warp per piece, 32 consecutive entries per step.
+__global__ void __launch_bounds__(kNT) expand_pieces(LevelArgs a) {
+    const int64_t np = (int64_t)*reinterpret_cast<volatile unsigned long long*>(a.ctr + C_PIECES);
+    const int64_t lim = np < a.piece_cap ? np : a.piece_cap;
+    const int64_t gw0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t gws = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t pc = gw0; pc < lim; pc += gws) {
+        const Item it = a.pieces[pc];
+        uint32_t e = lane_id();
+        for (; e + 96 < it.len; e += 128) {
+            const int32_t v0 = __ldg(a.ir + it.begin + e);
+            const int32_t v1 = __ldg(a.ir + it.begin + e + 32);
+            const int32_t v2 = __ldg(a.ir + it.begin + e + 64);
+            const int32_t v3 = __ldg(a.ir + it.begin + e + 96);
+            visit(a, v0, it.u);
+            visit(a, v1, it.u);
+            visit(a, v2, it.u);
+            visit(a, v3, it.u);
+        }
+        for (; e < it.len; e += 32) visit(a, __ldg(a.ir + it.begin + e), it.u);
+    }
+}
+
 // ------------------------------------------------------------------ PLAIN --
-// Unit = (block b, 256 raw frontier words of range j).  Thread t reads word t,
-// keeps the bits whose column is nonempty (word-wise AND with V_{i,j}) and
-// turns them into items.
+// Unit = (block b, 256 raw frontier words of range j).  Thread t reads word t
+// and keeps the bits whose column is nonempty (word-wise AND with V_{i,j}, the
+// column index of the block); the warps then expand the unit's items.
 __global__ void __launch_bounds__(kNT) expand_plain(LevelArgs a, int64_t units_per_block) {
-    __shared__ RoundSmem S;
     __shared__ uint32_t s_word[kNT];
     __shared__ uint32_t s_excl[kNT];
+    __shared__ unsigned long long red[kNT / 32 + 1];
     const int64_t nunits = (int64_t)a.p * a.p * units_per_block;
+    unsigned long long edges = 0, hits = 0;
     for (int64_t unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
         const int64_t b = unit / units_per_block, c = unit % units_per_block;
         const int64_t j = b % a.p;
@@ -164,31 +237,34 @@ __global__ void __launch_bounds__(kNT) expand_plain(LevelArgs a, int64_t units_p
             if (x) x &= __ldg(a.dir + b * a.dir_stride + w);
         }
         unsigned long long tot;
-        const unsigned long long ex = block_excl_scan<kNT>((unsigned long long)__popc(x), 0ull, OpSum(), S.red, &tot);
+        const unsigned long long ex = block_excl_scan<kNT>((unsigned long long)__popc(x), 0ull, OpSum(), red, &tot);
         if (tot == 0) continue;                                   // uniform
         s_word[threadIdx.x] = x;
         s_excl[threadIdx.x] = (uint32_t)ex;
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(a.ctr + C_ITEMS, tot);
-        for (uint64_t R = 0; R < tot; R += kNT) {
-            const uint64_t q = R + threadIdx.x;
+        const BlockView bv = block_view(a, b);
+        for (uint64_t q0 = (threadIdx.x & ~31u); q0 < tot; q0 += kNT) {
+            const uint64_t q = q0 + lane_id();
             int32_t u = 0;
             int64_t begin = 0;
             uint32_t len = 0;
             if (q < tot) {
-                int lo = 0, hi = kNT - 1;                          // last thread with excl <= q
+                int lo = 0, hi = kNT - 1;                          // last word with excl <= q
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
                     if (s_excl[mid] <= q) lo = mid; else hi = mid - 1;
                 }
                 const int bitpos = select32(s_word[lo], (int)(q - s_excl[lo]));
                 const int64_t ul = ((int64_t)c * kPlainUnitWords + lo) * 32 + bitpos;
-                column_of(a, b, ul, false, &begin, &len);
+                column_of(a, bv, ul, false, &begin, &len);
                 u = (int32_t)(jb + ul);
             }
-            expand_round(a, S, u, begin, len);
+            warp_expand(a, u, begin, len, edges, hits);
         }
+        __syncthreads();
     }
+    flush_counts(a, edges, hits);
 }
 
 // -------------------------------------------------------------------- WAH --
@@ -237,12 +313,12 @@ template <typename W>
 __global__ void __launch_bounds__(kNT) expand_wah(LevelArgs a) {
     using T = Wah<W>;
     constexpr int GB = T::GB;
-    __shared__ RoundSmem S;
     __shared__ W s_y[kChunkWords];
     __shared__ int64_t s_gs[kChunkWords];
     __shared__ uint32_t s_iex[kChunkWords];
     __shared__ unsigned long long red[kNT / 32 + 1];
     const int64_t nunits = (int64_t)*reinterpret_cast<volatile unsigned long long*>(a.ctr + C_UNITS);
+    unsigned long long edges = 0, hits = 0;
     for (int64_t ui = blockIdx.x; ui < nunits; ui += gridDim.x) {
         const Unit un = a.units[ui];
         const int64_t b = un.block;
@@ -296,8 +372,9 @@ __global__ void __launch_bounds__(kNT) expand_wah(LevelArgs a) {
         }
         __syncthreads();
         if (threadIdx.x == 0 && items) atomicAdd(a.ctr + C_ITEMS, items);
-        for (uint64_t R = 0; R < items; R += kNT) {
-            const uint64_t q = R + threadIdx.x;
+        const BlockView bv = block_view(a, b);
+        for (uint64_t q0 = (threadIdx.x & ~31u); q0 < items; q0 += kNT) {
+            const uint64_t q = q0 + lane_id();
             int32_t u = 0;
             int64_t begin = 0;
             uint32_t len = 0;
@@ -316,12 +393,14 @@ __global__ void __launch_bounds__(kNT) expand_wah(LevelArgs a) {
                 if (g0 >= G) ul = G * GB + T::select(T::from_active(yy, r), kk);
                 else if (is_fill<W>(yy)) ul = g0 * GB + kk;
                 else ul = g0 * GB + T::select(T::from_payload(yy), kk);
-                column_of(a, b, ul, !a.sieve, &begin, &len);
+                column_of(a, bv, ul, !a.sieve, &begin, &len);
                 u = (int32_t)(jb + ul);
             }
-            expand_round(a, S, u, begin, len);
+            warp_expand(a, u, begin, len, edges, hits);
         }
+        __syncthreads();
     }
+    flush_counts(a, edges, hits);
 }
 
 // ---------------------------------------------------------------- reduce --
@@ -460,6 +539,9 @@ bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
     BFS_TRY(W.chunk_base.alloc(sizeof(int64_t) * p2 * W.chunks_per_slot));
     BFS_TRY(W.units.alloc(sizeof(Unit) * p2 * W.chunks_per_slot));
     BFS_TRY(W.counters.alloc(sizeof(unsigned long long) * C_NUM));
+    // pieces: sum over long columns of ceil(len/kPiece) <= nnz/kPiece + nnz/kHub
+    W.piece_cap = L.nnz / kPiece + L.nnz / kHub + 16;
+    BFS_TRY(W.pieces.alloc(sizeof(Item) * W.piece_cap));
     if (!W.h_counters) {
         void* h = nullptr;
         BFS_CUDA_TRY(cudaMallocHost(&h, sizeof(uint64_t) * C_NUM));
@@ -475,7 +557,7 @@ bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
 void free_workspace(bfs_graph* g) {
     Workspace& W = g->W;
     W.pi.release(); W.fa.release(); W.fb.release(); W.fsum.release(); W.xbuf.release();
-    W.xcount.release(); W.chunk_base.release(); W.units.release(); W.counters.release();
+    W.xcount.release(); W.chunk_base.release(); W.units.release(); W.counters.release(); W.pieces.release();
     W.tmp_parent.release(); W.tmp_level.release();
     if (W.h_counters) cudaFreeHost(W.h_counters);
     W.h_counters = nullptr;
@@ -548,6 +630,8 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     a.chunk_base = W.chunk_base.as<int64_t>();
     a.chunks_per_slot = W.chunks_per_slot;
     a.units = static_cast<Unit*>(W.units.ptr);
+    a.pieces = W.pieces.as<Item>();
+    a.piece_cap = W.piece_cap;
     a.ctr = ctr;
     a.sieve = (mode == BFS_MODE_COMPRESS_SIEVE);
     a.nstreams = nslots;
@@ -608,6 +692,8 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             else expand_wah<unsigned long long><<<grid, kNT, 0, st>>>(a);
             BFS_CUDA_TRY(cudaGetLastError());
         }
+        expand_pieces<<<grid, kNT, 0, st>>>(a);
+        BFS_CUDA_TRY(cudaGetLastError());
         if (timing) cudaEventRecord(W.ev[3], st);
         reduce_level<<<std::min<int64_t>((W.bm_words + 255) / 256 + 1, sm_count() * 16), kNT, 0, st>>>(
             t, W.pi.as<uint32_t>(), f, W.fsum.as<uint8_t>(), W.bm_words, L.n, level, k + 1, ctr);

@@ -85,6 +85,7 @@ enum Counter : int {
     C_TRACE_USED,        // uint32 elements of the trace written so far
     C_WAH_WORDS,         // words of all streams of this level
     C_EXCHANGED,         // set bits carried by the exchange
+    C_PIECES,            // pieces of long columns queued for the piece kernel
     C_NUM
 };
 
@@ -98,7 +99,8 @@ struct Workspace {
     int slots = 0;              // exchange slots of the current mode
     int wah_bits = 0;
     int mode = -1;
-    DevBuf pi, fa, fb, fsum, xbuf, xcount, chunk_base, units, counters;
+    DevBuf pi, fa, fb, fsum, xbuf, xcount, chunk_base, units, counters, pieces;
+    int64_t piece_cap = 0;      // capacity of `pieces` (Item entries)
     DevBuf tmp_parent, tmp_level;      // for searches with host outputs
     uint64_t* h_counters = nullptr;    // pinned mirror of the counters
     cudaEvent_t ev[8] = {};
