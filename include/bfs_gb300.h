@@ -224,6 +224,27 @@ BFS_API bfs_status bfs_wah_encode(const uint32_t *bits, int64_t nbits, int32_t w
 BFS_API bfs_status bfs_wah_decode(const void *words, int64_t nwords, int64_t nbits, int32_t word_bits,
                           uint32_t *bits, void *cuda_stream);
 
+/*
+ * bfs_wah_decode without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory during a
+ * call -- a serving process that has reserved the whole HBM budget for
+ * resident graphs (where a cudaMalloc in the middle of a request fails), or a
+ * latency-critical thread that must not pay for cudaFree, which waits for the
+ * whole device.  It calls no cudaMalloc, cudaFree or allocating library code.
+ * Same arguments, output and errors as bfs_wah_decode, with one limit:
+ *   nbits <= 8,388,608; larger requests return BFS_ERR_INVALID_ARG.
+ * Its scratch (an error word and a staging copy of the bitmap, about 1 MiB) is
+ * one array in the library's static device memory, held by every device that
+ * loads the library until the process exits.  The first call on a device
+ * looks the array's address up (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call on a
+ * device shares the array and clears the part it uses before decoding, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it: order them.  Synchronises `cuda_stream`.
+ */
+BFS_API bfs_status bfs_wah_decode_static(const void *words, int64_t nwords, int64_t nbits, int32_t word_bits,
+                                         uint32_t *bits, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

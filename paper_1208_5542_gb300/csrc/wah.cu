@@ -12,6 +12,7 @@
 // whose frontier bits are all zero (frontier summary: one byte per 1024 bits)
 // are skipped without loading a word.
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -286,6 +287,36 @@ bfs_status launch_wah_decode_bitmap(const DecodeArgs& a, int wah_bits, cudaStrea
     return BFS_OK;
 }
 
+// ---------------------------------------------- allocation-free decoder --
+// Scratch of bfs_wah_decode_static: element 0 is the error word, the rest a
+// zeroed staging copy of the output bitmap (room for kStaticDecodeMaxBits
+// bits plus two words of padding).  Every device that loads the library holds
+// this array until the process exits; all calls on a device share it.
+constexpr int64_t kStaticDecodeMaxBits = (int64_t)1 << 23;                 // 8,388,608 bits
+constexpr int64_t kStaticDecodeWords = kStaticDecodeMaxBits / 32 + 2;      // uint32 staging words
+static __device__ __align__(256) unsigned long long g_decode_scratch[1 + (kStaticDecodeWords + 1) / 2];
+
+namespace {
+std::mutex g_scratch_mu;
+void* g_scratch_addr[256] = {};
+}
+
+// Device address of g_decode_scratch on the current device, resolved once per
+// device (the name is only a host-side stand-in in host code).
+bfs_status static_decode_scratch(void** out) {
+    int dev = 0;
+    BFS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return set_error(BFS_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        BFS_CUDA_TRY(cudaGetSymbolAddress(&p, g_decode_scratch));
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return BFS_OK;
+}
+
 }  // namespace bfsgb
 
 using namespace bfsgb;
@@ -343,6 +374,39 @@ bfs_status bfs_wah_decode(const void* words, int64_t nwords, int64_t nbits, int3
     BFS_CUDA_TRY(cudaMemcpyAsync(&h_err, err.ptr, sizeof(h_err), cudaMemcpyDeviceToHost, st));
     if (out_words > 0)
         BFS_CUDA_TRY(cudaMemcpyAsync(bits, pad.ptr, sizeof(uint32_t) * out_words, cudaMemcpyDeviceToDevice, st));
+    BFS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_err) return set_error(BFS_ERR_CORRUPT, "malformed WAH stream");
+    return BFS_OK;
+}
+
+bfs_status bfs_wah_decode_static(const void* words, int64_t nwords, int64_t nbits, int32_t word_bits, uint32_t* bits,
+                                 void* stream) {
+    if (word_bits != 32 && word_bits != 64) return set_error(BFS_ERR_INVALID_ARG, "word_bits must be 32 or 64");
+    if (nbits < 0 || nwords < 0 || (nwords > 0 && !words) || (nbits > 0 && !bits))
+        return set_error(BFS_ERR_INVALID_ARG, "bad decode arguments");
+    if (nbits > kStaticDecodeMaxBits)
+        return set_error(BFS_ERR_INVALID_ARG, "nbits %lld above the %lld-bit limit of the static scratch",
+                         (long long)nbits, (long long)kStaticDecodeMaxBits);
+    void* scratch = nullptr;
+    BFS_TRY(static_decode_scratch(&scratch));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned long long* err = static_cast<unsigned long long*>(scratch);
+    uint32_t* staging = reinterpret_cast<uint32_t*>(err + 1);
+    const int64_t out_words = (nbits + 31) / 32;
+    // the array keeps the previous call's contents: clear the error word and the staging words used
+    BFS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned long long), st));
+    BFS_CUDA_TRY(cudaMemsetAsync(staging, 0, sizeof(uint32_t) * (out_words + 2), st));
+    DecodeArgs a;
+    a.words = words;
+    a.nwords = nwords;
+    a.nbits = nbits;
+    a.bits = staging;
+    a.err = err;
+    BFS_TRY(launch_wah_decode_bitmap(a, word_bits, st));
+    unsigned long long h_err = 0;
+    BFS_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, st));
+    if (out_words > 0)
+        BFS_CUDA_TRY(cudaMemcpyAsync(bits, staging, sizeof(uint32_t) * out_words, cudaMemcpyDeviceToDevice, st));
     BFS_CUDA_TRY(cudaStreamSynchronize(st));
     if (h_err) return set_error(BFS_ERR_CORRUPT, "malformed WAH stream");
     return BFS_OK;

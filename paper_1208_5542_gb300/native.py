@@ -64,6 +64,7 @@ _SIGS = {
     "bfs_run": (ctypes.c_int, [vp, i32, vp, vp, P(RunStats), vp]),
     "bfs_wah_encode": (ctypes.c_int, [vp, i64, i32, vp, i64, vp, vp]),
     "bfs_wah_decode": (ctypes.c_int, [vp, i64, i64, i32, vp, vp]),
+    "bfs_wah_decode_static": (ctypes.c_int, [vp, i64, i64, i32, vp, vp]),
 }
 
 
