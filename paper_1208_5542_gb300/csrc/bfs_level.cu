@@ -19,6 +19,14 @@
 // The exchange itself (line 11) is the identity on one GPU: the receive buffer
 // g' is the send buffer in HBM; its sizes are scanned for the statistics and
 // packed into the caller's trace when one is requested.
+//
+// The expansion is row-affine: a block (i,j) only ever writes destinations of
+// range i, so a persistent CTA settles on one block-row at a time and keeps
+// that row's visited bits pi_i and its own partial next bits t_i in shared
+// memory (when a range fits); its warps take the row's units one at a time.
+// Visited tests and next-bit updates are then on-chip; the partial t_i of
+// every CTA is OR-folded into t when the CTA leaves the row (the fold of the
+// 2D partition, done through L2).
 #include <algorithm>
 #include <cstring>
 
@@ -33,17 +41,13 @@ bfs_status launch_wah_encode_counted(const EncodeArgs& a, int wah_bits, unsigned
 
 namespace {
 
-constexpr int kNT = 256;
-constexpr int kChunkWords = 1024;     // stream words per expansion unit (4 per thread)
-constexpr int kWordsPerThread = kChunkWords / kNT;
-constexpr int kPlainUnitWords = kNT;  // raw 32-bit frontier words per PLAIN unit
-
-struct Unit {
-    int32_t block;
-    int32_t stream;
-    int64_t word0;
-    int64_t gbase;
-};
+constexpr int kNT = 256;            // threads of the small kernels
+constexpr int kXT = 1024;           // threads of the expansion CTAs
+constexpr int kXW = kXT / 32;       // warps of the expansion CTAs
+constexpr uint32_t kCoop = 32;      // columns of at least this many entries take the whole warp
+constexpr uint32_t kHub = 1024;     // columns longer than this are cut into pieces
+constexpr uint32_t kPiece = 1024;   // entries per piece
+constexpr int64_t kSmemLimit = 227 * 1024;
 
 struct LevelArgs {
     // layout
@@ -67,12 +71,18 @@ struct LevelArgs {
     const int64_t* xcount;
     int64_t* chunk_base;
     int64_t chunks_per_slot;
-    Unit* units;
+    int64_t* slot_unit_base;            // p*p + 1: WAH units of slot s are [base[s], base[s+1])
+    // work distribution (per level)
+    unsigned long long* row_next;       // p
+    unsigned long long* row_piece_count;// p
+    unsigned long long* row_piece_next; // p
+    const int64_t* row_piece_base;      // p
+    const int64_t* row_piece_cap;       // p
     Item* pieces;
-    int64_t piece_cap;
     unsigned long long* ctr;
-    int sieve;                // 1: DIR-WAH streams (no directory test at the receiver)
-    int nstreams;
+    int mode;
+    int64_t plain_upb;                  // PLAIN units per block
+    int64_t win_words;                  // words of the shared-memory row window (0: none)
 };
 
 __device__ __forceinline__ int64_t range_begin(const LevelArgs& a, int64_t b) {
@@ -80,42 +90,73 @@ __device__ __forceinline__ int64_t range_begin(const LevelArgs& a, int64_t b) {
     return x < a.n ? x : a.n;
 }
 
-// Visit entry u -> v of the expansion: if v was not visited before this
-// level, lower parent[v] to u and set t[v].  Both updates are reductions whose
-// results are not used (fire-and-forget at L2); the only dependent load is the
-// visited word, read through the read-only path (pi does not change during the
-// expansion).
-__device__ __forceinline__ void visit(const LevelArgs& a, int32_t v, int32_t u) {
-    const uint32_t w = (uint32_t)v >> 5;
-    const uint32_t m = 1u << ((uint32_t)v & 31u);
-    if (__ldg(a.pi + w) & m) return;
-    atomicMin(reinterpret_cast<unsigned int*>(a.parent) + v, (unsigned int)u);   // -1 is the largest unsigned
-    atomicOr(a.t + w, m);
+// -------------------------------------------------------------- visiting --
+// Visit entry u -> v: if v was not visited before this level, lower parent[v]
+// to u and set v's next bit.  The parent update is a reduction whose result
+// is not used (fire-and-forget at L2).  With a row window, the visited test
+// and the next bit live in shared memory; without, the visited word is read
+// through the read-only path (pi does not change during the expansion) and
+// the next bit is a reduction at L2.
+template <bool WIN>
+struct Visitor {
+    const uint32_t* s_pi;
+    uint32_t* s_t;
+    int64_t rb;     // first vertex of the row
+    __device__ __forceinline__ void operator()(const LevelArgs& a, int32_t v, int32_t u) const {
+        if (WIN) {
+            const uint32_t vl = (uint32_t)(v - rb);
+            const uint32_t w = vl >> 5, m = 1u << (vl & 31u);
+            if (s_pi[w] & m) return;
+            atomicMin(reinterpret_cast<unsigned int*>(a.parent) + v, (unsigned int)u);   // -1 is the largest unsigned
+            atomicOr(s_t + w, m);
+        } else {
+            const uint32_t w = (uint32_t)v >> 5, m = 1u << ((uint32_t)v & 31u);
+            if (__ldg(a.pi + w) & m) return;
+            atomicMin(reinterpret_cast<unsigned int*>(a.parent) + v, (unsigned int)u);
+            atomicOr(a.t + w, m);
+        }
+    }
+};
+
+// All 32 lanes expand one column: 32 consecutive entries per step.
+template <bool WIN>
+__device__ __forceinline__ void warp_column(const LevelArgs& a, const Visitor<WIN>& vis, int32_t u, int64_t beg,
+                                            uint32_t len) {
+    const int32_t* col = a.ir + beg;
+    uint32_t e = lane_id();
+    for (; e + 32 < len; e += 64) {
+        const int32_t v0 = __ldg(col + e);
+        const int32_t v1 = __ldg(col + e + 32);
+        vis(a, v0, u);
+        vis(a, v1, u);
+    }
+    if (e < len) vis(a, __ldg(col + e), u);
 }
 
-constexpr uint32_t kHub = 1024;     // columns longer than this are cut into pieces
-constexpr uint32_t kPiece = 1024;   // entries per piece
-
 // Expand one item per lane (u, offset of its column in ir, length; length 0 =
-// none).  Columns longer than kHub go to the piece list; the rest are expanded
-// by the warp with a load-balanced search over the lanes' entry counts, so
-// every lane reads one entry per step and a step covers 32 consecutive entries
-// of the concatenated columns.
-__device__ __forceinline__ void warp_expand(const LevelArgs& a, int32_t u, int64_t beg, uint32_t len,
-                                            unsigned long long& edges, unsigned long long& hits) {
+// none).  Columns longer than kHub go to the row's piece list; columns of at
+// least kCoop entries are expanded by the whole warp one after the other; the
+// short ones share the warp through a load-balanced search over their entry
+// counts, 32 consecutive entries of the concatenated columns per step.
+template <bool WIN>
+__device__ __forceinline__ void warp_expand(const LevelArgs& a, const Visitor<WIN>& vis, int row, int32_t u,
+                                            int64_t beg, uint32_t len, unsigned long long& edges,
+                                            unsigned long long& hits) {
     const uint32_t lane = lane_id();
     hits += (len > 0);
+    edges += len;
     if (__any_sync(0xffffffffu, len > kHub)) {
         if (len > kHub) {
             const uint32_t np = (len + kPiece - 1) / kPiece;
-            const unsigned long long base = atomicAdd(a.ctr + C_PIECES, (unsigned long long)np);
-            if (base + np <= (unsigned long long)a.piece_cap) {
+            const unsigned long long base = atomicAdd(a.row_piece_count + row, (unsigned long long)np);
+            if (base + np <= (unsigned long long)a.row_piece_cap[row]) {
+                Item* dst = a.pieces + a.row_piece_base[row] + base;
                 for (uint32_t k = 0; k < np; ++k) {
                     Item it;
                     it.u = u;
                     it.len = (len - k * kPiece < kPiece) ? len - k * kPiece : kPiece;
                     it.begin = beg + (int64_t)k * kPiece;
-                    a.pieces[base + k] = it;
+                    dst[k] = it;
                 }
             } else {
                 atomicOr(a.ctr + C_ERROR, 8ull);        // piece list overflow (cannot happen by the bound)
@@ -123,32 +164,34 @@ __device__ __forceinline__ void warp_expand(const LevelArgs& a, int32_t u, int64
             len = 0;
         }
     }
+    uint32_t coop = __ballot_sync(0xffffffffu, len >= kCoop);
+    while (coop) {
+        const int src = __ffs(coop) - 1;
+        coop &= coop - 1;
+        warp_column<WIN>(a, vis, __shfl_sync(0xffffffffu, u, src), __shfl_sync(0xffffffffu, beg, src),
+                         __shfl_sync(0xffffffffu, len, src));
+    }
+    if (len >= kCoop) len = 0;
     const uint32_t incl = warp_incl_sum(len);
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     const uint32_t excl = incl - len;
-    edges += len;
     for (uint32_t e0 = 0; e0 < total; e0 += 32) {
         const uint32_t e = e0 + lane;
-        // owner: the first lane whose inclusive count exceeds e
-        int lo = 0, hi = 31;
+        int lo = 0, hi = 31;                       // owner: first lane whose inclusive count exceeds e
 #pragma unroll
         for (int step = 0; step < 5; ++step) {
             const int mid = (lo + hi) >> 1;
             const uint32_t im = __shfl_sync(0xffffffffu, incl, mid);
             if (im > e) hi = mid; else lo = mid + 1;
         }
-        const int o = lo;
-        const int64_t ob = __shfl_sync(0xffffffffu, beg, o);
-        const uint32_t oe = __shfl_sync(0xffffffffu, excl, o);
-        const int32_t ou = __shfl_sync(0xffffffffu, u, o);
-        if (e < total) {
-            const int32_t v = __ldg(a.ir + ob + (int64_t)(e - oe));
-            visit(a, v, ou);
-        }
+        const int64_t ob = __shfl_sync(0xffffffffu, beg, lo);
+        const uint32_t oe = __shfl_sync(0xffffffffu, excl, lo);
+        const int32_t ou = __shfl_sync(0xffffffffu, u, lo);
+        if (e < total) vis(a, __ldg(a.ir + ob + (int64_t)(e - oe)), ou);
     }
 }
 
-// Column of source u_local in block b: (offset into ir, len); len 0 if empty.
+// Column of source u_local in block b: (offset into ir, length); 0 if empty.
 struct BlockView {
     const uint32_t* dir;
     const uint32_t* rank;
@@ -182,225 +225,312 @@ __device__ __forceinline__ void column_of(const LevelArgs& a, const BlockView& b
     *len = c1 - c0;
 }
 
-__device__ __forceinline__ void flush_counts(const LevelArgs& a, unsigned long long edges, unsigned long long hits) {
+__device__ __forceinline__ void flush_counts(const LevelArgs& a, unsigned long long edges, unsigned long long hits,
+                                             unsigned long long items) {
     edges = warp_sum(edges);
     hits = warp_sum(hits);
+    items = warp_sum(items);
     if (lane_id() == 0) {
         if (edges) atomicAdd(a.ctr + C_EDGES, edges);
         if (hits) atomicAdd(a.ctr + C_HITS, hits);
+        if (items) atomicAdd(a.ctr + C_ITEMS, items);
     }
 }
 
-// Pieces of long columns: one warp per piece, 32 consecutive entries per step.
-__global__ void __launch_bounds__(kNT) expand_pieces(LevelArgs a) {
-    const int64_t np = (int64_t)*reinterpret_cast<volatile unsigned long long*>(a.ctr + C_PIECES);
-    const int64_t lim = np < a.piece_cap ? np : a.piece_cap;
-    const int64_t gw0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t gws = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t pc = gw0; pc < lim; pc += gws) {
-        const Item it = a.pieces[pc];
-        uint32_t e = lane_id();
-        for (; e + 96 < it.len; e += 128) {
-            const int32_t v0 = __ldg(a.ir + it.begin + e);
-            const int32_t v1 = __ldg(a.ir + it.begin + e + 32);
-            const int32_t v2 = __ldg(a.ir + it.begin + e + 64);
-            const int32_t v3 = __ldg(a.ir + it.begin + e + 96);
-            visit(a, v0, it.u);
-            visit(a, v1, it.u);
-            visit(a, v2, it.u);
-            visit(a, v3, it.u);
-        }
-        for (; e < it.len; e += 32) visit(a, __ldg(a.ir + it.begin + e), it.u);
+// Lane of the last of the 32 lanes whose exclusive count is <= q (the counts
+// are nondecreasing over the lanes); every lane must call it.
+__device__ __forceinline__ int owner_lane(uint32_t excl, uint64_t q) {
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int mid = (lo + hi + 1) >> 1;
+        const uint32_t em = __shfl_sync(0xffffffffu, excl, mid);
+        if ((uint64_t)em <= q) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------ row window --
+// Leave the current row: OR the CTA's partial next bits into t.
+__device__ void window_leave(const LevelArgs& a, uint32_t* s_t, int row) {
+    const int64_t rb = range_begin(a, row);
+    for (int64_t w = threadIdx.x; w < a.win_words; w += kXT) {
+        const uint32_t x = s_t[w];
+        if (!x) continue;
+        const int64_t pos = rb + 32 * w;
+        const int64_t gw = pos >> 5;
+        const uint32_t sh = (uint32_t)(pos & 31);
+        atomicOr(a.t + gw, x << sh);
+        if (sh && (x >> (32 - sh))) atomicOr(a.t + gw + 1, x >> (32 - sh));
     }
 }
 
-// ------------------------------------------------------------------ PLAIN --
-// Unit = (block b, 256 raw frontier words of range j).  Thread t reads word t
-// and keeps the bits whose column is nonempty (word-wise AND with V_{i,j}, the
-// column index of the block); the warps then expand the unit's items.
-__global__ void __launch_bounds__(kNT) expand_plain(LevelArgs a, int64_t units_per_block) {
-    __shared__ uint32_t s_word[kNT];
-    __shared__ uint32_t s_excl[kNT];
-    __shared__ unsigned long long red[kNT / 32 + 1];
-    const int64_t nunits = (int64_t)a.p * a.p * units_per_block;
-    unsigned long long edges = 0, hits = 0;
-    for (int64_t unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
-        const int64_t b = unit / units_per_block, c = unit % units_per_block;
-        const int64_t j = b % a.p;
-        const int64_t jb = range_begin(a, j), jl = range_begin(a, j + 1) - jb;
-        const int64_t w = c * kPlainUnitWords + threadIdx.x;     // word of the slice
-        uint32_t x = 0;
-        if (w * 32 < jl) {
-            x = bits32_at_cg(a.f, (uint64_t)(jb + w * 32));
-            const int64_t left = jl - w * 32;
-            if (left < 32) x &= (1u << left) - 1u;
-            if (x) x &= __ldg(a.dir + b * a.dir_stride + w);
-        }
-        unsigned long long tot;
-        const unsigned long long ex = block_excl_scan<kNT>((unsigned long long)__popc(x), 0ull, OpSum(), red, &tot);
-        if (tot == 0) continue;                                   // uniform
-        s_word[threadIdx.x] = x;
-        s_excl[threadIdx.x] = (uint32_t)ex;
-        __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(a.ctr + C_ITEMS, tot);
-        const BlockView bv = block_view(a, b);
-        for (uint64_t q0 = (threadIdx.x & ~31u); q0 < tot; q0 += kNT) {
-            const uint64_t q = q0 + lane_id();
-            int32_t u = 0;
-            int64_t begin = 0;
-            uint32_t len = 0;
-            if (q < tot) {
-                int lo = 0, hi = kNT - 1;                          // last word with excl <= q
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_excl[mid] <= q) lo = mid; else hi = mid - 1;
-                }
-                const int bitpos = select32(s_word[lo], (int)(q - s_excl[lo]));
-                const int64_t ul = ((int64_t)c * kPlainUnitWords + lo) * 32 + bitpos;
-                column_of(a, bv, ul, false, &begin, &len);
-                u = (int32_t)(jb + ul);
-            }
-            warp_expand(a, u, begin, len, edges, hits);
-        }
-        __syncthreads();
+// Enter a row: load pi_i into the window and clear the partial next bits.
+__device__ void window_enter(const LevelArgs& a, uint32_t* s_pi, uint32_t* s_t, int row) {
+    const int64_t rb = range_begin(a, row);
+    for (int64_t w = threadIdx.x; w < a.win_words; w += kXT) {
+        const int64_t pos = rb + 32 * w;
+        s_pi[w] = (pos < a.n) ? bits32_at_cg(a.pi, (uint64_t)pos) : 0xffffffffu;
+        s_t[w] = 0u;
     }
-    flush_counts(a, edges, hits);
 }
 
-// -------------------------------------------------------------------- WAH --
-// Per stream: group base of every chunk of kChunkWords words, and the units
-// (block, stream, chunk) of the expansion.  One CTA per stream.
-template <typename W>
-__global__ void __launch_bounds__(kNT) stream_chunks(LevelArgs a) {
-    __shared__ unsigned long long red[kNT / 32 + 1];
-    __shared__ int64_t s_base;
-    const int s = blockIdx.x;
-    const W* in = static_cast<const W*>(a.xbuf) + (int64_t)s * a.slot_cap;
-    const int64_t count = a.xcount[s];
-    const int64_t nch = (count + kChunkWords - 1) / kChunkWords;
-    unsigned long long gpos = 0;
-    for (int64_t ch = 0; ch < nch; ++ch) {
-        unsigned long long g = 0;
-        for (int k = 0; k < kWordsPerThread; ++k) {
-            const int64_t x = ch * kChunkWords + (int64_t)k * kNT + threadIdx.x;
-            if (x < count) g += word_groups<W>(in[x]);
+// Row-affine persistent loop.  The CTA settles on a block-row with units
+// left; its warps take the row's units one at a time (warp-granular, no block
+// barrier per unit) until the row is drained, then the CTA folds its partial
+// next bits into t, picks the next row with units left and loads that row's
+// visited bits.  Every row is tried at most once per CTA.
+template <bool WIN, typename Units, typename Work>
+__device__ __forceinline__ void row_affine(const LevelArgs& a, unsigned long long* counters, Units units_in_row,
+                                           Work do_unit, uint32_t* s_pi, uint32_t* s_t, int* s_row) {
+    const int p = a.p;
+    int tried = 0;
+    int start = blockIdx.x % p;
+    auto pick = [&](int from) -> int {          // thread 0: next row with units, or -1
+        while (tried < p) {
+            const int r = from;
+            from = (from + 1 == p) ? 0 : from + 1;
+            ++tried;
+            if ((int64_t)*reinterpret_cast<volatile unsigned long long*>(counters + r) < units_in_row(r)) return r;
         }
-        if (threadIdx.x == 0) a.chunk_base[(int64_t)s * a.chunks_per_slot + ch] = (int64_t)gpos;
-        unsigned long long tot;
-        block_excl_scan<kNT>(g, 0ull, OpSum(), red, &tot);
-        gpos += tot;
-    }
-    const int copies = a.sieve ? 1 : a.p;       // COMPRESS: every block-row decodes stream j
-    if (threadIdx.x == 0) {
-        s_base = (int64_t)atomicAdd(a.ctr + C_UNITS, (unsigned long long)(nch * copies));
-        atomicAdd(a.ctr + C_WAH_WORDS, (unsigned long long)count);
-    }
+        return -1;
+    };
+    if (threadIdx.x == 0) s_row[0] = pick(start);
     __syncthreads();
-    for (int64_t q = threadIdx.x; q < nch * copies; q += kNT) {
-        const int64_t ch = q % nch, i = q / nch;
-        Unit un;
-        un.block = a.sieve ? s : (int32_t)(i * a.p + s);
-        un.stream = s;
-        un.word0 = ch * kChunkWords;
-        un.gbase = a.chunk_base[(int64_t)s * a.chunks_per_slot + ch];
-        a.units[s_base + q] = un;
+    int row = s_row[0];
+    if (WIN && row >= 0) window_enter(a, s_pi, s_t, row);
+    __syncthreads();
+    while (row >= 0) {
+        const int64_t nu = units_in_row(row);
+        for (;;) {
+            int64_t x = 0;
+            if (lane_id() == 0) {
+                x = ((int64_t)*reinterpret_cast<volatile unsigned long long*>(counters + row) < nu)
+                        ? (int64_t)atomicAdd(counters + row, 1ull) : nu;
+            }
+            x = __shfl_sync(0xffffffffu, x, 0);
+            if (x >= nu) break;
+            do_unit(row, x);
+        }
+        __syncthreads();
+        if (WIN) window_leave(a, s_t, row);
+        if (threadIdx.x == 0) s_row[0] = pick(row + 1 == p ? 0 : row + 1);
+        __syncthreads();
+        row = s_row[0];
+        if (WIN && row >= 0) window_enter(a, s_pi, s_t, row);
+        __syncthreads();
     }
 }
 
-// Fused decode + expansion of the units: words of one chunk -> (u, block)
-// items -> entries.
-template <typename W>
-__global__ void __launch_bounds__(kNT) expand_wah(LevelArgs a) {
+// ---------------------------------------------------------------- kernels --
+// Expansion of the WAH units (COMPRESS, COMPRESS_SIEVE).  Unit = 32 words of
+// one stream, decoded by one warp: a warp scan of run lengths from the
+// chunk's group base places every word, a scan of item counts numbers the
+// decoded vertices, and the warp expands them 32 at a time.
+template <typename W, bool WIN>
+__global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
     using T = Wah<W>;
     constexpr int GB = T::GB;
-    __shared__ W s_y[kChunkWords];
-    __shared__ int64_t s_gs[kChunkWords];
-    __shared__ uint32_t s_iex[kChunkWords];
-    __shared__ unsigned long long red[kNT / 32 + 1];
-    const int64_t nunits = (int64_t)*reinterpret_cast<volatile unsigned long long*>(a.ctr + C_UNITS);
-    unsigned long long edges = 0, hits = 0;
-    for (int64_t ui = blockIdx.x; ui < nunits; ui += gridDim.x) {
-        const Unit un = a.units[ui];
-        const int64_t b = un.block;
-        const int64_t j = b % a.p;
+    extern __shared__ uint32_t s_win[];                   // s_pi | s_t (WIN only)
+    __shared__ int s_row[2];
+    uint32_t* s_pi = s_win;
+    uint32_t* s_t = s_win + a.win_words;
+    const int p = a.p;
+    unsigned long long edges = 0, hits = 0, nitems = 0;
+    auto units_in_row = [&](int r) -> int64_t {
+        return a.slot_unit_base[(int64_t)(r + 1) * p] - a.slot_unit_base[(int64_t)r * p];
+    };
+    auto do_unit = [&](int row, int64_t x) {
+        // unit -> (slot, chunk): the slot s of the row with base[s] <= g < base[s+1]
+        const int64_t g = a.slot_unit_base[(int64_t)row * p] + x;
+        int64_t lo = (int64_t)row * p, hi = (int64_t)row * p + p - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (a.slot_unit_base[mid] <= g) lo = mid; else hi = mid - 1;
+        }
+        const int64_t s = lo, k = g - a.slot_unit_base[s];
+        const int64_t j = s % p;
+        const int64_t stream = (a.mode == BFS_MODE_COMPRESS_SIEVE) ? s : j;
         const int64_t jb = range_begin(a, j), jl = range_begin(a, j + 1) - jb;
         const int64_t G = jl / GB;
         const int r = (int)(jl % GB);
-        const W* in = static_cast<const W*>(a.xbuf) + (int64_t)un.stream * a.slot_cap;
-        const int64_t count = a.xcount[un.stream];
-        // this thread's words: blocked, kWordsPerThread consecutive words
-        W y[kWordsPerThread];
-        unsigned long long glen[kWordsPerThread];
-        unsigned long long gsum = 0;
-#pragma unroll
-        for (int k = 0; k < kWordsPerThread; ++k) {
-            const int64_t x = un.word0 + (int64_t)threadIdx.x * kWordsPerThread + k;
-            y[k] = (x < count) ? in[x] : W(0);
-            glen[k] = (x < count) ? word_groups<W>(y[k]) : 0ull;
-            gsum += glen[k];
-        }
-        unsigned long long tot;
-        unsigned long long gs = (unsigned long long)un.gbase +
-                                block_excl_scan<kNT>(gsum, 0ull, OpSum(), red, &tot);
-        unsigned long long icount = 0;
-        uint32_t ic[kWordsPerThread];
-#pragma unroll
-        for (int k = 0; k < kWordsPerThread; ++k) {
-            const int64_t x = un.word0 + (int64_t)threadIdx.x * kWordsPerThread + k;
-            uint32_t c = 0;
-            if (x < count) {
-                if (gs < (unsigned long long)G) {
-                    if (is_fill<W>(y[k])) c = (y[k] & T::VAL) ? (uint32_t)(glen[k] * GB) : 0u;
-                    else c = (uint32_t)T::popc(T::from_payload(y[k]));
-                } else if (r > 0) {
-                    c = (uint32_t)T::popc(T::from_active(y[k], r));      // the active word
-                    glen[k] = 0;
-                }
+        const W* in = static_cast<const W*>(a.xbuf) + stream * a.slot_cap;
+        const int64_t count = a.xcount[stream];
+        const int64_t xw = k * 32 + lane_id();
+        const W y = (xw < count) ? in[xw] : W(0);
+        const uint64_t glen = (xw < count) ? word_groups<W>(y) : 0ull;
+        const uint64_t gincl = warp_incl_sum(glen);
+        const int64_t gs = a.chunk_base[stream * a.chunks_per_slot + k] + (int64_t)(gincl - glen);
+        uint32_t c = 0;
+        if (xw < count) {
+            if (gs < G) {
+                if (is_fill<W>(y)) c = (y & T::VAL) ? (uint32_t)(glen * GB) : 0u;
+                else c = (uint32_t)T::popc(T::from_payload(y));
+            } else if (r > 0) {
+                c = (uint32_t)T::popc(T::from_active(y, r));      // the active word
             }
-            ic[k] = c;
-            s_y[threadIdx.x * kWordsPerThread + k] = y[k];
-            s_gs[threadIdx.x * kWordsPerThread + k] = (int64_t)gs;
-            gs += glen[k];
-            icount += c;
         }
-        unsigned long long items;
-        unsigned long long iex = block_excl_scan<kNT>(icount, 0ull, OpSum(), red, &items);
-#pragma unroll
-        for (int k = 0; k < kWordsPerThread; ++k) {
-            s_iex[threadIdx.x * kWordsPerThread + k] = (uint32_t)iex;
-            iex += ic[k];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && items) atomicAdd(a.ctr + C_ITEMS, items);
-        const BlockView bv = block_view(a, b);
-        for (uint64_t q0 = (threadIdx.x & ~31u); q0 < items; q0 += kNT) {
-            const uint64_t q = q0 + lane_id();
+        const uint32_t cincl = warp_incl_sum(c);
+        const uint32_t cexcl = cincl - c;
+        const uint32_t items = __shfl_sync(0xffffffffu, cincl, 31);
+        nitems += c;
+        const BlockView bv = block_view(a, s);
+        const Visitor<WIN> vis{s_pi, s_t, range_begin(a, row)};
+        for (uint32_t q0 = 0; q0 < items; q0 += 32) {
+            const uint32_t q = q0 + lane_id();
+            const int o = owner_lane(cexcl, q < items ? q : items - 1);
+            const W yy = __shfl_sync(0xffffffffu, y, o);
+            const int64_t g0 = __shfl_sync(0xffffffffu, gs, o);
+            const uint32_t oex = __shfl_sync(0xffffffffu, cexcl, o);
             int32_t u = 0;
             int64_t begin = 0;
             uint32_t len = 0;
             if (q < items) {
-                int lo = 0, hi = kChunkWords - 1;                  // last word with iex <= q
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_iex[mid] <= q) lo = mid; else hi = mid - 1;
-                }
-                // words with no items share the same iex: step back over none (lo is the last
-                // word with iex <= q; it has items because q < next word's iex)
-                const W yy = s_y[lo];
-                const int64_t g0 = s_gs[lo];
-                const int kk = (int)(q - s_iex[lo]);
+                const int kk = (int)(q - oex);
                 int64_t ul;
                 if (g0 >= G) ul = G * GB + T::select(T::from_active(yy, r), kk);
                 else if (is_fill<W>(yy)) ul = g0 * GB + kk;
                 else ul = g0 * GB + T::select(T::from_payload(yy), kk);
-                column_of(a, bv, ul, !a.sieve, &begin, &len);
+                if (a.mode == BFS_MODE_COMPRESS_SIEVE &&
+                    !(__ldg(bv.dir + (ul >> 5)) & (1u << (ul & 31))) &&
+                    atomicCAS(a.ctr + C_DBG, 0ull, 1ull + (unsigned long long)s) == 0ull) {
+                    // context of the first decoded vertex without a column
+                    a.ctr[C_DBG + 1] = (unsigned long long)k;
+                    a.ctr[C_DBG + 2] = (unsigned long long)(k * 32 + o);
+                    a.ctr[C_DBG + 3] = (unsigned long long)yy;
+                    a.ctr[C_DBG + 4] = (unsigned long long)g0;
+                    a.ctr[C_DBG + 5] = (unsigned long long)ul;
+                }
+                column_of(a, bv, ul, a.mode != BFS_MODE_COMPRESS_SIEVE, &begin, &len);
                 u = (int32_t)(jb + ul);
             }
-            warp_expand(a, u, begin, len, edges, hits);
+            warp_expand<WIN>(a, vis, row, u, begin, len, edges, hits);
         }
-        __syncthreads();
+    };
+    row_affine<WIN>(a, a.row_next, units_in_row, do_unit, s_pi, s_t, s_row);
+    flush_counts(a, edges, hits, nitems);
+}
+
+// Expansion of the PLAIN units.  Unit = (block (row, j), 32 raw frontier words
+// of range j), one warp: lane l keeps word l's bits whose column is nonempty
+// (word-wise AND with V_{i,j}, the block's column index) and the warp expands
+// them 32 at a time.
+template <bool WIN>
+__global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
+    extern __shared__ uint32_t s_win[];
+    __shared__ int s_row[2];
+    uint32_t* s_pi = s_win;
+    uint32_t* s_t = s_win + a.win_words;
+    const int p = a.p;
+    unsigned long long edges = 0, hits = 0, nitems = 0;
+    const int64_t per_row = (int64_t)p * a.plain_upb;
+    auto units_in_row = [&](int) -> int64_t { return per_row; };
+    auto do_unit = [&](int row, int64_t x) {
+        const int64_t j = x / a.plain_upb, c = x % a.plain_upb;
+        const int64_t b = (int64_t)row * p + j;
+        const int64_t jb = range_begin(a, j), jl = range_begin(a, j + 1) - jb;
+        const int64_t w = c * 32 + lane_id();
+        uint32_t bits = 0;
+        if (w * 32 < jl) {
+            bits = bits32_at_cg(a.f, (uint64_t)(jb + w * 32));
+            const int64_t left = jl - w * 32;
+            if (left < 32) bits &= (1u << left) - 1u;
+            if (bits) bits &= __ldg(a.dir + b * a.dir_stride + w);
+        }
+        const uint32_t cnt = __popc(bits);
+        const uint32_t cincl = warp_incl_sum(cnt);
+        const uint32_t cexcl = cincl - cnt;
+        const uint32_t items = __shfl_sync(0xffffffffu, cincl, 31);
+        if (items == 0) return;
+        nitems += cnt;
+        const BlockView bv = block_view(a, b);
+        const Visitor<WIN> vis{s_pi, s_t, range_begin(a, row)};
+        for (uint32_t q0 = 0; q0 < items; q0 += 32) {
+            const uint32_t q = q0 + lane_id();
+            const int o = owner_lane(cexcl, q < items ? q : items - 1);
+            const uint32_t ob = __shfl_sync(0xffffffffu, bits, o);
+            const uint32_t oex = __shfl_sync(0xffffffffu, cexcl, o);
+            int32_t u = 0;
+            int64_t begin = 0;
+            uint32_t len = 0;
+            if (q < items) {
+                const int64_t ul = (c * 32 + o) * 32 + select32(ob, (int)(q - oex));
+                column_of(a, bv, ul, false, &begin, &len);
+                u = (int32_t)(jb + ul);
+            }
+            warp_expand<WIN>(a, vis, row, u, begin, len, edges, hits);
+        }
+    };
+    row_affine<WIN>(a, a.row_next, units_in_row, do_unit, s_pi, s_t, s_row);
+    flush_counts(a, edges, hits, nitems);
+}
+
+// Pieces of long columns, row by row: one warp per piece.
+template <bool WIN>
+__global__ void __launch_bounds__(kXT, 1) expand_pieces(LevelArgs a) {
+    extern __shared__ uint32_t s_win[];
+    __shared__ int s_row[2];
+    uint32_t* s_pi = s_win;
+    uint32_t* s_t = s_win + a.win_words;
+    auto units_in_row = [&](int r) -> int64_t {
+        return (int64_t)min(a.row_piece_count[r], (unsigned long long)a.row_piece_cap[r]);
+    };
+    auto do_unit = [&](int row, int64_t x) {
+        const Item it = a.pieces[a.row_piece_base[row] + x];
+        const Visitor<WIN> vis{s_pi, s_t, range_begin(a, row)};
+        warp_column<WIN>(a, vis, it.u, it.begin, it.len);
+    };
+    row_affine<WIN>(a, a.row_piece_next, units_in_row, do_unit, s_pi, s_t, s_row);
+}
+
+// Per stream: group base of every chunk of 32 words.  One CTA per stream;
+// thread t holds 4 consecutive words of a 1024-word tile, so threads 8m..8m+7
+// cover chunk m of the tile and thread 8m's exclusive prefix is its base.
+template <typename W>
+__global__ void __launch_bounds__(kNT) stream_chunks(LevelArgs a, int nstreams) {
+    __shared__ unsigned long long red[kNT / 32 + 1];
+    const int s = blockIdx.x;
+    if (s >= nstreams) return;
+    const W* in = static_cast<const W*>(a.xbuf) + (int64_t)s * a.slot_cap;
+    const int64_t count = a.xcount[s];
+    unsigned long long gpos = 0;
+    for (int64_t t0 = 0; t0 < count; t0 += 4 * kNT) {
+        const int64_t x0 = t0 + 4 * (int64_t)threadIdx.x;
+        unsigned long long g = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (x0 + k < count) g += word_groups<W>(in[x0 + k]);
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan<kNT>(g, 0ull, OpSum(), red, &tot);
+        if ((threadIdx.x & 7) == 0 && x0 < count)
+            a.chunk_base[(int64_t)s * a.chunks_per_slot + x0 / 32] = (int64_t)(gpos + ex);
+        gpos += tot;
     }
-    flush_counts(a, edges, hits);
+    if (threadIdx.x == 0) atomicAdd(a.ctr + C_WAH_WORDS, (unsigned long long)count);
+}
+
+// Units of every slot (block (i,j) decodes stream s = i*p+j, or stream j in
+// COMPRESS mode): exclusive scan of 32-word chunk counts over the slots, row-major.
+__global__ void __launch_bounds__(kNT) plan_units(LevelArgs a) {
+    __shared__ unsigned long long red[kNT / 32 + 1];
+    const int64_t nslots = (int64_t)a.p * a.p;
+    unsigned long long carry = 0;
+    for (int64_t s0 = 0; s0 < nslots; s0 += kNT) {
+        const int64_t s = s0 + threadIdx.x;
+        unsigned long long nch = 0;
+        if (s < nslots) {
+            const int64_t stream = (a.mode == BFS_MODE_COMPRESS_SIEVE) ? s : s % a.p;
+            nch = (unsigned long long)((a.xcount[stream] + 31) / 32);
+        }
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan<kNT>(nch, 0ull, OpSum(), red, &tot);
+        if (s < nslots) a.slot_unit_base[s] = (int64_t)(carry + ex);
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        a.slot_unit_base[nslots] = (int64_t)carry;
+        a.ctr[C_UNITS] = carry;
+    }
 }
 
 // ---------------------------------------------------------------- reduce --
@@ -514,6 +644,16 @@ int sm_count() {
     return cached;
 }
 
+// Dynamic shared memory of the expansion kernels: the row window (pi_i and
+// the partial t_i), when it fits next to the static arrays.
+size_t window_bytes(int64_t win_words) { return (size_t)(2 * win_words * sizeof(uint32_t)); }
+
+template <typename K>
+bfs_status allow_smem(K kernel, size_t dyn) {
+    BFS_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    return BFS_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- workspace --
@@ -522,13 +662,14 @@ bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
     Workspace& W = g->W;
     const Layout& L = g->L;
     if (W.bm_words) return BFS_OK;
-    const int64_t p2 = (int64_t)L.p * L.p;
+    const int p = L.p;
+    const int64_t p2 = (int64_t)p * p;
     W.bm_words = ((L.n + 31) / 32 + 4 + 3) / 4 * 4;
-    W.fsum_len = (W.bm_words + 31) / 32 + 64;
+    W.fsum_len = ((W.bm_words + 31) / 32 + 64 + 3) / 4 * 4;   // whole 32-bit words
     const int64_t cap32 = L.nb / 31 + 2, cap64 = L.nb / 63 + 2;
-    W.slot_cap = cap32;                                   // in words of the current width (set per run)
-    W.chunk_words = kChunkWords;
-    W.chunks_per_slot = (cap32 + kChunkWords - 1) / kChunkWords;
+    W.slot_cap = cap32;
+    W.chunk_words = 32;
+    W.chunks_per_slot = (cap32 + 31) / 32;
     const int64_t xbytes = p2 * std::max<int64_t>(4 * cap32, 8 * cap64);
     BFS_TRY(W.pi.alloc(4 * W.bm_words));
     BFS_TRY(W.fa.alloc(4 * W.bm_words));
@@ -537,11 +678,25 @@ bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
     BFS_TRY(W.xbuf.alloc(xbytes));
     BFS_TRY(W.xcount.alloc(sizeof(int64_t) * p2));
     BFS_TRY(W.chunk_base.alloc(sizeof(int64_t) * p2 * W.chunks_per_slot));
-    BFS_TRY(W.units.alloc(sizeof(Unit) * p2 * W.chunks_per_slot));
+    BFS_TRY(W.units.alloc(sizeof(int64_t) * (p2 + 1)));              // slot unit bases
     BFS_TRY(W.counters.alloc(sizeof(unsigned long long) * C_NUM));
-    // pieces: sum over long columns of ceil(len/kPiece) <= nnz/kPiece + nnz/kHub
-    W.piece_cap = L.nnz / kPiece + L.nnz / kHub + 16;
-    BFS_TRY(W.pieces.alloc(sizeof(Item) * W.piece_cap));
+    // pieces: per row, sum over long columns of ceil(len/kPiece) <= nnz_row/kPiece + nnz_row/kHub
+    std::vector<int64_t> meta(2 * (size_t)p);
+    int64_t total = 0;
+    for (int i = 0; i < p; ++i) {
+        int64_t nnz_row = 0;
+        for (int j = 0; j < p; ++j) nnz_row += L.nnz_b[(int64_t)i * p + j];
+        const int64_t cap = nnz_row / kPiece + nnz_row / kHub + 4;
+        meta[i] = total;
+        meta[p + i] = cap;
+        total += cap;
+    }
+    W.piece_cap = total;
+    BFS_TRY(W.pieces.alloc(sizeof(Item) * (total > 0 ? total : 1)));
+    // per-level scratch: row_next[p], row_piece_count[p], row_piece_next[p]; row piece bases and caps
+    BFS_TRY(W.level_scratch.alloc(sizeof(unsigned long long) * 3 * p));
+    BFS_TRY(W.row_meta.alloc(sizeof(int64_t) * 2 * p));
+    BFS_CUDA_TRY(cudaMemcpy(W.row_meta.ptr, meta.data(), sizeof(int64_t) * 2 * p, cudaMemcpyHostToDevice));
     if (!W.h_counters) {
         void* h = nullptr;
         BFS_CUDA_TRY(cudaMallocHost(&h, sizeof(uint64_t) * C_NUM));
@@ -551,6 +706,17 @@ bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
         for (auto& e : W.ev) BFS_CUDA_TRY(cudaEventCreate(&e));
         W.events = true;
     }
+    // the row window of the expansion: pi_i and t_i of one range, if they fit
+    const int64_t win = (L.nb + 31) / 32;
+    const size_t static_bytes = 1024;
+    W.win_words = (window_bytes(win) + static_bytes <= (size_t)kSmemLimit) ? win : 0;
+    if (W.win_words) {
+        const size_t dyn = window_bytes(W.win_words);
+        BFS_TRY(allow_smem(expand_wah<uint32_t, true>, dyn));
+        BFS_TRY(allow_smem(expand_wah<unsigned long long, true>, dyn));
+        BFS_TRY(allow_smem(expand_plain<true>, dyn));
+        BFS_TRY(allow_smem(expand_pieces<true>, dyn));
+    }
     return BFS_OK;
 }
 
@@ -558,6 +724,7 @@ void free_workspace(bfs_graph* g) {
     Workspace& W = g->W;
     W.pi.release(); W.fa.release(); W.fb.release(); W.fsum.release(); W.xbuf.release();
     W.xcount.release(); W.chunk_base.release(); W.units.release(); W.counters.release(); W.pieces.release();
+    W.level_scratch.release(); W.row_meta.release();
     W.tmp_parent.release(); W.tmp_level.release();
     if (W.h_counters) cudaFreeHost(W.h_counters);
     W.h_counters = nullptr;
@@ -598,7 +765,9 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     const bool timing = stats && stats->timing;
     const bool tracing = stats && stats->trace_words && stats->trace_counts && nslots > 0;
     unsigned long long* ctr = W.counters.as<unsigned long long>();
-    const int grid = sm_count() * 8;
+    const bool win = W.win_words > 0;
+    const int xgrid = sm_count();                  // persistent: one 1024-thread CTA per SM
+    const size_t dyn = win ? window_bytes(W.win_words) : 0;
     DevBuf slot_off;
     if (tracing) BFS_TRY(slot_off.alloc(sizeof(int64_t) * nslots));
     if (stats) { stats->n_levels = 0; stats->trace_used = 0; }
@@ -629,12 +798,18 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     a.xcount = W.xcount.as<int64_t>();
     a.chunk_base = W.chunk_base.as<int64_t>();
     a.chunks_per_slot = W.chunks_per_slot;
-    a.units = static_cast<Unit*>(W.units.ptr);
+    a.slot_unit_base = W.units.as<int64_t>();
+    unsigned long long* lvl = W.level_scratch.as<unsigned long long>();
+    a.row_next = lvl;
+    a.row_piece_count = lvl + p;
+    a.row_piece_next = lvl + 2 * p;
+    a.row_piece_base = W.row_meta.as<int64_t>();
+    a.row_piece_cap = W.row_meta.as<int64_t>() + p;
     a.pieces = W.pieces.as<Item>();
-    a.piece_cap = W.piece_cap;
     a.ctr = ctr;
-    a.sieve = (mode == BFS_MODE_COMPRESS_SIEVE);
-    a.nstreams = nslots;
+    a.mode = mode;
+    a.plain_upb = (L.nb + 1023) / 1024;               // 32 raw words per PLAIN unit
+    a.win_words = W.win_words;
 
     EncodeArgs ea;
     memset(&ea, 0, sizeof(ea));
@@ -643,7 +818,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     ea.p = p;
     ea.nb = L.nb;
     ea.n = L.n;
-    ea.sieve = a.sieve;
+    ea.sieve = (mode == BFS_MODE_COMPRESS_SIEVE);
     ea.nslots = nslots;
     ea.fsum = W.fsum.as<uint8_t>();
     ea.out = W.xbuf.ptr;
@@ -656,25 +831,28 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     int64_t raw_bytes = 0;
     for (int j = 0; j < p; ++j) raw_bytes += 4 * ((L.range_len(j) + 31) / 32);
     raw_bytes *= p;
-    const int64_t units_per_block = (L.nb + 32LL * kPlainUnitWords - 1) / (32LL * kPlainUnitWords);
 
     for (int32_t k = 0;; ++k) {
         if (k > 0) {   // per-level counters; the error flag and the trace cursor persist
             BFS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * C_ERROR, st));
             BFS_CUDA_TRY(cudaMemsetAsync(ctr + C_WAH_WORDS, 0, sizeof(unsigned long long) * (C_NUM - C_WAH_WORDS), st));
         }
+        BFS_CUDA_TRY(cudaMemsetAsync(lvl, 0, sizeof(unsigned long long) * 3 * p, st));
         a.f = f;
         a.t = t;
         ea.frontier = f;
         if (timing) cudaEventRecord(W.ev[0], st);
         if (mode == BFS_MODE_PLAIN) {
             if (timing) { cudaEventRecord(W.ev[1], st); cudaEventRecord(W.ev[2], st); }
-            expand_plain<<<grid, kNT, 0, st>>>(a, units_per_block);
+            if (win) expand_plain<true><<<xgrid, kXT, dyn, st>>>(a);
+            else expand_plain<false><<<xgrid, kXT, 0, st>>>(a);
             BFS_CUDA_TRY(cudaGetLastError());
         } else {
             BFS_TRY(launch_wah_encode_counted(ea, wbits, ctr + C_EXCHANGED, st));
-            if (wbits == 32) stream_chunks<uint32_t><<<nslots, kNT, 0, st>>>(a);
-            else stream_chunks<unsigned long long><<<nslots, kNT, 0, st>>>(a);
+            if (wbits == 32) stream_chunks<uint32_t><<<nslots, kNT, 0, st>>>(a, nslots);
+            else stream_chunks<unsigned long long><<<nslots, kNT, 0, st>>>(a, nslots);
+            BFS_CUDA_TRY(cudaGetLastError());
+            plan_units<<<1, kNT, 0, st>>>(a);
             BFS_CUDA_TRY(cudaGetLastError());
             if (timing) cudaEventRecord(W.ev[1], st);
             if (tracing && k < stats->capacity_levels) {
@@ -688,11 +866,17 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
                 BFS_CUDA_TRY(cudaGetLastError());
             }
             if (timing) cudaEventRecord(W.ev[2], st);
-            if (wbits == 32) expand_wah<uint32_t><<<grid, kNT, 0, st>>>(a);
-            else expand_wah<unsigned long long><<<grid, kNT, 0, st>>>(a);
+            if (wbits == 32) {
+                if (win) expand_wah<uint32_t, true><<<xgrid, kXT, dyn, st>>>(a);
+                else expand_wah<uint32_t, false><<<xgrid, kXT, 0, st>>>(a);
+            } else {
+                if (win) expand_wah<unsigned long long, true><<<xgrid, kXT, dyn, st>>>(a);
+                else expand_wah<unsigned long long, false><<<xgrid, kXT, 0, st>>>(a);
+            }
             BFS_CUDA_TRY(cudaGetLastError());
         }
-        expand_pieces<<<grid, kNT, 0, st>>>(a);
+        if (win) expand_pieces<true><<<xgrid, kXT, dyn, st>>>(a);
+        else expand_pieces<false><<<xgrid, kXT, 0, st>>>(a);
         BFS_CUDA_TRY(cudaGetLastError());
         if (timing) cudaEventRecord(W.ev[3], st);
         reduce_level<<<std::min<int64_t>((W.bm_words + 255) / 256 + 1, sm_count() * 16), kNT, 0, st>>>(
@@ -703,8 +887,14 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         BFS_CUDA_TRY(cudaStreamSynchronize(st));
         const uint64_t* h = W.h_counters;
         if (h[C_ERROR] & 2ull) return set_error(BFS_ERR_INVALID_ARG, "trace capacity exceeded");
-        if (h[C_ERROR]) return set_error(BFS_ERR_CORRUPT, "device invariant check failed (code %llu)",
-                                         (unsigned long long)h[C_ERROR]);
+        if (h[C_ERROR])
+            return set_error(BFS_ERR_CORRUPT,
+                             "device invariant check failed (code %llu) at level %d; slot %lld chunk %llu word %llu "
+                             "value %llx group %llu vertex %llu",
+                             (unsigned long long)h[C_ERROR], k, (long long)h[C_DBG] - 1,
+                             (unsigned long long)h[C_DBG + 1], (unsigned long long)h[C_DBG + 2],
+                             (unsigned long long)h[C_DBG + 3], (unsigned long long)h[C_DBG + 4],
+                             (unsigned long long)h[C_DBG + 5]);
         if (stats) {
             if (stats->levels && k < stats->capacity_levels) {
                 bfs_level_stats& ls = stats->levels[k];

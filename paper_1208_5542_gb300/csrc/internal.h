@@ -86,7 +86,8 @@ enum Counter : int {
     C_WAH_WORDS,         // words of all streams of this level
     C_EXCHANGED,         // set bits carried by the exchange
     C_PIECES,            // pieces of long columns queued for the piece kernel
-    C_NUM
+    C_DBG,               // first failed invariant: 6 slots of context (see bfs_level.cu)
+    C_NUM = C_DBG + 6
 };
 
 // Per-search workspace (owned by the graph, reused by every search).
@@ -100,7 +101,10 @@ struct Workspace {
     int wah_bits = 0;
     int mode = -1;
     DevBuf pi, fa, fb, fsum, xbuf, xcount, chunk_base, units, counters, pieces;
+    DevBuf level_scratch;       // per-level work counters (3 per row)
+    DevBuf row_meta;            // per-row piece bases and capacities
     int64_t piece_cap = 0;      // capacity of `pieces` (Item entries)
+    int64_t win_words = 0;      // shared-memory row window of the expansion (0: none)
     DevBuf tmp_parent, tmp_level;      // for searches with host outputs
     uint64_t* h_counters = nullptr;    // pinned mirror of the counters
     cudaEvent_t ev[8] = {};

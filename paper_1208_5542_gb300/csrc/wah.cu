@@ -43,6 +43,20 @@ __device__ __forceinline__ SlotGeom slot_geom(const EncodeArgs& a, int s) {
     return g;
 }
 
+// True if the frontier-summary bytes q0..q1 (inclusive) are all zero; the
+// summary is padded to whole 32-bit words.
+__device__ __forceinline__ bool fsum_zero(const uint8_t* fsum, int64_t q0, int64_t q1) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(fsum);
+    const int64_t a = q0 >> 2, b = q1 >> 2;
+    for (int64_t i = a; i <= b; ++i) {
+        uint32_t x = __ldcg(w + i);
+        if (i == a) x &= 0xffffffffu << (8 * (q0 & 3));
+        if (i == b) x &= 0xffffffffu >> (8 * (3 - (q1 & 3)));
+        if (x) return false;
+    }
+    return true;
+}
+
 template <typename W>
 __device__ __forceinline__ W load_group(const EncodeArgs& a, const SlotGeom& sg, int64_t g) {
     W x = Wah<W>::group(a.frontier, (uint64_t)(sg.src0 + g * Wah<W>::GB));
@@ -73,24 +87,30 @@ __global__ void __launch_bounds__(kNT) wah_encode_kernel(EncodeArgs a, unsigned 
     int64_t run_start = 0;     // start group of the run holding the group before the tile
     unsigned long long ones = 0;
 
-    for (int64_t tb = 0; tb < G; tb += kTile) {
-        const int64_t tend = (tb + kTile < G) ? tb + kTile : G;
-        // ---- zero skip from the frontier summary ----
+    for (int64_t tb = 0; tb < G;) {
+        int64_t tend = (tb + kTile < G) ? tb + kTile : G;
+        // ---- zero skip from the frontier summary: lane l of warp 0 tests tile
+        // tb + l*kTile; a run of leading all-zero tiles extends the zero fill ----
         if (a.fsum) {
             if (threadIdx.x < 32) {
-                const int64_t lo = sg.src0 + tb * GB, hi = sg.src0 + tend * GB;   // [lo, hi)
-                const int64_t q0 = lo >> 10, q1 = (hi - 1) >> 10;
-                bool any = false;
-                for (int64_t q = q0 + lane_id(); q <= q1; q += 32) any |= (a.fsum[q] != 0);
-                any = __any_sync(0xffffffffu, any);
-                if (threadIdx.x == 0) sm_flag = any ? 1 : 0;
+                const int64_t t0 = tb + (int64_t)lane_id() * kTile;
+                bool zero = false;
+                if (t0 < G) {
+                    const int64_t t1 = (t0 + kTile < G) ? t0 + kTile : G;
+                    zero = fsum_zero(a.fsum, (sg.src0 + t0 * GB) >> 10, (sg.src0 + t1 * GB - 1) >> 10);
+                }
+                const uint32_t zmask = __ballot_sync(0xffffffffu, zero);
+                if (threadIdx.x == 0) sm_flag = __ffs(~zmask) - 1;      // leading zero tiles (0..31)
+                if (threadIdx.x == 0 && zmask == 0xffffffffu) sm_flag = 32;
             }
             __syncthreads();
-            const int any = sm_flag;
+            const int nz = sm_flag;
             __syncthreads();
-            if (!any) {
+            if (nz > 0) {
+                const int64_t skip_end = (tb + (int64_t)nz * kTile < G) ? tb + (int64_t)nz * kTile : G;
                 if (prev_type != G_ZERO) { nw += 1; run_start = tb; prev_type = G_ZERO; }
-                if (tend == G && threadIdx.x == 0) out[nw - 1] = fill_word<W>(G_ZERO, (uint64_t)(G - run_start));
+                if (skip_end == G && threadIdx.x == 0) out[nw - 1] = fill_word<W>(G_ZERO, (uint64_t)(G - run_start));
+                tb = skip_end;
                 continue;
             }
         }
@@ -110,6 +130,11 @@ __global__ void __launch_bounds__(kNT) wah_encode_kernel(EncodeArgs a, unsigned 
                 ty[k] = G_NONE;
             }
         }
+        // a zero run carried into this tile (possibly across skipped tiles) ends
+        // here if the tile opens with another type: write its fill word (when the
+        // run ended in a processed tile the same word was already written there)
+        if (threadIdx.x == 0 && prev_type == G_ZERO && ty[0] != G_ZERO)
+            out[nw - 1] = fill_word<W>(G_ZERO, (uint64_t)(tb - run_start));
         sm_first[threadIdx.x] = (uint8_t)ty[0];
         sm_last[threadIdx.x] = (uint8_t)ty[kK - 1];
         if (threadIdx.x == 0) sm_next_type = (tend < G) ? group_type<W>(load_group<W>(a, sg, tend)) : G_NONE;
@@ -154,6 +179,7 @@ __global__ void __launch_bounds__(kNT) wah_encode_kernel(EncodeArgs a, unsigned 
         prev_type = sm_carry_type;
         run_start = sm_carry_start;
         __syncthreads();
+        tb = tend;
     }
     if (setbits) {
         unsigned long long tot;

@@ -205,3 +205,53 @@ def test_scale20_grid8(mode):
         lv, pa = oracle.bfs(go, int(r))
         parent, level, _ = _run(g, int(r))
         assert (level == lv).all() and (parent == pa).all()
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_ranges_too_long_for_the_shared_window(mode):
+    """Scale 21 on a 2x2 grid: 1M-vertex ranges do not fit the on-chip row
+    window, so the expansion takes its global-memory visiting path."""
+    bfs = _lib()
+    n, src, dst = graphgen.edges(21, 8)
+    go = oracle.csr(n, src, dst)
+    g = bfs.Graph.from_edges(n, src, dst, p=2, mode=mode)
+    for r in graphgen.pick_roots(n, src, dst, 2):
+        lv, pa = oracle.bfs(go, int(r))
+        parent, level, _ = _run(g, int(r))
+        assert (level == lv).all() and (parent == pa).all()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_many_rows(mode):
+    """A 64 x 64 grid on a small graph: many rows for the row-affine work hand-out."""
+    bfs = _lib()
+    n, src, dst = graphgen.edges(13, 16)
+    go = oracle.csr(n, src, dst)
+    g = bfs.Graph.from_edges(n, src, dst, p=64, mode=mode)
+    for r in graphgen.pick_roots(n, src, dst, 3):
+        lv, pa = oracle.bfs(go, int(r))
+        parent, level, _ = _run(g, int(r))
+        assert (level == lv).all() and (parent == pa).all()
+
+
+@pytest.mark.parametrize("gap_tiles", [1, 2, 33, 40])
+def test_zero_tiles_skipped_then_set_bit_at_tile_start(gap_tiles):
+    """The encoder skips all-zero tiles of 1024 groups using the frontier summary.
+    Put the only frontier vertex of level 1 at the first bit of a tile that
+    follows gap_tiles all-zero tiles, and a second one further on, so the zero
+    fill must close exactly at a tile boundary after a skip (and after a run
+    of skips longer than one look-ahead of 32 tiles)."""
+    bfs = _lib()
+    tile_bits = 1024 * 31
+    first = gap_tiles * tile_bits
+    second = first + 3 * tile_bits + 5
+    n = second + tile_bits + 100
+    src = np.array([0, 0, first, second], np.int32)
+    dst = np.array([first, second, n - 1, n - 2], np.int32)
+    go = oracle.csr(n, src, dst)
+    for mode in (1, 2):
+        g = bfs.Graph.from_edges(n, src, dst, p=1, mode=mode)
+        lv, pa, tr = oracle.dist_bfs(go, 1, 0, mode=ORACLE_MODE[mode], trace=True)
+        parent, level, st = _run(g, 0, stats=True, trace_capacity=1 << 16)
+        assert (level == lv).all() and (parent == pa).all()
+        _check_trace(_unpack_trace(st, 32), tr)
