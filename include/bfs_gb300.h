@@ -194,6 +194,46 @@ typedef struct {
 BFS_API bfs_status bfs_run(bfs_graph_t g, int32_t root, int32_t *parent, int32_t *level,
                    bfs_run_stats *stats, void *cuda_stream);
 
+/* Counters of one batched search. */
+typedef struct {
+    int32_t n_levels;            /* levels performed (the deepest search's depth + 1) */
+    int32_t reserved;
+    int64_t edges_scanned;       /* adjacency entries read, all levels */
+} bfs_batch_stats;
+
+/*
+ * Up to 64 breadth-first searches at once, bit-parallel: every vertex holds a
+ * 64-bit lane word per state (frontier, visited, next; bit r = search r), and
+ * one level is the boolean SpMV of Sec. III-A applied to all lanes, sieved by
+ * the directories V_{i,j} (Eq. 4) like the single search.  The whole batch is
+ * one CUDA-graph launch (a conditional WHILE node iterates the level body on
+ * the device).
+ *   roots: n_roots (1..64) vertex ids, host or device; duplicates allowed.
+ *   levels: device, [n_roots][n] int32; levels[r][v] = hop distance of v from
+ *     roots[r], or -1.
+ *   parents: device [n_roots][n] or NULL; parents[r][v] = the smallest
+ *     neighbour u of v with levels[r][u] = levels[r][v] - 1 (roots[r] for the
+ *     root, -1 if unreached).  Computing parents adds one reduction per newly
+ *     reached (vertex, search) pair per candidate edge and is markedly slower.
+ *   stats: NULL or filled after the batch.
+ * Synchronises `cuda_stream` before returning.  The first call on a graph
+ * builds and instantiates the CUDA graph.
+ * Errors: BFS_ERR_INVALID_ARG (n_roots, a root out of range, host output
+ * pointers), BFS_ERR_BUSY, BFS_ERR_CUDA.
+ */
+BFS_API bfs_status bfs_run_batch(bfs_graph_t g, const int32_t *roots, int32_t n_roots, int32_t *levels,
+                                 int32_t *parents, bfs_batch_stats *stats, void *cuda_stream);
+
+/*
+ * Autotune the launch shape of the batched expansion on `g`: time the batch
+ * for every candidate (threads per CTA in {128, 256, 512, 1024} x CTAs per SM
+ * in {1, 2, 4, 8, 16}, at most 2048 threads per SM) on the given roots and
+ * keep the fastest for later bfs_run_batch calls.  `levels` is a device
+ * [n_roots][n] scratch output.  best_threads / best_ctas_per_sm may be NULL.
+ */
+BFS_API bfs_status bfs_batch_autotune(bfs_graph_t g, const int32_t *roots, int32_t n_roots, int32_t *levels,
+                                      int32_t *best_threads, int32_t *best_ctas_per_sm, void *cuda_stream);
+
 /*
  * WAH-encode one bitmap (Sec. IV, Table 3) on the device.
  *   bits: device, bit b of the bitmap = bit b%32 of bits[b/32], nbits >= 0

@@ -181,6 +181,29 @@ class Graph:
                 out_stats.trace_counts = out_stats.trace_counts[: out_stats.n_levels]
         return parent, level, out_stats
 
+    # -------------------------------------------------------------- batch --
+    def run_batch(self, roots, parents: bool = False, levels=None, stream=None):
+        """Up to 64 searches at once; returns ``(levels [k, n], parents [k, n] | None, stats)``."""
+        roots = np.ascontiguousarray(np.asarray(roots, dtype=np.int32))
+        k = len(roots)
+        if levels is None:
+            levels = torch.empty((k, self.n), dtype=torch.int32, device="cuda")
+        par = torch.empty((k, self.n), dtype=torch.int32, device="cuda") if parents else None
+        st = native.BatchStats()
+        check(native.lib().bfs_run_batch(self._h, roots.ctypes.data, k, _ptr(levels),
+                                         _ptr(par) if par is not None else None, ctypes.byref(st),
+                                         _stream_ptr(stream)))
+        return levels, par, {"n_levels": int(st.n_levels), "edges_scanned": int(st.edges_scanned)}
+
+    def batch_autotune(self, roots, stream=None):
+        """Pick the launch shape of the batched expansion for this graph; returns (threads, ctas_per_sm)."""
+        roots = np.ascontiguousarray(np.asarray(roots, dtype=np.int32))
+        scratch = torch.empty((len(roots), self.n), dtype=torch.int32, device="cuda")
+        t, c = ctypes.c_int32(), ctypes.c_int32()
+        check(native.lib().bfs_batch_autotune(self._h, roots.ctypes.data, len(roots), _ptr(scratch),
+                                              ctypes.byref(t), ctypes.byref(c), _stream_ptr(stream)))
+        return int(t.value), int(c.value)
+
 
 def wah_encode(bits: torch.Tensor, nbits: int, word_bits: int = 32, stream=None) -> torch.Tensor:
     """Encode the first ``nbits`` bits of ``bits`` (int32 CUDA words, bit b = bit b%32 of word b//32).

@@ -515,6 +515,7 @@ bfs_status bfs_graph_destroy(bfs_graph_t g) {
     cudaGetDevice(&cur);
     cudaSetDevice(g->device);
     cudaDeviceSynchronize();
+    free_msbfs(g);
     free_workspace(g);
     delete g;
     cudaSetDevice(cur);

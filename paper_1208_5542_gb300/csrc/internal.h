@@ -13,6 +13,8 @@
 
 #include "bfs_gb300.h"
 
+struct bfs_graph;
+
 namespace bfsgb {
 
 // ---------------------------------------------------------------- errors --
@@ -111,6 +113,9 @@ struct Workspace {
     bool events = false;
 };
 
+struct MsContext;    // batched search state (msbfs.cu)
+void free_msbfs(bfs_graph* g);
+
 }  // namespace bfsgb
 
 struct bfs_graph {
@@ -122,6 +127,7 @@ struct bfs_graph {
     int device = 0;
     std::atomic<int> busy{0};
     std::mutex mu;
+    bfsgb::MsContext* ms = nullptr;
 };
 
 namespace bfsgb {

@@ -44,6 +44,10 @@ class LevelStats(ctypes.Structure):
                 ("ms_traversing", ctypes.c_float), ("ms_reducing", ctypes.c_float)]
 
 
+class BatchStats(ctypes.Structure):
+    _fields_ = [("n_levels", i32), ("reserved", i32), ("edges_scanned", i64)]
+
+
 class RunStats(ctypes.Structure):
     _fields_ = [("capacity_levels", i32), ("n_levels", i32), ("timing", i32), ("reserved", i32),
                 ("levels", P(LevelStats)), ("trace_words", vp), ("trace_capacity", i64),
@@ -62,6 +66,8 @@ _SIGS = {
     "bfs_graph_set_mode": (ctypes.c_int, [vp, i32, i32]),
     "bfs_graph_directory": (ctypes.c_int, [vp, i32, i32, vp, vp]),
     "bfs_run": (ctypes.c_int, [vp, i32, vp, vp, P(RunStats), vp]),
+    "bfs_run_batch": (ctypes.c_int, [vp, vp, i32, vp, vp, P(BatchStats), vp]),
+    "bfs_batch_autotune": (ctypes.c_int, [vp, vp, i32, vp, P(i32), P(i32), vp]),
     "bfs_wah_encode": (ctypes.c_int, [vp, i64, i32, vp, i64, vp, vp]),
     "bfs_wah_decode": (ctypes.c_int, [vp, i64, i64, i32, vp, vp]),
     "bfs_wah_decode_static": (ctypes.c_int, [vp, i64, i64, i32, vp, vp]),
