@@ -44,6 +44,7 @@ extern "C" {
 #endif
 
 typedef struct bfs_graph *bfs_graph_t;
+typedef struct bfs_server *bfs_server_t;
 
 typedef enum {
     BFS_OK = 0,
@@ -233,6 +234,45 @@ BFS_API bfs_status bfs_run_batch(bfs_graph_t g, const int32_t *roots, int32_t n_
  */
 BFS_API bfs_status bfs_batch_autotune(bfs_graph_t g, const int32_t *roots, int32_t n_roots, int32_t *levels,
                                       int32_t *best_threads, int32_t *best_ctas_per_sm, void *cuda_stream);
+
+/*
+ * Query server with continuous batching (no counterpart in the paper, which
+ * runs one search at a time): graphs stay resident with up to 64 lanes of the
+ * batched search each; a server thread runs one level of every running lane
+ * per iteration, each graph on its own stream (their work overlaps on the
+ * GPU), admits queued queries into free lanes at every iteration boundary and
+ * retires lanes whose frontier emptied.  Every result is the level vector of
+ * a single search from the query's root, the same as bfs_run alone.
+ * Graphs are admitted against `hbm_budget_bytes` by footprint (layout + lane
+ * state + level rows; the lane count is halved until it fits); results not
+ * yet collected count against the budget and hold back new admissions.
+ * All waits are bounded.  Thread-safe.
+ */
+typedef struct {
+    int64_t submitted, completed, rejected, queued;
+    int64_t iterations;          /* level iterations run, all graphs */
+    int32_t peak_lanes;          /* most lanes running at once, all graphs */
+    int32_t graphs;
+    int64_t hbm_used_bytes;      /* resident graphs + results awaiting collection */
+    double p50_us, p99_us, max_us;   /* latency submit -> result ready */
+} bfs_server_stats_t;
+
+/* max_lanes in [1, 64] per graph. */
+BFS_API bfs_status bfs_server_create(int64_t hbm_budget_bytes, int32_t max_lanes, bfs_server_t *out);
+/* Make `g` resident; the server holds it (BFS_ERR_BUSY for other calls on it)
+ * until bfs_server_destroy.  BFS_ERR_OUT_OF_MEMORY if it does not fit. */
+BFS_API bfs_status bfs_server_add_graph(bfs_server_t s, bfs_graph_t g, int32_t *graph_id);
+/* Queue a query; BFS_ERR_BUSY when the queue is full, BFS_ERR_NOT_FOUND for an unknown graph. */
+BFS_API bfs_status bfs_server_submit(bfs_server_t s, int32_t graph_id, int32_t root, int64_t *ticket);
+BFS_API bfs_status bfs_server_poll(bfs_server_t s, int64_t ticket, int32_t *done);
+/* Wait at most timeout_us for the query (BFS_ERR_TIMEOUT otherwise), copy its
+ * level vector (n int32) to `level` (host or device; may be NULL) and release
+ * it.  `parent` must be NULL: the server returns levels only. */
+BFS_API bfs_status bfs_server_wait(bfs_server_t s, int64_t ticket, int64_t timeout_us, int32_t *level,
+                                   int32_t *parent);
+BFS_API bfs_status bfs_server_stats(bfs_server_t s, bfs_server_stats_t *stats);
+/* Stop the server thread, drop uncollected results, release the graphs. */
+BFS_API bfs_status bfs_server_destroy(bfs_server_t s);
 
 /*
  * WAH-encode one bitmap (Sec. IV, Table 3) on the device.

@@ -228,3 +228,52 @@ def wah_decode(words: torch.Tensor, nbits: int, word_bits: int = 32, stream=None
     check(native.lib().bfs_wah_decode(_ptr(words) if words.numel() else None, int(words.numel()), int(nbits),
                                       int(word_bits), _ptr(out), _stream_ptr(stream)))
     return out[: (nbits + 31) // 32]
+
+
+class Server:
+    """Continuous-batching query server over resident graphs (``bfs_server_*``)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_lanes: int = 64):
+        h = ctypes.c_void_p()
+        check(native.lib().bfs_server_create(int(hbm_budget_bytes), int(max_lanes), ctypes.byref(h)))
+        self._h = h
+        self._n = {}
+
+    def add_graph(self, graph: Graph) -> int:
+        gid = ctypes.c_int32()
+        check(native.lib().bfs_server_add_graph(self._h, graph.handle, ctypes.byref(gid)))
+        self._n[int(gid.value)] = graph.n
+        return int(gid.value)
+
+    def submit(self, graph_id: int, root: int) -> int:
+        t = ctypes.c_int64()
+        check(native.lib().bfs_server_submit(self._h, int(graph_id), int(root), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int32()
+        check(native.lib().bfs_server_poll(self._h, int(ticket), ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int, n: int, timeout_s: float = 30.0, out=None):
+        """Level vector (int32 CUDA tensor of length n, or ``out``) of a finished query."""
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, device="cuda")
+        check(native.lib().bfs_server_wait(self._h, int(ticket), int(timeout_s * 1e6), _ptr(out), None))
+        return out
+
+    def stats(self) -> dict:
+        st = native.ServerStats()
+        check(native.lib().bfs_server_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in native.ServerStats._fields_}
+
+    def close(self):
+        if self._h and self._h.value:
+            check(native.lib().bfs_server_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

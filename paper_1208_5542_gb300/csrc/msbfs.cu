@@ -67,6 +67,9 @@ struct MsState {
     unsigned long long piece_next;
     unsigned long long edges;        // entries scanned (all levels)
     unsigned long long levels_done;  // levels performed
+    // continuous batching (server): lane r's level of v is (iteration + 1) - lane_start[r]
+    int32_t lane_start[64];
+    unsigned long long alive;        // lanes that reached a new vertex in this iteration
 };
 
 __device__ __forceinline__ int64_t ms_range_begin(const MsState& s, int64_t b) {
@@ -76,6 +79,8 @@ __device__ __forceinline__ int64_t ms_range_begin(const MsState& s, int64_t b) {
 
 // ------------------------------------------------------------------ init --
 __global__ void ms_reset(MsState* S) {
+    for (int r = 0; r < 64; ++r) S->lane_start[r] = 0;
+    S->alive = 0;
     S->cur = 0;
     S->level = 0;
     S->act_count[0] = 0;
@@ -280,13 +285,17 @@ __global__ void __launch_bounds__(kMT) ms_reduce(MsState* S) {
                     while (m) {
                         const int r = __ffsll((long long)m) - 1;
                         m &= m - 1;
-                        s.levels[(int64_t)r * s.n + v] = lv;
+                        s.levels[(int64_t)r * s.n + v] = lv - s.lane_start[r];
                     }
                 }
             }
             fn[v] = nv;
         }
         const uint32_t ball = __ballot_sync(0xffffffffu, nv != 0ull);
+        unsigned long long any = nv;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) any |= __shfl_xor_sync(0xffffffffu, any, d);
+        if (any && lane_id() == 0) atomicOr(&s.alive, any);
         if (ball) {
             unsigned long long base = 0;
             if (lane_id() == 0) base = atomicAdd(&s.act_count[nxt_i], (unsigned long long)__popc(ball));
@@ -310,6 +319,59 @@ __global__ void ms_finalize(MsState* S, cudaGraphConditionalHandle handle) {
     s.piece_next = 0;
     cudaGraphSetConditional(handle, (cnt > 0 && s.level < s.max_levels) ? 1u : 0u);
 }
+
+// One server iteration ends: switch buffers, advance the iteration.
+__global__ void ms_step_end(MsState* S) {
+    MsState& s = *S;
+    const int nxt_i = s.cur ^ 1;
+    s.act_count[s.cur] = 0;
+    s.cur = nxt_i;
+    s.level += 1;
+    s.levels_done += 1;
+    s.act_next = 0;
+    s.piece_count = 0;
+    s.piece_next = 0;
+}
+
+// Admission, phase A: lanes in `mask` start over -- clear their bits in every
+// lane word and their level rows.
+__global__ void ms_admit_clear(MsState* S, unsigned long long mask, const int32_t* lanes, int nlanes) {
+    MsState& s = *S;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const unsigned long long keep = ~mask;
+    for (int64_t v = tid; v < s.n; v += stride) {
+        if (s.vis[v] & mask) s.vis[v] &= keep;
+        if (s.f[s.cur][v] & mask) s.f[s.cur][v] &= keep;
+        if (s.nxt[v] & mask) s.nxt[v] &= keep;
+    }
+    const int64_t total = (int64_t)nlanes * s.n;
+    for (int64_t x = tid; x < total; x += stride) {
+        const int r = lanes[x / s.n];
+        s.levels[(int64_t)r * s.n + x % s.n] = -1;
+    }
+    if (tid == 0) s.alive = 0;
+}
+
+// Admission, phase B: lane lanes[q] starts from roots[q] at this iteration.
+__global__ void ms_admit_roots(MsState* S, const int32_t* lanes, const int32_t* roots, int nlanes) {
+    MsState& s = *S;
+    const int q = threadIdx.x;
+    if (q >= nlanes) return;
+    const int r = lanes[q];
+    const int32_t v = roots[q];
+    const unsigned long long bit = 1ull << r;
+    atomicOr(s.vis + v, bit);
+    const unsigned long long old = atomicOr(s.f[s.cur] + v, bit);
+    s.levels[(int64_t)r * s.n + v] = 0;
+    s.lane_start[r] = s.level;
+    if (old == 0ull) {
+        const unsigned long long pos = atomicAdd(&s.act_count[s.cur], 1ull);
+        s.act[s.cur][pos] = v;
+    }
+}
+
+__global__ void ms_clear_alive(MsState* S) { S->alive = 0; }
 
 int ms_sm_count() {
     int dev = 0, v = 0;
@@ -573,3 +635,394 @@ extern "C" bfs_status bfs_batch_autotune(bfs_graph_t g, const int32_t* roots, in
     return BFS_OK;
 }
 
+
+// ===================================================================== server
+// Continuous batching over resident graphs.  Every graph keeps up to 64 lanes
+// of the bit-parallel search resident on the device; a server thread runs
+// iterations (one BFS level of every running lane) on each graph's own stream,
+// so the graphs' work overlaps on the GPU.  At every iteration boundary queued
+// requests are admitted into free lanes (a lane admitted at iteration s reports
+// level = iteration + 1 - s), and lanes whose frontier emptied are retired:
+// their level row is copied to a result buffer and the request completes.
+// Graphs are admitted against an HBM budget by their footprint (layout, lane
+// state and level rows); results awaiting collection count against it too, and
+// admission of new requests pauses while they would not fit.
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+namespace bfsgb {
+namespace {
+
+struct ServeGraph {
+    bfs_graph* g = nullptr;
+    int lanes = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf levels;                   // [lanes][n]
+    DevBuf admit;                    // lanes[64], roots[64]
+    int32_t* h_admit = nullptr;      // pinned staging of `admit`
+    unsigned long long* h_alive = nullptr;   // pinned copy of the alive mask
+    cudaGraphExec_t step = nullptr;  // expand, pieces, reduce, step end
+    cudaGraph_t step_graph = nullptr;
+    int64_t lane_ticket[64];
+    unsigned long long running = 0;
+    std::deque<int64_t> pending;
+    int64_t footprint = 0;
+    int64_t iterations = 0;
+};
+
+struct Request {
+    int32_t graph = 0;
+    int32_t root = 0;
+    int state = 0;                   // 0 queued, 1 running, 2 done
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    int32_t* result = nullptr;       // device [n] once done
+};
+
+}  // namespace
+}  // namespace bfsgb
+
+struct bfs_server {
+    int64_t budget = 0;
+    int64_t used = 0;                // resident graphs
+    int64_t results_bytes = 0;       // results awaiting collection
+    int max_lanes = 64;
+    std::vector<bfsgb::ServeGraph*> graphs;
+    std::unordered_map<int64_t, bfsgb::Request> req;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    bool failed = false;
+    char fail_msg[256] = {0};
+    int64_t next_ticket = 1;
+    int64_t submitted = 0, completed = 0, rejected = 0, queued = 0;
+    int64_t iterations = 0;
+    int peak_lanes = 0;
+    std::vector<double> lat_us;
+    std::chrono::steady_clock::time_point t0;
+    int device = 0;
+};
+
+namespace bfsgb {
+namespace {
+
+constexpr int64_t kMaxQueued = 1 << 20;
+
+bfs_status build_step_graph(ServeGraph* sg) {
+    MsContext* c = sg->g->ms;
+    MsState* S = c->state.as<MsState>();
+    const int sms = ms_sm_count();
+    BFS_CUDA_TRY(cudaStreamBeginCapture(sg->stream, cudaStreamCaptureModeThreadLocal));
+    ms_expand<<<sms * c->expand_ctas_per_sm, c->expand_threads, 0, sg->stream>>>(S);
+    ms_pieces<<<sms * 4, kMT, 0, sg->stream>>>(S);
+    ms_reduce<<<sms * 8, kMT, 0, sg->stream>>>(S);
+    ms_step_end<<<1, 1, 0, sg->stream>>>(S);
+    cudaGraph_t graph = nullptr;
+    BFS_CUDA_TRY(cudaStreamEndCapture(sg->stream, &graph));
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_error(e, "cudaGraphInstantiate(step)", __FILE__, __LINE__); }
+    sg->step_graph = graph;
+    sg->step = exec;
+    return BFS_OK;
+}
+
+void release_graph(ServeGraph* sg) {
+    if (sg->stream) cudaStreamSynchronize(sg->stream);
+    if (sg->step) cudaGraphExecDestroy(sg->step);
+    if (sg->step_graph) cudaGraphDestroy(sg->step_graph);
+    if (sg->h_admit) cudaFreeHost(sg->h_admit);
+    if (sg->h_alive) cudaFreeHost(sg->h_alive);
+    if (sg->stream) cudaStreamDestroy(sg->stream);
+    sg->levels.release();
+    sg->admit.release();
+    if (sg->g) sg->g->busy.store(0);
+}
+
+void fail(bfs_server* s, const char* what) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->failed = true;
+    snprintf(s->fail_msg, sizeof(s->fail_msg), "%s", what);
+    s->cv_done.notify_all();
+}
+
+// One pass of the server loop: admit, launch one iteration per graph, retire.
+bool serve_pass(bfs_server* s) {
+    struct Launch { ServeGraph* sg; unsigned long long before; };
+    std::vector<Launch> launched;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        for (ServeGraph* sg : s->graphs) {
+            // admission into free lanes, while the results would fit in the budget
+            int nadm = 0;
+            unsigned long long mask = 0;
+            const int64_t row = 4 * sg->g->L.n;
+            for (int r = 0; r < sg->lanes && !sg->pending.empty(); ++r) {
+                if (sg->running & (1ull << r)) continue;
+                if (s->used + s->results_bytes + row > s->budget) break;     // wait for results to be collected
+                const int64_t t = sg->pending.front();
+                sg->pending.pop_front();
+                --s->queued;
+                Request& q = s->req[t];
+                q.state = 1;
+                sg->lane_ticket[r] = t;
+                sg->running |= 1ull << r;
+                sg->h_admit[nadm] = r;
+                sg->h_admit[64 + nadm] = q.root;
+                mask |= 1ull << r;
+                ++nadm;
+            }
+            if (!sg->running) continue;
+            MsState* S = sg->g->ms->state.as<MsState>();
+            if (nadm) {
+                int32_t* d = sg->admit.as<int32_t>();
+                if (cudaMemcpyAsync(d, sg->h_admit, sizeof(int32_t) * 128, cudaMemcpyHostToDevice, sg->stream) != cudaSuccess) {
+                    lk.unlock(); fail(s, "admission copy failed"); return false;
+                }
+                ms_admit_clear<<<ms_sm_count() * 4, kMT, 0, sg->stream>>>(S, mask, d, nadm);
+                ms_admit_roots<<<1, 64, 0, sg->stream>>>(S, d, d + 64, nadm);
+            } else {
+                ms_clear_alive<<<1, 1, 0, sg->stream>>>(S);
+            }
+            if (cudaGraphLaunch(sg->step, sg->stream) != cudaSuccess) {
+                lk.unlock(); fail(s, "iteration launch failed"); return false;
+            }
+            cudaMemcpyAsync(sg->h_alive, reinterpret_cast<char*>(S) + offsetof(MsState, alive),
+                            sizeof(unsigned long long), cudaMemcpyDeviceToHost, sg->stream);
+            launched.push_back({sg, sg->running});
+            int lanes_now = 0;
+            for (ServeGraph* x : s->graphs) lanes_now += __builtin_popcountll(x->running);
+            if (lanes_now > s->peak_lanes) s->peak_lanes = lanes_now;
+        }
+    }
+    if (launched.empty()) return false;
+    for (Launch& L : launched) {
+        ServeGraph* sg = L.sg;
+        if (cudaStreamSynchronize(sg->stream) != cudaSuccess) { fail(s, "iteration failed on the device"); return false; }
+        const unsigned long long done = L.before & ~*sg->h_alive;
+        const int64_t n = sg->g->L.n;
+        std::vector<std::pair<int64_t, int32_t*>> fin;
+        for (int r = 0; r < sg->lanes; ++r) {
+            if (!(done & (1ull << r))) continue;
+            void* buf = nullptr;
+            if (cudaMallocAsync(&buf, sizeof(int32_t) * n, sg->stream) != cudaSuccess) { fail(s, "result allocation failed"); return false; }
+            cudaMemcpyAsync(buf, sg->levels.as<int32_t>() + (int64_t)r * n, sizeof(int32_t) * n,
+                            cudaMemcpyDeviceToDevice, sg->stream);
+            fin.push_back({sg->lane_ticket[r], static_cast<int32_t*>(buf)});
+            sg->lane_ticket[r] = -1;
+        }
+        if (!fin.empty() && cudaStreamSynchronize(sg->stream) != cudaSuccess) { fail(s, "result copy failed"); return false; }
+        std::lock_guard<std::mutex> lk(s->mu);
+        sg->running &= ~done;
+        ++sg->iterations;
+        ++s->iterations;
+        const auto now = std::chrono::steady_clock::now();
+        for (auto& f : fin) {
+            Request& q = s->req[f.first];
+            q.state = 2;
+            q.result = f.second;
+            q.t_done = now;
+            s->results_bytes += sizeof(int32_t) * n;
+            ++s->completed;
+            s->lat_us.push_back(std::chrono::duration<double, std::micro>(now - q.t_submit).count());
+        }
+        if (!fin.empty()) s->cv_done.notify_all();
+    }
+    return true;
+}
+
+void serve_loop(bfs_server* s) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (s->stop || s->failed) return;
+            bool work = false;
+            for (ServeGraph* sg : s->graphs) work |= (sg->running != 0) || !sg->pending.empty();
+            if (!work) s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
+            if (s->stop) return;
+        }
+        serve_pass(s);
+    }
+}
+
+}  // namespace
+}  // namespace bfsgb
+
+extern "C" {
+
+bfs_status bfs_server_create(int64_t hbm_budget_bytes, int32_t max_lanes, bfs_server_t* out) {
+    if (!out || hbm_budget_bytes <= 0 || max_lanes < 1 || max_lanes > 64)
+        return set_error(BFS_ERR_INVALID_ARG, "bad server arguments (budget > 0, 1 <= max_lanes <= 64)");
+    bfs_server* s = new (std::nothrow) bfs_server();
+    if (!s) return set_error(BFS_ERR_OUT_OF_MEMORY, "host allocation");
+    s->budget = hbm_budget_bytes;
+    s->max_lanes = max_lanes;
+    s->t0 = std::chrono::steady_clock::now();
+    cudaGetDevice(&s->device);
+    s->worker = std::thread(serve_loop, s);
+    *out = s;
+    return BFS_OK;
+}
+
+bfs_status bfs_server_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id) {
+    if (!s || !g || !graph_id) return set_error(BFS_ERR_INVALID_ARG, "NULL argument");
+    int expect = 0;
+    if (!g->busy.compare_exchange_strong(expect, 1)) return set_error(BFS_ERR_BUSY, "graph is in use");
+    ServeGraph* sg = new (std::nothrow) ServeGraph();
+    if (!sg) { g->busy.store(0); return set_error(BFS_ERR_OUT_OF_MEMORY, "host allocation"); }
+    sg->g = g;
+    for (auto& t : sg->lane_ticket) t = -1;
+    const int64_t n = g->L.n;
+    int64_t layout = 0;
+    bfs_graph_footprint(g, &layout);
+    const int64_t lane_state = 32 * n + 8 * n + (int64_t)sizeof(Item) * (g->L.nnz / kMsPiece + g->L.nnz / kMsHub + 16);
+    int lanes = s->max_lanes;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        while (lanes > 0 && s->used + layout + lane_state + 4 * n * (int64_t)lanes > s->budget) lanes /= 2;
+    }
+    if (lanes == 0) {
+        delete sg;
+        g->busy.store(0);
+        return set_error(BFS_ERR_OUT_OF_MEMORY, "graph does not fit the server's HBM budget");
+    }
+    sg->lanes = lanes;
+    sg->footprint = layout + lane_state + 4 * n * (int64_t)lanes;
+    bfs_status rc = ms_ensure(g);
+    if (rc == BFS_OK) rc = sg->levels.alloc(sizeof(int32_t) * n * lanes);
+    if (rc == BFS_OK) rc = sg->admit.alloc(sizeof(int32_t) * 128);
+    if (rc == BFS_OK && cudaMallocHost(reinterpret_cast<void**>(&sg->h_admit), sizeof(int32_t) * 128) != cudaSuccess)
+        rc = set_error(BFS_ERR_OUT_OF_MEMORY, "pinned host allocation");
+    if (rc == BFS_OK && cudaMallocHost(reinterpret_cast<void**>(&sg->h_alive), sizeof(unsigned long long)) != cudaSuccess)
+        rc = set_error(BFS_ERR_OUT_OF_MEMORY, "pinned host allocation");
+    if (rc == BFS_OK && cudaStreamCreateWithFlags(&sg->stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = set_error(BFS_ERR_CUDA, "stream creation failed");
+    if (rc == BFS_OK) {
+        MsState* S = g->ms->state.as<MsState>();
+        MsCall call{g->ms->roots.as<int32_t>(), lanes, 0x7fffffff, sg->levels.as<int32_t>(), nullptr};
+        if (cudaMemcpyAsync(reinterpret_cast<char*>(S) + offsetof(MsState, roots), &call, sizeof(call),
+                            cudaMemcpyHostToDevice, sg->stream) != cudaSuccess)
+            rc = set_error(BFS_ERR_CUDA, "state copy failed");
+        if (rc == BFS_OK) {
+            ms_reset<<<1, 1, 0, sg->stream>>>(S);
+            ms_clear<<<ms_sm_count() * 8, kMT, 0, sg->stream>>>(S);
+            if (cudaStreamSynchronize(sg->stream) != cudaSuccess) rc = set_error(BFS_ERR_CUDA, "lane state initialisation failed");
+        }
+    }
+    if (rc == BFS_OK) rc = build_step_graph(sg);
+    if (rc != BFS_OK) {
+        release_graph(sg);
+        delete sg;
+        return rc;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->used += sg->footprint;
+    s->graphs.push_back(sg);
+    *graph_id = (int32_t)s->graphs.size() - 1;
+    return BFS_OK;
+}
+
+bfs_status bfs_server_submit(bfs_server_t s, int32_t graph_id, int32_t root, int64_t* ticket) {
+    if (!s || !ticket) return set_error(BFS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->failed) return set_error(BFS_ERR_CUDA, "server failed: %s", s->fail_msg);
+    if (graph_id < 0 || graph_id >= (int32_t)s->graphs.size()) return set_error(BFS_ERR_NOT_FOUND, "unknown graph id %d", graph_id);
+    ServeGraph* sg = s->graphs[graph_id];
+    if (root < 0 || (int64_t)root >= sg->g->L.n) return set_error(BFS_ERR_INVALID_ARG, "root %d outside [0, %lld)", root, (long long)sg->g->L.n);
+    if (s->queued >= kMaxQueued) { ++s->rejected; return set_error(BFS_ERR_BUSY, "server queue is full"); }
+    const int64_t t = s->next_ticket++;
+    Request q;
+    q.graph = graph_id;
+    q.root = root;
+    q.t_submit = std::chrono::steady_clock::now();
+    s->req.emplace(t, q);
+    sg->pending.push_back(t);
+    ++s->queued;
+    ++s->submitted;
+    *ticket = t;
+    s->cv_work.notify_one();
+    return BFS_OK;
+}
+
+bfs_status bfs_server_poll(bfs_server_t s, int64_t ticket, int32_t* done) {
+    if (!s || !done) return set_error(BFS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->req.find(ticket);
+    if (it == s->req.end()) return set_error(BFS_ERR_NOT_FOUND, "unknown ticket %lld", (long long)ticket);
+    *done = it->second.state == 2;
+    return BFS_OK;
+}
+
+bfs_status bfs_server_wait(bfs_server_t s, int64_t ticket, int64_t timeout_us, int32_t* level, int32_t* parent) {
+    if (!s) return set_error(BFS_ERR_INVALID_ARG, "NULL server");
+    if (parent) return set_error(BFS_ERR_INVALID_ARG, "the server returns levels only (parent must be NULL)");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->req.find(ticket);
+    if (it == s->req.end()) return set_error(BFS_ERR_NOT_FOUND, "unknown ticket %lld", (long long)ticket);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
+    while (s->req[ticket].state != 2 && !s->failed) {
+        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && s->req[ticket].state != 2)
+            return set_error(BFS_ERR_TIMEOUT, "request %lld not finished", (long long)ticket);
+    }
+    if (s->failed) return set_error(BFS_ERR_CUDA, "server failed: %s", s->fail_msg);
+    Request q = s->req[ticket];
+    s->req.erase(ticket);
+    ServeGraph* sg = s->graphs[q.graph];
+    const int64_t n = sg->g->L.n;
+    s->results_bytes -= sizeof(int32_t) * n;
+    lk.unlock();
+    bfs_status rc = BFS_OK;
+    if (level) {
+        cudaError_t e = cudaMemcpy(level, q.result, sizeof(int32_t) * n, cudaMemcpyDefault);
+        if (e != cudaSuccess) rc = cuda_error(e, "result copy", __FILE__, __LINE__);
+    }
+    cudaFree(q.result);
+    s->cv_work.notify_one();
+    return rc;
+}
+
+bfs_status bfs_server_stats(bfs_server_t s, bfs_server_stats_t* st) {
+    if (!s || !st) return set_error(BFS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(st, 0, sizeof(*st));
+    st->submitted = s->submitted;
+    st->completed = s->completed;
+    st->rejected = s->rejected;
+    st->queued = s->queued;
+    st->iterations = s->iterations;
+    st->peak_lanes = s->peak_lanes;
+    st->graphs = (int32_t)s->graphs.size();
+    st->hbm_used_bytes = s->used + s->results_bytes;
+    std::vector<double> v = s->lat_us;
+    if (!v.empty()) {
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) { return v[std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1) + 0.5))]; };
+        st->p50_us = pct(0.50);
+        st->p99_us = pct(0.99);
+        st->max_us = v.back();
+    }
+    return BFS_OK;
+}
+
+bfs_status bfs_server_destroy(bfs_server_t s) {
+    if (!s) return BFS_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (auto& kv : s->req)
+        if (kv.second.result) cudaFree(kv.second.result);
+    for (ServeGraph* sg : s->graphs) {
+        release_graph(sg);
+        delete sg;
+    }
+    delete s;
+    return BFS_OK;
+}
+
+}  // extern "C"

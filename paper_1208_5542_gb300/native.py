@@ -48,6 +48,12 @@ class BatchStats(ctypes.Structure):
     _fields_ = [("n_levels", i32), ("reserved", i32), ("edges_scanned", i64)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", i64), ("completed", i64), ("rejected", i64), ("queued", i64), ("iterations", i64),
+                ("peak_lanes", i32), ("graphs", i32), ("hbm_used_bytes", i64), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double)]
+
+
 class RunStats(ctypes.Structure):
     _fields_ = [("capacity_levels", i32), ("n_levels", i32), ("timing", i32), ("reserved", i32),
                 ("levels", P(LevelStats)), ("trace_words", vp), ("trace_capacity", i64),
@@ -68,6 +74,13 @@ _SIGS = {
     "bfs_run": (ctypes.c_int, [vp, i32, vp, vp, P(RunStats), vp]),
     "bfs_run_batch": (ctypes.c_int, [vp, vp, i32, vp, vp, P(BatchStats), vp]),
     "bfs_batch_autotune": (ctypes.c_int, [vp, vp, i32, vp, P(i32), P(i32), vp]),
+    "bfs_server_create": (ctypes.c_int, [i64, i32, P(vp)]),
+    "bfs_server_add_graph": (ctypes.c_int, [vp, vp, P(i32)]),
+    "bfs_server_submit": (ctypes.c_int, [vp, i32, i32, P(i64)]),
+    "bfs_server_poll": (ctypes.c_int, [vp, i64, P(i32)]),
+    "bfs_server_wait": (ctypes.c_int, [vp, i64, i64, vp, vp]),
+    "bfs_server_stats": (ctypes.c_int, [vp, P(ServerStats)]),
+    "bfs_server_destroy": (ctypes.c_int, [vp]),
     "bfs_wah_encode": (ctypes.c_int, [vp, i64, i32, vp, i64, vp, vp]),
     "bfs_wah_decode": (ctypes.c_int, [vp, i64, i64, i32, vp, vp]),
     "bfs_wah_decode_static": (ctypes.c_int, [vp, i64, i64, i32, vp, vp]),
