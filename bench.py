@@ -36,6 +36,7 @@ WORKLOADS = {
     "s12": (12, 16, 2, 0, 16, "kronecker-s12-ef16-grid2x2"),
     "s20": (20, 16, 8, 0, 64, "kronecker-s20-ef16-grid8x8"),
     "s22": (22, 16, 8, 0, 64, "kronecker-s22-ef16-grid8x8"),
+    "s24": (24, 16, 16, 0, 64, "kronecker-s24-ef16-grid16x16"),
     "s26": (26, 16, 16, 0, 64, "kronecker-s26-ef16-grid16x16"),
     "s26er": (26, 16, 16, 1, 64, "erdos-renyi-s26-ef16-grid16x16"),
 }
@@ -51,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="s22", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="s26", choices=sorted(WORKLOADS))
     ap.add_argument("--mode", type=int, default=2, help="0 plain, 1 compress, 2 compress+sieve")
     ap.add_argument("--wah-bits", type=int, default=32)
     ap.add_argument("--roots", type=int, default=0, help="override the number of roots")
@@ -141,6 +142,21 @@ class ClockSampler:
                         reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def job_value(inv, ms_step, n_roots, dist=None, device=None):
+    """Whole-job harmonic-mean GTEPS over replicas: the roots searched by all
+    ranks divided by the slowest rank's sum of t_r / m_r (every rank searches
+    n_roots roots of its own replica; no data-path collective, only this
+    timing reduction).  Returns (GTEPS, the slowest rank's ms per step)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        x = torch.tensor([inv, ms_step], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        inv, ms_step = float(x[0]), float(x[1])
+    return ((n_roots * world / inv) / 1e9 if inv > 0 else 0.0), ms_step
 
 
 def hm_gteps(m, t):
@@ -238,11 +254,19 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     if args.profile_run:
+        # one untimed search per mode from the first root, with the per-level
+        # algorithmic bytes of the expansion (to set against ncu's DRAM bytes)
+        out = {"profile_run": True, "workload": desc, "root": int(roots[0]), "kernel_hash": kernel_hash()}
         for mode in (args.mode, 0):
             g.set_mode(mode, args.wah_bits)
-            g.run(int(roots[0]), parent, level)
+            _, _, st = g.run(int(roots[0]), parent, level, stats=True)
+            alg = []
+            for k, ls in enumerate(st.levels):
+                nxt = st.levels[k + 1]["frontier_vertices"] if k + 1 < len(st.levels) else 0
+                alg.append(4 * ls["edges_scanned"] + 12 * ls["column_hits"] + ls["wah_bytes"] + 4 * nxt)
+            out[MODE_NAMES[mode]] = {"levels": st.n_levels, "expand_algorithmic_bytes": alg}
         torch.cuda.synchronize()
-        print(json.dumps({"profile_run": True, "workload": desc}))
+        print(json.dumps(out))
         return
 
     def step(record=False):
@@ -291,13 +315,7 @@ def main():
 
     # whole-job value: roots of all ranks over the slowest rank's sum of t_r/m_r
     inv = sum(t / m for t, m in zip(t_cs, m_r) if m > 0)
-    ms_step = 1e3 * sum(t_cs)
-    if world > 1:
-        x = torch.tensor([inv, ms_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        inv, ms_step = float(x[0]), float(x[1])
-    total_roots = len(roots) * world
-    value = (total_roots / inv) / 1e9 if inv > 0 else 0.0
+    value, ms_step = job_value(inv, 1e3 * sum(t_cs), len(roots), dist if world > 1 else None, dev)
 
     # roofline of the expansion kernel (algorithmic bytes per launch / event time per launch)
     ex_bytes = ex_ms = 0.0

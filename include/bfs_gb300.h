@@ -73,9 +73,11 @@ typedef struct {
     int32_t autotune;        /* reserved, 0 */
     int32_t debug_checks;    /* 1: kernels verify internal invariants and report
                                 BFS_ERR_CORRUPT instead of continuing */
+    int32_t row_exchange;    /* 1: compressed row exchange (see bfs_graph_set_row_exchange) */
 } bfs_options;
 
-/* Fill `opt` with the defaults: 1 x 1 grid, BFS_MODE_COMPRESS_SIEVE, 32-bit words. */
+/* Fill `opt` with the defaults: 1 x 1 grid, BFS_MODE_COMPRESS_SIEVE, 32-bit words,
+ * row exchange off. */
 BFS_API void bfs_options_default(bfs_options *opt);
 
 /* Human-readable name of a status ("BFS_OK", ...). Never NULL. */
@@ -125,7 +127,7 @@ typedef struct {
     int32_t p;               /* grid is p x p */
     int32_t mode;
     int32_t wah_word_bits;
-    int32_t reserved;
+    int32_t row_exchange;
     int64_t range_size;      /* ceil(n / p) */
     int64_t nonempty_columns;/* sum over blocks of |V_{i,j}| (set directory bits) */
 } bfs_graph_info_t;
@@ -136,6 +138,21 @@ BFS_API bfs_status bfs_graph_info(bfs_graph_t g, bfs_graph_info_t *info);
  * serves all three algorithms of Table 5).  Not safe while a search on `g`
  * is running. */
 BFS_API bfs_status bfs_graph_set_mode(bfs_graph_t g, int32_t mode, int32_t wah_word_bits);
+
+/*
+ * The row exchange of the 2D partition (the fold of the partial next
+ * frontiers of one block-row; the paper names the combination with 2D
+ * partitioning in Sec. VIII).  The expansion keeps, per CTA and block-row i, a
+ * partial next bitmap t_i of the destinations it reached, already sieved by
+ * not(pi_i) (vertices visited before the level are never set: the row
+ * exchange drops already-visited vertices).  With `enabled` = 0 the partials
+ * are OR-folded into t through L2; with 1 each partial is WAH-encoded
+ * (32-bit words) into a row buffer when its CTA leaves the row, and the row is
+ * folded by OR-decoding its buffers.  The result never changes t_i.  Applies
+ * when a range's bitmaps fit in shared memory (range size up to about 830K
+ * vertices); larger ranges fold through L2 either way.
+ */
+BFS_API bfs_status bfs_graph_set_row_exchange(bfs_graph_t g, int32_t enabled);
 
 /*
  * Copy the directory vector V_{i,j} (Eq. 4: bit k set iff source column
@@ -156,6 +173,7 @@ typedef struct {
     int64_t raw_bytes;           /* bytes of the raw bitmap exchange: p slices of each range */
     int64_t wah_bytes;           /* bytes of the compressed streams (0 in PLAIN mode) */
     int64_t edges_scanned;       /* adjacency entries read by the expansion */
+    int64_t row_wah_bytes;       /* bytes of the compressed row exchange (0 when off) */
     float ms_compress_sieve;     /* sieve + compress + decompress kernels */
     float ms_communication;      /* exchange: size scan (and packing when traced) */
     float ms_traversing;         /* expansion (the local SpMV) */

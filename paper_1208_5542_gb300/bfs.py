@@ -119,6 +119,9 @@ class Graph:
     def set_mode(self, mode: int, wah_bits: int = 32):
         check(native.lib().bfs_graph_set_mode(self._h, int(mode), int(wah_bits)))
 
+    def set_row_exchange(self, enabled: bool):
+        check(native.lib().bfs_graph_set_row_exchange(self._h, int(bool(enabled))))
+
     def mode(self):
         info = native.GraphInfo()
         check(native.lib().bfs_graph_info(self._h, ctypes.byref(info)))

@@ -83,6 +83,14 @@ struct LevelArgs {
     int mode;
     int64_t plain_upb;                  // PLAIN units per block
     int64_t win_words;                  // words of the shared-memory row window (0: none)
+    // compressed row exchange (2D fold): row buffers of the partial next bits
+    int row_exchange;
+    uint32_t* rowbuf;                   // rowbuf_slots x rowbuf_cap 32-bit WAH words
+    int64_t rowbuf_cap;
+    int64_t rowbuf_slots;
+    unsigned long long* rowbuf_count;   // slots used in this level
+    int32_t* rowbuf_row;                // block-row of each slot
+    int64_t* rowbuf_words;              // words in each slot
 };
 
 __device__ __forceinline__ int64_t range_begin(const LevelArgs& a, int64_t b) {
@@ -251,9 +259,90 @@ __device__ __forceinline__ int owner_lane(uint32_t excl, uint64_t q) {
 }
 
 // ------------------------------------------------------------ row window --
-// Leave the current row: OR the CTA's partial next bits into t.
-__device__ void window_leave(const LevelArgs& a, uint32_t* s_t, int row) {
+// 32-bit WAH stream (Sec. IV, Table 3) of the CTA's window bits t & ~pi
+// (nbits of them), written to out by the whole CTA: tiles of kXT groups, one
+// group per thread, block scans of head flags and of head positions as in the
+// exchange encoder.  Returns the word count (to every thread).
+__device__ int64_t cta_encode_window(const uint32_t* s_t, const uint32_t* s_pi, int64_t win, int64_t nbits,
+                                     uint32_t* out) {
+    __shared__ uint8_t s_ty[kXT];
+    __shared__ int64_t s_red[kXW + 1];
+    __shared__ int s_next, s_carry_type;
+    __shared__ int64_t s_carry_start, s_total;
+    auto word_at = [&](int64_t w) -> uint32_t { return (w < win) ? (s_t[w] & ~s_pi[w]) : 0u; };
+    auto group = [&](int64_t g) -> uint32_t {
+        const int64_t pos = g * 31;
+        const int64_t w = pos >> 5;
+        return __funnelshift_r(word_at(w), word_at(w + 1), (uint32_t)(pos & 31)) & 0x7fffffffu;
+    };
+    auto type_of = [](uint32_t x) -> int { return x == 0u ? G_ZERO : (x == 0x7fffffffu ? G_ONE : G_LIT); };
+    const int64_t G = nbits / 31;
+    const int r = (int)(nbits % 31);
+    int64_t nw = 0, run_start = 0;
+    int prev = -1;
+    for (int64_t tb = 0; tb < G; tb += kXT) {
+        const int64_t tend = (tb + kXT < G) ? tb + kXT : G;
+        const int64_t g = tb + threadIdx.x;
+        const bool valid = g < tend;
+        const uint32_t x = valid ? group(g) : 0u;
+        const int ty = valid ? type_of(x) : G_NONE;
+        s_ty[threadIdx.x] = (uint8_t)ty;
+        if (threadIdx.x == 0) s_next = (tend < G) ? type_of(group(tend)) : G_NONE;
+        __syncthreads();
+        const int pt = (threadIdx.x == 0) ? prev : (int)s_ty[threadIdx.x - 1];
+        const bool h = valid && (ty == G_LIT || ty != pt);
+        int64_t tot_h, dummy;
+        const int64_t excl_h = block_excl_scan<kXT>((int64_t)h, (int64_t)0, OpSum(), s_red, &tot_h);
+        const int64_t excl_pos = block_excl_scan<kXT>(h ? g : (int64_t)-1, (int64_t)-1, OpMax(), s_red, &dummy);
+        const int64_t start = h ? g : (excl_pos > run_start ? excl_pos : run_start);
+        const int64_t widx = nw + excl_h - (h ? 0 : 1);
+        if (valid) {
+            const int nt = (g + 1 < tend) ? (int)s_ty[threadIdx.x + 1] : s_next;
+            if (ty == G_LIT) out[widx] = __brev(x) >> 1;
+            else if (nt != ty) out[widx] = 0x80000000u | (ty == G_ONE ? 0x40000000u : 0u) | (uint32_t)(g - start + 1);
+            if (g + 1 == tend) { s_carry_type = ty; s_carry_start = start; }
+        }
+        __syncthreads();
+        nw += tot_h;
+        prev = s_carry_type;
+        run_start = s_carry_start;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int64_t total = nw;
+        if (r > 0) {
+            const int64_t pos = G * 31;
+            const uint32_t y = __funnelshift_r(word_at(pos >> 5), word_at((pos >> 5) + 1), (uint32_t)(pos & 31)) &
+                               ((1u << r) - 1u);
+            out[total++] = __brev(y) >> (32 - r);
+        }
+        s_total = total;
+    }
+    __syncthreads();
+    return s_total;
+}
+
+// Leave the current row: fold the CTA's partial next bits into t -- directly
+// (OR through L2), or, with the compressed row exchange, as a WAH row buffer
+// of t_i & ~pi_i that fold_rows OR-decodes into t.
+__device__ void window_leave(const LevelArgs& a, uint32_t* s_t, const uint32_t* s_pi, int row) {
     const int64_t rb = range_begin(a, row);
+    if (a.row_exchange) {
+        __shared__ unsigned long long s_slot;
+        if (threadIdx.x == 0) s_slot = atomicAdd(a.rowbuf_count, 1ull);
+        __syncthreads();
+        const unsigned long long slot = s_slot;
+        if (slot < (unsigned long long)a.rowbuf_slots) {
+            const int64_t nbits = range_begin(a, row + 1) - rb;
+            const int64_t nw = cta_encode_window(s_t, s_pi, a.win_words, nbits, a.rowbuf + (int64_t)slot * a.rowbuf_cap);
+            if (threadIdx.x == 0) {
+                a.rowbuf_row[slot] = row;
+                a.rowbuf_words[slot] = nw;
+            }
+            return;
+        }
+        if (threadIdx.x == 0) atomicOr(a.ctr + C_ERROR, 32ull);    // no slot left (cannot happen by the bound)
+    }
     for (int64_t w = threadIdx.x; w < a.win_words; w += kXT) {
         const uint32_t x = s_t[w];
         if (!x) continue;
@@ -313,7 +402,7 @@ __device__ __forceinline__ void row_affine(const LevelArgs& a, unsigned long lon
             do_unit(row, x);
         }
         __syncthreads();
-        if (WIN) window_leave(a, s_t, row);
+        if (WIN) window_leave(a, s_t, s_pi, row);
         if (threadIdx.x == 0) s_row[0] = pick(row + 1 == p ? 0 : row + 1);
         __syncthreads();
         row = s_row[0];
@@ -533,6 +622,28 @@ __global__ void __launch_bounds__(kNT) plan_units(LevelArgs a) {
     }
 }
 
+// The fold of the compressed row exchange: one CTA per row buffer OR-decodes it
+// into t at its row's first bit.
+__global__ void __launch_bounds__(kXT) fold_rows(LevelArgs a) {
+    __shared__ unsigned long long smu[kXW + 1];
+    __shared__ unsigned long long s_err;
+    const unsigned long long used = *a.rowbuf_count;
+    const unsigned long long nslots = used < (unsigned long long)a.rowbuf_slots ? used : (unsigned long long)a.rowbuf_slots;
+    if (threadIdx.x == 0) s_err = 0ull;
+    __syncthreads();
+    for (unsigned long long slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
+        const int row = a.rowbuf_row[slot];
+        const int64_t rb = range_begin(a, row);
+        const int64_t nbits = range_begin(a, row + 1) - rb;
+        const int64_t nw = a.rowbuf_words[slot];
+        cta_wah_decode_or<uint32_t, kXT>(a.rowbuf + (int64_t)slot * a.rowbuf_cap, nw, nbits, a.t, (uint64_t)rb,
+                                         &s_err, smu);
+        if (threadIdx.x == 0) atomicAdd(a.ctr + C_ROW_WORDS, (unsigned long long)nw);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && s_err) atomicOr(a.ctr + C_ERROR, 16ull);
+}
+
 // ---------------------------------------------------------------- reduce --
 // t = t & ~pi; pi |= t; level of the new vertices; |t|; clear the old
 // frontier (it becomes the next t); frontier summary of t.
@@ -694,7 +805,7 @@ bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
     W.piece_cap = total;
     BFS_TRY(W.pieces.alloc(sizeof(Item) * (total > 0 ? total : 1)));
     // per-level scratch: row_next[p], row_piece_count[p], row_piece_next[p]; row piece bases and caps
-    BFS_TRY(W.level_scratch.alloc(sizeof(unsigned long long) * 3 * p));
+    BFS_TRY(W.level_scratch.alloc(sizeof(unsigned long long) * (3 * p + 1)));
     BFS_TRY(W.row_meta.alloc(sizeof(int64_t) * 2 * p));
     BFS_CUDA_TRY(cudaMemcpy(W.row_meta.ptr, meta.data(), sizeof(int64_t) * 2 * p, cudaMemcpyHostToDevice));
     if (!W.h_counters) {
@@ -708,7 +819,7 @@ bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
     }
     // the row window of the expansion: pi_i and t_i of one range, if they fit
     const int64_t win = (L.nb + 31) / 32;
-    const size_t static_bytes = 1024;
+    const size_t static_bytes = 4096;
     W.win_words = (window_bytes(win) + static_bytes <= (size_t)kSmemLimit) ? win : 0;
     if (W.win_words) {
         const size_t dyn = window_bytes(W.win_words);
@@ -725,6 +836,7 @@ void free_workspace(bfs_graph* g) {
     W.pi.release(); W.fa.release(); W.fb.release(); W.fsum.release(); W.xbuf.release();
     W.xcount.release(); W.chunk_base.release(); W.units.release(); W.counters.release(); W.pieces.release();
     W.level_scratch.release(); W.row_meta.release();
+    W.rowbuf.release(); W.rowbuf_row.release(); W.rowbuf_words.release();
     W.tmp_parent.release(); W.tmp_level.release();
     if (W.h_counters) cudaFreeHost(W.h_counters);
     W.h_counters = nullptr;
@@ -767,6 +879,15 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     unsigned long long* ctr = W.counters.as<unsigned long long>();
     const bool win = W.win_words > 0;
     const int xgrid = sm_count();                  // persistent: one 1024-thread CTA per SM
+    const bool rowx = win && g->row_exchange;      // the compressed row exchange needs the row window
+    if (rowx && !W.rowbuf.ptr) {
+        // every CTA leaves every row at most once per kernel: expansion + pieces
+        W.rowbuf_slots = 2LL * xgrid * p;
+        W.rowbuf_cap = L.nb / 31 + 2;
+        BFS_TRY(W.rowbuf.alloc(sizeof(uint32_t) * W.rowbuf_slots * W.rowbuf_cap));
+        BFS_TRY(W.rowbuf_row.alloc(sizeof(int32_t) * W.rowbuf_slots));
+        BFS_TRY(W.rowbuf_words.alloc(sizeof(int64_t) * W.rowbuf_slots));
+    }
     const size_t dyn = win ? window_bytes(W.win_words) : 0;
     DevBuf slot_off;
     if (tracing) BFS_TRY(slot_off.alloc(sizeof(int64_t) * nslots));
@@ -810,6 +931,13 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     a.mode = mode;
     a.plain_upb = (L.nb + 1023) / 1024;               // 32 raw words per PLAIN unit
     a.win_words = W.win_words;
+    a.row_exchange = rowx ? 1 : 0;
+    a.rowbuf = W.rowbuf.as<uint32_t>();
+    a.rowbuf_cap = W.rowbuf_cap;
+    a.rowbuf_slots = W.rowbuf_slots;
+    a.rowbuf_count = lvl + 3 * p;
+    a.rowbuf_row = W.rowbuf_row.as<int32_t>();
+    a.rowbuf_words = W.rowbuf_words.as<int64_t>();
 
     EncodeArgs ea;
     memset(&ea, 0, sizeof(ea));
@@ -837,7 +965,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             BFS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * C_ERROR, st));
             BFS_CUDA_TRY(cudaMemsetAsync(ctr + C_WAH_WORDS, 0, sizeof(unsigned long long) * (C_NUM - C_WAH_WORDS), st));
         }
-        BFS_CUDA_TRY(cudaMemsetAsync(lvl, 0, sizeof(unsigned long long) * 3 * p, st));
+        BFS_CUDA_TRY(cudaMemsetAsync(lvl, 0, sizeof(unsigned long long) * (3 * p + 1), st));
         a.f = f;
         a.t = t;
         ea.frontier = f;
@@ -878,6 +1006,10 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         if (win) expand_pieces<true><<<xgrid, kXT, dyn, st>>>(a);
         else expand_pieces<false><<<xgrid, kXT, 0, st>>>(a);
         BFS_CUDA_TRY(cudaGetLastError());
+        if (rowx) {
+            fold_rows<<<xgrid, kXT, 0, st>>>(a);
+            BFS_CUDA_TRY(cudaGetLastError());
+        }
         if (timing) cudaEventRecord(W.ev[3], st);
         reduce_level<<<std::min<int64_t>((W.bm_words + 255) / 256 + 1, sm_count() * 16), kNT, 0, st>>>(
             t, W.pi.as<uint32_t>(), f, W.fsum.as<uint8_t>(), W.bm_words, L.n, level, k + 1, ctr);
@@ -905,6 +1037,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
                 ls.raw_bytes = raw_bytes;
                 ls.wah_bytes = (mode == BFS_MODE_PLAIN) ? 0 : (int64_t)h[C_WAH_WORDS] * (wbits / 8);
                 ls.edges_scanned = (int64_t)h[C_EDGES];
+                ls.row_wah_bytes = (int64_t)h[C_ROW_WORDS] * 4;
                 if (timing) {
                     ls.ms_compress_sieve = elapsed(W.ev[0], W.ev[1]);
                     ls.ms_communication = elapsed(W.ev[1], W.ev[2]);

@@ -385,6 +385,7 @@ bfs_status create_common(int64_t n, int64_t m, const int32_t* src, const int32_t
     g->mode = o.mode;
     g->wah_bits = o.wah_word_bits;
     g->debug_checks = o.debug_checks;
+    g->row_exchange = o.row_exchange ? 1 : 0;
     cudaGetDevice(&g->device);
 
     DevBuf dsrc, ddst;
@@ -432,6 +433,7 @@ void bfs_options_default(bfs_options* opt) {
     opt->wah_word_bits = 32;
     opt->autotune = 0;
     opt->debug_checks = 0;
+    opt->row_exchange = 0;
 }
 
 const char* bfs_status_string(bfs_status s) {
@@ -543,6 +545,7 @@ bfs_status bfs_graph_info(bfs_graph_t g, bfs_graph_info_t* info) {
     info->mode = g->mode;
     info->wah_word_bits = g->wah_bits;
     info->range_size = g->L.nb;
+    info->row_exchange = g->row_exchange;
     info->nonempty_columns = g->L.nnzc_total;
     return BFS_OK;
 }
@@ -555,6 +558,14 @@ bfs_status bfs_graph_set_mode(bfs_graph_t g, int32_t mode, int32_t wah_word_bits
     std::lock_guard<std::mutex> lk(g->mu);
     g->mode = mode;
     g->wah_bits = wah_word_bits;
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_set_row_exchange(bfs_graph_t g, int32_t enabled) {
+    if (!g) return set_error(BFS_ERR_INVALID_ARG, "graph is NULL");
+    if (g->busy.load()) return set_error(BFS_ERR_BUSY, "graph is in use");
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->row_exchange = enabled ? 1 : 0;
     return BFS_OK;
 }
 

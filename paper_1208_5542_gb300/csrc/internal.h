@@ -88,6 +88,7 @@ enum Counter : int {
     C_WAH_WORDS,         // words of all streams of this level
     C_EXCHANGED,         // set bits carried by the exchange
     C_PIECES,            // pieces of long columns queued for the piece kernel
+    C_ROW_WORDS,         // WAH words of the compressed row exchange
     C_DBG,               // first failed invariant: 6 slots of context (see bfs_level.cu)
     C_NUM = C_DBG + 6
 };
@@ -107,6 +108,8 @@ struct Workspace {
     DevBuf row_meta;            // per-row piece bases and capacities
     int64_t piece_cap = 0;      // capacity of `pieces` (Item entries)
     int64_t win_words = 0;      // shared-memory row window of the expansion (0: none)
+    DevBuf rowbuf, rowbuf_row, rowbuf_words;   // compressed row exchange
+    int64_t rowbuf_cap = 0, rowbuf_slots = 0;
     DevBuf tmp_parent, tmp_level;      // for searches with host outputs
     uint64_t* h_counters = nullptr;    // pinned mirror of the counters
     cudaEvent_t ev[8] = {};
@@ -124,6 +127,7 @@ struct bfs_graph {
     int mode = BFS_MODE_COMPRESS_SIEVE;
     int wah_bits = 32;
     int debug_checks = 0;
+    int row_exchange = 0;
     int device = 0;
     std::atomic<int> busy{0};
     std::mutex mu;

@@ -200,85 +200,12 @@ __global__ void __launch_bounds__(kNT) wah_encode_kernel(EncodeArgs a, unsigned 
 }
 
 // ------------------------------------------------------- standalone decode --
-// One CTA walks the stream in tiles of kNT words (one per thread), scanning run
-// lengths to place each word, and ORs the decoded groups into the zeroed
-// output.  Malformed streams set *err.
+// One CTA decodes the stream into the zeroed output (cta_wah_decode_or);
+// malformed streams set *err.
 template <typename W>
 __global__ void __launch_bounds__(kNT) wah_decode_bitmap_kernel(DecodeArgs a) {
-    using T = Wah<W>;
-    constexpr int GB = T::GB;
-    const W* in = static_cast<const W*>(a.words);
-    const int64_t G = a.nbits / GB;
-    const int r = (int)(a.nbits % GB);
     __shared__ unsigned long long smu[kNT / 32 + 1];
-    unsigned long long gpos = 0;     // groups consumed before the tile
-    for (int64_t wb = 0; wb < a.nwords; wb += kNT) {
-        const int64_t x = wb + threadIdx.x;
-        const bool valid = x < a.nwords;
-        const W y = valid ? in[x] : W(0);
-        const unsigned long long len = valid ? (unsigned long long)word_groups<W>(y) : 0ull;
-        unsigned long long tot;
-        const unsigned long long gs = gpos + block_excl_scan<kNT>(len, 0ull, OpSum(), smu, &tot);
-        if (valid) {
-            bool bad = false;
-            if (gs < (unsigned long long)G) {
-                if (is_fill<W>(y)) {
-                    if (len == 0 || gs + len > (unsigned long long)G) bad = true;
-                    else if (y & T::VAL) {
-                        // set bits [gs*GB, (gs+len)*GB)
-                        const uint64_t b0 = gs * GB, b1 = (gs + len) * GB;
-                        uint64_t b = b0;
-                        while (b < b1) {
-                            const uint64_t w = b >> 5;
-                            const uint32_t lo = (uint32_t)(b & 31);
-                            const uint64_t take = (b1 - b < 32 - lo) ? b1 - b : 32 - lo;
-                            const uint32_t mask = (take == 32) ? 0xffffffffu : (((1u << take) - 1u) << lo);
-                            if (mask == 0xffffffffu) a.bits[w] = mask;
-                            else atomicOr(a.bits + w, mask);
-                            b += take;
-                        }
-                    }
-                } else {
-                    const W v = T::from_payload(y);
-                    const uint64_t b0 = gs * GB;
-                    // OR the GB bits at b0 (may touch three 32-bit words)
-                    for (int q = 0; q < GB; q += 32) {
-                        const uint64_t bq = b0 + q;
-                        const int nbit = (GB - q < 32) ? GB - q : 32;
-                        uint32_t part = (uint32_t)(v >> q);
-                        if (nbit < 32) part &= (1u << nbit) - 1u;
-                        if (!part) continue;
-                        const uint64_t w = bq >> 5;
-                        const uint32_t sh = (uint32_t)(bq & 31);
-                        atomicOr(a.bits + w, part << sh);
-                        if (sh && (part >> (32 - sh))) atomicOr(a.bits + w + 1, part >> (32 - sh));
-                    }
-                }
-            } else if (gs == (unsigned long long)G && r > 0 && x == a.nwords - 1) {
-                if ((y >> r) != W(0)) bad = true;
-                else {
-                    const W v = T::from_active(y, r);
-                    const uint64_t b0 = gs * GB;
-                    for (int q = 0; q < r; q += 32) {
-                        const uint64_t bq = b0 + q;
-                        const int nbit = (r - q < 32) ? r - q : 32;
-                        uint32_t part = (uint32_t)(v >> q);
-                        if (nbit < 32) part &= (1u << nbit) - 1u;
-                        if (!part) continue;
-                        const uint64_t w = bq >> 5;
-                        const uint32_t sh = (uint32_t)(bq & 31);
-                        atomicOr(a.bits + w, part << sh);
-                        if (sh && (part >> (32 - sh))) atomicOr(a.bits + w + 1, part >> (32 - sh));
-                    }
-                }
-            } else {
-                bad = true;           // word past the groups, or misplaced active word
-            }
-            if (bad) atomicOr(a.err, 1ull);
-        }
-        gpos += tot;
-    }
-    if (threadIdx.x == 0 && gpos != (unsigned long long)G + (r > 0 ? 1ull : 0ull)) atomicOr(a.err, 1ull);
+    cta_wah_decode_or<W, kNT>(static_cast<const W*>(a.words), a.nwords, a.nbits, a.bits, 0ull, a.err, smu);
 }
 
 }  // namespace

@@ -109,4 +109,79 @@ __device__ __forceinline__ uint64_t word_groups(W y) {
     return is_fill(y) ? (uint64_t)(y & Wah<W>::CNT) : 1ull;
 }
 
+// OR bit q of a bitmap of nbits bits into bits[(bit0 + q) / 32], for every
+// bit set in the WAH stream in[0, nwords).  One CTA of NT threads walks the
+// stream in tiles of NT words (one per thread), scanning run lengths to place
+// each word.  Malformed streams (a fill of length 0, groups past nbits, a
+// missing or oversized active word, trailing words) set *err; smu needs NT/32+1
+// elements.  Words of the output entirely inside a 1-fill are stored whole.
+template <typename W, int NT>
+__device__ void cta_wah_decode_or(const W* in, int64_t nwords, int64_t nbits, uint32_t* bits, uint64_t bit0,
+                                  unsigned long long* err, unsigned long long* smu) {
+    using T = Wah<W>;
+    constexpr int GB = T::GB;
+    const int64_t G = nbits / GB;
+    const int r = (int)(nbits % GB);
+    unsigned long long gpos = 0;     // groups consumed before the tile
+    auto or_bits = [&](uint64_t bq, uint32_t part) {
+        const uint64_t w = bq >> 5;
+        const uint32_t sh = (uint32_t)(bq & 31);
+        atomicOr(bits + w, part << sh);
+        if (sh && (part >> (32 - sh))) atomicOr(bits + w + 1, part >> (32 - sh));
+    };
+    for (int64_t wb = 0; wb < nwords; wb += NT) {
+        const int64_t x = wb + threadIdx.x;
+        const bool valid = x < nwords;
+        const W y = valid ? in[x] : W(0);
+        const unsigned long long len = valid ? (unsigned long long)word_groups<W>(y) : 0ull;
+        unsigned long long tot;
+        const unsigned long long gs = gpos + block_excl_scan<NT>(len, 0ull, OpSum(), smu, &tot);
+        if (valid) {
+            bool bad = false;
+            if (gs < (unsigned long long)G) {
+                if (is_fill<W>(y)) {
+                    if (len == 0 || gs + len > (unsigned long long)G) bad = true;
+                    else if (y & T::VAL) {
+                        const uint64_t b1 = bit0 + (gs + len) * GB;
+                        uint64_t b = bit0 + gs * GB;
+                        while (b < b1) {
+                            const uint64_t w = b >> 5;
+                            const uint32_t lo = (uint32_t)(b & 31);
+                            const uint64_t take = (b1 - b < 32 - lo) ? b1 - b : 32 - lo;
+                            const uint32_t mask = (take == 32) ? 0xffffffffu : (((1u << take) - 1u) << lo);
+                            if (mask == 0xffffffffu) bits[w] = mask;
+                            else atomicOr(bits + w, mask);
+                            b += take;
+                        }
+                    }
+                } else {
+                    const W v = T::from_payload(y);
+                    for (int q = 0; q < GB; q += 32) {
+                        const int nbit = (GB - q < 32) ? GB - q : 32;
+                        uint32_t part = (uint32_t)(v >> q);
+                        if (nbit < 32) part &= (1u << nbit) - 1u;
+                        if (part) or_bits(bit0 + gs * GB + q, part);
+                    }
+                }
+            } else if (gs == (unsigned long long)G && r > 0 && x == nwords - 1) {
+                if ((y >> r) != W(0)) bad = true;
+                else {
+                    const W v = T::from_active(y, r);
+                    for (int q = 0; q < r; q += 32) {
+                        const int nbit = (r - q < 32) ? r - q : 32;
+                        uint32_t part = (uint32_t)(v >> q);
+                        if (nbit < 32) part &= (1u << nbit) - 1u;
+                        if (part) or_bits(bit0 + gs * GB + q, part);
+                    }
+                }
+            } else {
+                bad = true;           // word past the groups, or misplaced active word
+            }
+            if (bad) atomicOr(err, 1ull);
+        }
+        gpos += tot;
+    }
+    if (threadIdx.x == 0 && gpos != (unsigned long long)G + (r > 0 ? 1ull : 0ull)) atomicOr(err, 1ull);
+}
+
 }  // namespace bfsgb

@@ -29,17 +29,17 @@ MODE_PLAIN, MODE_COMPRESS, MODE_COMPRESS_SIEVE = 0, 1, 2
 
 class Options(ctypes.Structure):
     _fields_ = [("grid_r", i32), ("grid_c", i32), ("mode", i32), ("wah_word_bits", i32),
-                ("autotune", i32), ("debug_checks", i32)]
+                ("autotune", i32), ("debug_checks", i32), ("row_exchange", i32)]
 
 
 class GraphInfo(ctypes.Structure):
     _fields_ = [("n_vertices", i64), ("n_entries", i64), ("p", i32), ("mode", i32), ("wah_word_bits", i32),
-                ("reserved", i32), ("range_size", i64), ("nonempty_columns", i64)]
+                ("row_exchange", i32), ("range_size", i64), ("nonempty_columns", i64)]
 
 
 class LevelStats(ctypes.Structure):
     _fields_ = [("frontier_vertices", i64), ("exchanged_vertices", i64), ("column_hits", i64),
-                ("raw_bytes", i64), ("wah_bytes", i64), ("edges_scanned", i64),
+                ("raw_bytes", i64), ("wah_bytes", i64), ("edges_scanned", i64), ("row_wah_bytes", i64),
                 ("ms_compress_sieve", ctypes.c_float), ("ms_communication", ctypes.c_float),
                 ("ms_traversing", ctypes.c_float), ("ms_reducing", ctypes.c_float)]
 
@@ -70,6 +70,7 @@ _SIGS = {
     "bfs_graph_footprint": (ctypes.c_int, [vp, P(i64)]),
     "bfs_graph_info": (ctypes.c_int, [vp, P(GraphInfo)]),
     "bfs_graph_set_mode": (ctypes.c_int, [vp, i32, i32]),
+    "bfs_graph_set_row_exchange": (ctypes.c_int, [vp, i32]),
     "bfs_graph_directory": (ctypes.c_int, [vp, i32, i32, vp, vp]),
     "bfs_run": (ctypes.c_int, [vp, i32, vp, vp, P(RunStats), vp]),
     "bfs_run_batch": (ctypes.c_int, [vp, vp, i32, vp, vp, P(BatchStats), vp]),

@@ -255,3 +255,25 @@ def test_zero_tiles_skipped_then_set_bit_at_tile_start(gap_tiles):
         parent, level, st = _run(g, 0, stats=True, trace_capacity=1 << 16)
         assert (level == lv).all() and (parent == pa).all()
         _check_trace(_unpack_trace(st, 32), tr)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("scale,p", [(14, 4), (16, 8), (13, 7)])
+def test_compressed_row_exchange_never_changes_the_result(mode, scale, p):
+    """With the row exchange on, every CTA's partial next bitmap of a block-row
+    (sieved by not(pi)) travels as a WAH row buffer and the row is folded by
+    OR-decoding them; levels and parents stay those of the oracle."""
+    bfs = _lib()
+    n, src, dst = graphgen.edges(scale, 16)
+    go = oracle.csr(n, src, dst)
+    g = bfs.Graph.from_edges(n, src, dst, p=p, mode=mode)
+    g.set_row_exchange(True)
+    for r in graphgen.pick_roots(n, src, dst, 3):
+        lv, pa = oracle.bfs(go, int(r))
+        parent, level, st = _run(g, int(r), stats=True)
+        assert (level == lv).all() and (parent == pa).all()
+        assert sum(ls["row_wah_bytes"] for ls in st.levels) > 0
+    g.set_row_exchange(False)
+    parent, level, st = _run(g, int(r), stats=True)
+    assert (level == lv).all() and (parent == pa).all()
+    assert sum(ls["row_wah_bytes"] for ls in st.levels) == 0
