@@ -38,6 +38,12 @@ namespace bfsgb {
 
 bfs_status launch_wah_encode_counted(const EncodeArgs& a, int wah_bits, unsigned long long* setbits,
                                      cudaStream_t st);
+int64_t parallel_encode_chunks(int64_t max_nbits, int wah_bits);
+bfs_status launch_wah_encode_parallel(const EncodeArgs& a, int wah_bits, void* sums, void* bases, int64_t cps,
+                                      void* flags, void* list, unsigned long long* nlist, unsigned long long* setbits,
+                                      int grid, cudaStream_t st);
+size_t parallel_encode_sum_bytes();
+size_t parallel_encode_base_bytes();
 
 namespace {
 
@@ -82,6 +88,7 @@ struct LevelArgs {
     unsigned long long* ctr;
     int mode;
     int64_t plain_upb;                  // PLAIN units per block
+    int64_t plain_batch;                // PLAIN units per hand-out (set per level)
     int64_t win_words;                  // words of the shared-memory row window (0: none)
     // compressed row exchange (2D fold): row buffers of the partial next bits
     int row_exchange;
@@ -366,12 +373,14 @@ __device__ void window_enter(const LevelArgs& a, uint32_t* s_pi, uint32_t* s_t, 
 
 // Row-affine persistent loop.  The CTA settles on a block-row with units
 // left; its warps take the row's units one at a time (warp-granular, no block
-// barrier per unit) until the row is drained, then the CTA folds its partial
-// next bits into t, picks the next row with units left and loads that row's
-// visited bits.  Every row is tried at most once per CTA.
+// barrier per unit; `batch` units per hand-out) until the row is drained, then
+// the CTA folds its partial next bits into t, picks the next row with units
+// left and loads that row's visited bits.  Every row is tried at most once
+// per CTA.
 template <bool WIN, typename Units, typename Work>
-__device__ __forceinline__ void row_affine(const LevelArgs& a, unsigned long long* counters, Units units_in_row,
-                                           Work do_unit, uint32_t* s_pi, uint32_t* s_t, int* s_row) {
+__device__ __forceinline__ void row_affine(const LevelArgs& a, unsigned long long* counters, int64_t batch,
+                                           Units units_in_row, Work do_unit, uint32_t* s_pi, uint32_t* s_t,
+                                           int* s_row) {
     const int p = a.p;
     int tried = 0;
     int start = blockIdx.x % p;
@@ -395,11 +404,12 @@ __device__ __forceinline__ void row_affine(const LevelArgs& a, unsigned long lon
             int64_t x = 0;
             if (lane_id() == 0) {
                 x = ((int64_t)*reinterpret_cast<volatile unsigned long long*>(counters + row) < nu)
-                        ? (int64_t)atomicAdd(counters + row, 1ull) : nu;
+                        ? (int64_t)atomicAdd(counters + row, (unsigned long long)batch) : nu;
             }
             x = __shfl_sync(0xffffffffu, x, 0);
             if (x >= nu) break;
-            do_unit(row, x);
+            const int64_t xe = (x + batch < nu) ? x + batch : nu;
+            for (; x < xe; ++x) do_unit(row, x);
         }
         __syncthreads();
         if (WIN) window_leave(a, s_t, s_pi, row);
@@ -496,7 +506,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
             warp_expand<WIN>(a, vis, row, u, begin, len, edges, hits);
         }
     };
-    row_affine<WIN>(a, a.row_next, units_in_row, do_unit, s_pi, s_t, s_row);
+    row_affine<WIN>(a, a.row_next, 2, units_in_row, do_unit, s_pi, s_t, s_row);
     flush_counts(a, edges, hits, nitems);
 }
 
@@ -550,7 +560,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
             warp_expand<WIN>(a, vis, row, u, begin, len, edges, hits);
         }
     };
-    row_affine<WIN>(a, a.row_next, units_in_row, do_unit, s_pi, s_t, s_row);
+    row_affine<WIN>(a, a.row_next, a.plain_batch, units_in_row, do_unit, s_pi, s_t, s_row);
     flush_counts(a, edges, hits, nitems);
 }
 
@@ -569,7 +579,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_pieces(LevelArgs a) {
         const Visitor<WIN> vis{s_pi, s_t, range_begin(a, row)};
         warp_column<WIN>(a, vis, it.u, it.begin, it.len);
     };
-    row_affine<WIN>(a, a.row_piece_next, units_in_row, do_unit, s_pi, s_t, s_row);
+    row_affine<WIN>(a, a.row_piece_next, 1, units_in_row, do_unit, s_pi, s_t, s_row);
 }
 
 // Per stream: group base of every chunk of 32 words.  One CTA per stream;
@@ -790,6 +800,11 @@ bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
     BFS_TRY(W.xcount.alloc(sizeof(int64_t) * p2));
     BFS_TRY(W.chunk_base.alloc(sizeof(int64_t) * p2 * W.chunks_per_slot));
     BFS_TRY(W.units.alloc(sizeof(int64_t) * (p2 + 1)));              // slot unit bases
+    W.enc_cps = parallel_encode_chunks(L.nb, 32);                       // 31-bit groups: the most chunks
+    BFS_TRY(W.enc_sums.alloc(parallel_encode_sum_bytes() * p2 * W.enc_cps));
+    BFS_TRY(W.enc_bases.alloc(parallel_encode_base_bytes() * p2 * W.enc_cps));
+    BFS_TRY(W.enc_flags.alloc(p2 * W.enc_cps));
+    BFS_TRY(W.enc_list.alloc(sizeof(int64_t) * p2 * W.enc_cps));
     BFS_TRY(W.counters.alloc(sizeof(unsigned long long) * C_NUM));
     // pieces: per row, sum over long columns of ceil(len/kPiece) <= nnz_row/kPiece + nnz_row/kHub
     std::vector<int64_t> meta(2 * (size_t)p);
@@ -837,6 +852,7 @@ void free_workspace(bfs_graph* g) {
     W.xcount.release(); W.chunk_base.release(); W.units.release(); W.counters.release(); W.pieces.release();
     W.level_scratch.release(); W.row_meta.release();
     W.rowbuf.release(); W.rowbuf_row.release(); W.rowbuf_words.release();
+    W.enc_sums.release(); W.enc_bases.release(); W.enc_flags.release(); W.enc_list.release();
     W.tmp_parent.release(); W.tmp_level.release();
     if (W.h_counters) cudaFreeHost(W.h_counters);
     W.h_counters = nullptr;
@@ -968,6 +984,9 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         BFS_CUDA_TRY(cudaMemsetAsync(lvl, 0, sizeof(unsigned long long) * (3 * p + 1), st));
         a.f = f;
         a.t = t;
+        // PLAIN scans every raw word of every block: hand out many units at a
+        // time on sparse levels (few items each), few on dense ones (balance)
+        a.plain_batch = (frontier * 64 < L.n) ? 32 : 2;
         ea.frontier = f;
         if (timing) cudaEventRecord(W.ev[0], st);
         if (mode == BFS_MODE_PLAIN) {
@@ -976,7 +995,9 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             else expand_plain<false><<<xgrid, kXT, 0, st>>>(a);
             BFS_CUDA_TRY(cudaGetLastError());
         } else {
-            BFS_TRY(launch_wah_encode_counted(ea, wbits, ctr + C_EXCHANGED, st));
+            BFS_TRY(launch_wah_encode_parallel(ea, wbits, W.enc_sums.ptr, W.enc_bases.ptr, W.enc_cps,
+                                               W.enc_flags.ptr, W.enc_list.ptr, ctr + C_ENC_LIST, ctr + C_EXCHANGED,
+                                               sm_count() * 8, st));
             if (wbits == 32) stream_chunks<uint32_t><<<nslots, kNT, 0, st>>>(a, nslots);
             else stream_chunks<unsigned long long><<<nslots, kNT, 0, st>>>(a, nslots);
             BFS_CUDA_TRY(cudaGetLastError());

@@ -531,7 +531,9 @@ bfs_status bfs_graph_footprint(bfs_graph_t g, int64_t* bytes) {
     int64_t b = (int64_t)(L.dir.bytes + L.rank.bytes + L.cp.bytes + L.ir.bytes + L.cp_base_d.bytes + L.ir_base_d.bytes);
     b += (int64_t)(W.pi.bytes + W.fa.bytes + W.fb.bytes + W.fsum.bytes + W.xbuf.bytes + W.xcount.bytes +
                    W.chunk_base.bytes + W.units.bytes + W.counters.bytes + W.tmp_parent.bytes + W.tmp_level.bytes +
-                   W.pieces.bytes + W.level_scratch.bytes + W.row_meta.bytes);
+                   W.pieces.bytes + W.level_scratch.bytes + W.row_meta.bytes + W.rowbuf.bytes + W.rowbuf_row.bytes +
+                   W.rowbuf_words.bytes + W.enc_sums.bytes + W.enc_bases.bytes + W.enc_flags.bytes +
+                   W.enc_list.bytes);
     *bytes = b;
     return BFS_OK;
 }

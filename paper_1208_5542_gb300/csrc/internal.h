@@ -89,6 +89,7 @@ enum Counter : int {
     C_EXCHANGED,         // set bits carried by the exchange
     C_PIECES,            // pieces of long columns queued for the piece kernel
     C_ROW_WORDS,         // WAH words of the compressed row exchange
+    C_ENC_LIST,          // chunks listed for the parallel encoder
     C_DBG,               // first failed invariant: 6 slots of context (see bfs_level.cu)
     C_NUM = C_DBG + 6
 };
@@ -109,6 +110,9 @@ struct Workspace {
     int64_t piece_cap = 0;      // capacity of `pieces` (Item entries)
     int64_t win_words = 0;      // shared-memory row window of the expansion (0: none)
     DevBuf rowbuf, rowbuf_row, rowbuf_words;   // compressed row exchange
+    DevBuf enc_sums, enc_bases;  // chunk summaries of the parallel encoder
+    DevBuf enc_flags, enc_list;  // chunks with frontier bits, and their list
+    int64_t enc_cps = 0;         // encoder chunks per slot
     int64_t rowbuf_cap = 0, rowbuf_slots = 0;
     DevBuf tmp_parent, tmp_level;      // for searches with host outputs
     uint64_t* h_counters = nullptr;    // pinned mirror of the counters

@@ -11,6 +11,7 @@
 // run, the word count and the previous type carry from tile to tile.  Tiles
 // whose frontier bits are all zero (frontier summary: one byte per 1024 bits)
 // are skipped without loading a word.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -199,6 +200,274 @@ __global__ void __launch_bounds__(kNT) wah_encode_kernel(EncodeArgs a, unsigned 
     }
 }
 
+// ------------------------------------------------- parallel slot encoder --
+// The same stream as wah_encode_kernel, built in data-parallel passes over
+// (slot, chunk of kTile groups):
+//   0. enc_chunk_flags: one thread per chunk tests the frontier summary and
+//      appends the chunks with any frontier bit to a work list;
+//   1. enc_chunk_sums: per listed chunk, its head count (its first group
+//      counted as a head), first and last group type and last head position;
+//   2. enc_chunk_scan: per slot, one warp scans the chunk sums (an all-zero
+//      chunk is one zero run): a chunk whose first group continues the previous
+//      chunk's fill run merges with it; this gives every chunk its first word
+//      index and the start of the run it opens with, the slot's word count and
+//      the active word, and writes the fill word of every zero run that ends
+//      in an all-zero chunk;
+//   3. enc_chunk_write: per listed chunk, the tile body of the sequential
+//      encoder with the carry taken from pass 2.
+struct ChunkSum {
+    uint32_t heads;
+    uint32_t types;        // first type | last type << 8
+    int64_t last_head;     // group index of the chunk's last head
+};
+struct ChunkBase {
+    int64_t words;         // index of the next word to open at the chunk's first group
+    int64_t run_start;     // start group of the run open before the chunk
+    int32_t prev_type;     // type of the group before the chunk (-1 at the slot start)
+    int32_t next_type;     // type of the group after the chunk (G_NONE at the slot end)
+};
+
+template <typename W>
+__global__ void enc_chunk_flags(EncodeArgs a, int64_t cps, uint8_t* flags, int64_t* list,
+                                unsigned long long* nlist) {
+    constexpr int GB = Wah<W>::GB;
+    const int64_t total = (int64_t)a.nslots * cps;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q - (int64_t)lane_id() < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        bool live = false;
+        if (q < total) {
+            const int s = (int)(q / cps);
+            const int64_t c = q % cps;
+            const SlotGeom sg = slot_geom(a, s);
+            const int64_t G = sg.nbits / GB;
+            const int64_t tb = c * kTile;
+            if (tb < G) {
+                const int64_t tend = (tb + kTile < G) ? tb + kTile : G;
+                live = !a.fsum || !fsum_zero(a.fsum, (sg.src0 + tb * GB) >> 10, (sg.src0 + tend * GB - 1) >> 10);
+            }
+            flags[q] = live ? 1 : 0;
+        }
+        const uint32_t ball = __ballot_sync(0xffffffffu, live);
+        if (ball) {
+            unsigned long long base = 0;
+            if (lane_id() == 0) base = atomicAdd(nlist, (unsigned long long)__popc(ball));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (live) list[base + __popc(ball & ((1u << lane_id()) - 1u))] = q;
+        }
+    }
+}
+
+template <typename W>
+__global__ void __launch_bounds__(kNT) enc_chunk_sums(EncodeArgs a, ChunkSum* sums, int64_t cps,
+                                                      const int64_t* list, const unsigned long long* nlist,
+                                                      unsigned long long* setbits) {
+    using T = Wah<W>;
+    constexpr int GB = T::GB;
+    __shared__ uint8_t sm_last[kNT];
+    __shared__ int64_t sm64[kNT / 32 + 1];
+    __shared__ unsigned long long smu[kNT / 32 + 1];
+    __shared__ int sm_first_type, sm_last_type;
+    const unsigned long long n = *nlist;
+    for (unsigned long long li = blockIdx.x; li < n; li += gridDim.x) {
+        const int64_t q = list[li];
+        const int s = (int)(q / cps);
+        const int64_t c = q % cps;
+        const SlotGeom sg = slot_geom(a, s);
+        const int64_t G = sg.nbits / GB;
+        const int64_t tb = c * kTile;
+        const int64_t tend = (tb + kTile < G) ? tb + kTile : G;
+        const int64_t g0 = tb + (int64_t)threadIdx.x * kK;
+        int ty[kK];
+        unsigned long long ones = 0;
+#pragma unroll
+        for (int k = 0; k < kK; ++k) {
+            const int64_t g = g0 + k;
+            if (g < tend) {
+                const W x = load_group<W>(a, sg, g);
+                ty[k] = group_type<W>(x);
+                ones += (unsigned long long)T::popc(x);
+                if (g == tb) sm_first_type = ty[k];
+                if (g + 1 == tend) sm_last_type = ty[k];
+            } else {
+                ty[k] = G_NONE;
+            }
+        }
+        sm_last[threadIdx.x] = (uint8_t)ty[kK - 1];
+        __syncthreads();
+        int pt = (threadIdx.x == 0) ? -1 : (int)sm_last[threadIdx.x - 1];
+        int64_t hc = 0, lastpos = -1;
+#pragma unroll
+        for (int k = 0; k < kK; ++k) {
+            const bool h = (ty[k] != G_NONE) && (ty[k] == G_LIT || ty[k] != pt);
+            if (h) { ++hc; lastpos = g0 + k; }
+            pt = ty[k];
+        }
+        int64_t heads, lasth;
+        block_excl_scan<kNT>(hc, (int64_t)0, OpSum(), sm64, &heads);
+        block_excl_scan<kNT>(lastpos, (int64_t)-1, OpMax(), sm64, &lasth);
+        unsigned long long tot_ones;
+        block_excl_scan<kNT>(ones, 0ull, OpSum(), smu, &tot_ones);
+        if (threadIdx.x == 0) {
+            ChunkSum cs;
+            cs.heads = (uint32_t)heads;
+            cs.types = (uint32_t)sm_first_type | ((uint32_t)sm_last_type << 8);
+            cs.last_head = lasth;
+            sums[q] = cs;
+            if (setbits && tot_ones) atomicAdd(setbits, tot_ones);
+        }
+        __syncthreads();
+    }
+}
+
+// One warp per slot (blockDim.x = 32).
+template <typename W>
+__global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t* flags, ChunkBase* bases,
+                               int64_t cps, unsigned long long* setbits) {
+    using T = Wah<W>;
+    constexpr int GB = T::GB;
+    const int s = blockIdx.x;
+    const SlotGeom sg = slot_geom(a, s);
+    const int64_t G = sg.nbits / GB;
+    const int r = (int)(sg.nbits % GB);
+    const int64_t nch = (G + kTile - 1) / kTile;
+    const int lane = (int)lane_id();
+    W* out = static_cast<W*>(a.out) + (int64_t)s * a.slot_cap;
+    auto sum_of = [&](int64_t c) -> ChunkSum {
+        ChunkSum cs;
+        if (flags[(int64_t)s * cps + c]) return sums[(int64_t)s * cps + c];
+        cs.heads = 1;                                   // an all-zero chunk: one zero run
+        cs.types = G_ZERO | (G_ZERO << 8);
+        cs.last_head = c * kTile;
+        return cs;
+    };
+    int64_t words = 0, hmax = -1;
+    int prev_last = -1;
+    for (int64_t c0 = 0; c0 < nch; c0 += 32) {
+        const int64_t c = c0 + lane;
+        ChunkSum cs;
+        cs.heads = 0;
+        cs.types = G_NONE | (G_NONE << 8);
+        cs.last_head = -1;
+        if (c < nch) cs = sum_of(c);
+        const int first = (int)(cs.types & 0xff), last = (int)((cs.types >> 8) & 0xff);
+        int before = __shfl_up_sync(0xffffffffu, last, 1);
+        if (lane == 0) before = prev_last;
+        const bool merge = (c < nch) && before == first && first != G_LIT && before >= 0;
+        const int64_t eff = (c < nch) ? (int64_t)cs.heads - (merge ? 1 : 0) : 0;
+        const int64_t h = (c < nch) ? ((merge && cs.heads == 1) ? (int64_t)-1 : cs.last_head) : (int64_t)-1;
+        int64_t incl = eff, hin = h;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, incl, d);
+            const int64_t z = __shfl_up_sync(0xffffffffu, hin, d);
+            if (lane >= d) { incl += y; hin = z > hin ? z : hin; }
+        }
+        int64_t hex = __shfl_up_sync(0xffffffffu, hin, 1);
+        if (lane == 0) hex = -1;
+        hex = hex > hmax ? hex : hmax;
+        int nxt = __shfl_down_sync(0xffffffffu, first, 1);
+        if (c < nch) {
+            ChunkBase cb;
+            cb.words = words + incl - eff;
+            cb.run_start = merge ? hex : c * kTile;
+            cb.prev_type = before;
+            if (c + 1 >= nch) nxt = G_NONE;
+            else if (lane == 31) nxt = (int)(sum_of(c + 1).types & 0xff);
+            cb.next_type = nxt;
+            bases[(int64_t)s * cps + c] = cb;
+            if (!flags[(int64_t)s * cps + c] && nxt != G_ZERO) {
+                // the zero run through this all-zero chunk ends at its last group
+                const int64_t tend = ((c + 1) * kTile < G) ? (c + 1) * kTile : G;
+                const int64_t start = merge ? cb.run_start : c * kTile;
+                out[merge ? cb.words - 1 : cb.words] = fill_word<W>(G_ZERO, (uint64_t)(tend - start));
+            }
+        }
+        words += __shfl_sync(0xffffffffu, incl, 31);
+        const int64_t hb = __shfl_sync(0xffffffffu, hin, 31);
+        hmax = hb > hmax ? hb : hmax;
+        const int last_lane = (c0 + 32 > nch) ? (int)((nch - 1) % 32) : 31;
+        prev_last = __shfl_sync(0xffffffffu, last, last_lane);
+    }
+    if (lane == 0) {
+        int64_t total = words;
+        if (r > 0) {
+            const uint64_t pos = (uint64_t)(sg.src0 + G * GB);
+            W y = T::tail(a.frontier, pos, r);
+            if (sg.dirb && y) y &= T::tail(sg.dirb, (uint64_t)(G * GB), r);
+            if (setbits && y) atomicAdd(setbits, (unsigned long long)T::popc(y));
+            out[total++] = T::to_active(y, r);
+        }
+        a.counts[s] = total;
+    }
+}
+
+template <typename W>
+__global__ void __launch_bounds__(kNT) enc_chunk_write(EncodeArgs a, const ChunkBase* bases, int64_t cps,
+                                                       const int64_t* list, const unsigned long long* nlist) {
+    using T = Wah<W>;
+    constexpr int GB = T::GB;
+    __shared__ int64_t sm64[kNT / 32 + 1];
+    __shared__ uint8_t sm_first[kNT], sm_last[kNT];
+    const unsigned long long n = *nlist;
+    for (unsigned long long li = blockIdx.x; li < n; li += gridDim.x) {
+        const int64_t q = list[li];
+        const int s = (int)(q / cps);
+        const int64_t c = q % cps;
+        const SlotGeom sg = slot_geom(a, s);
+        const int64_t G = sg.nbits / GB;
+        const int64_t tb = c * kTile;
+        const int64_t tend = (tb + kTile < G) ? tb + kTile : G;
+        const ChunkBase cb = bases[q];
+        W* out = static_cast<W*>(a.out) + (int64_t)s * a.slot_cap;
+        const int64_t g0 = tb + (int64_t)threadIdx.x * kK;
+        W x[kK];
+        int ty[kK];
+#pragma unroll
+        for (int k = 0; k < kK; ++k) {
+            const int64_t g = g0 + k;
+            if (g < tend) {
+                x[k] = load_group<W>(a, sg, g);
+                ty[k] = group_type<W>(x[k]);
+            } else {
+                x[k] = W(0);
+                ty[k] = G_NONE;
+            }
+        }
+        sm_first[threadIdx.x] = (uint8_t)ty[0];
+        sm_last[threadIdx.x] = (uint8_t)ty[kK - 1];
+        __syncthreads();
+        const int prev0 = (threadIdx.x == 0) ? cb.prev_type : (int)sm_last[threadIdx.x - 1];
+        bool h[kK];
+        int hc = 0;
+        int64_t lastpos = -1;
+        int pt = prev0;
+#pragma unroll
+        for (int k = 0; k < kK; ++k) {
+            h[k] = (ty[k] != G_NONE) && (ty[k] == G_LIT || ty[k] != pt);
+            if (h[k]) { ++hc; lastpos = g0 + k; }
+            pt = ty[k];
+        }
+        int64_t tot_h, dummy;
+        const int64_t excl_h = block_excl_scan<kNT>((int64_t)hc, (int64_t)0, OpSum(), sm64, &tot_h);
+        const int64_t excl_pos = block_excl_scan<kNT>(lastpos, (int64_t)-1, OpMax(), sm64, &dummy);
+        int64_t cur_start = excl_pos > cb.run_start ? excl_pos : cb.run_start;
+        int64_t widx = cb.words + excl_h - 1;
+#pragma unroll
+        for (int k = 0; k < kK; ++k) {
+            const int64_t g = g0 + k;
+            if (ty[k] == G_NONE) break;
+            if (h[k]) { cur_start = g; ++widx; }
+            int nt;
+            if (k + 1 < kK) nt = ty[k + 1];
+            else nt = (threadIdx.x + 1 < kNT) ? (int)sm_first[threadIdx.x + 1] : G_NONE;
+            if (g + 1 == tend) nt = cb.next_type;
+            if (ty[k] == G_LIT) out[widx] = T::to_payload(x[k]);
+            else if (nt != ty[k]) out[widx] = fill_word<W>(ty[k], (uint64_t)(g - cur_start + 1));
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------- standalone decode --
 // One CTA decodes the stream into the zeroed output (cta_wah_decode_or);
 // malformed streams set *err.
@@ -230,6 +499,40 @@ bfs_status launch_wah_encode_counted(const EncodeArgs& a, int wah_bits, unsigned
     BFS_CUDA_TRY(cudaGetLastError());
     return BFS_OK;
 }
+
+int64_t parallel_encode_chunks(int64_t max_nbits, int wah_bits) {
+    const int64_t G = max_nbits / (wah_bits - 1);
+    return (G + kTile - 1) / kTile + 1;
+}
+
+bfs_status launch_wah_encode_parallel(const EncodeArgs& a, int wah_bits, void* sums, void* bases, int64_t cps,
+                                      void* flags, void* list, unsigned long long* nlist, unsigned long long* setbits,
+                                      int grid, cudaStream_t st) {
+    if (a.nslots <= 0) return BFS_OK;
+    ChunkSum* cs = static_cast<ChunkSum*>(sums);
+    ChunkBase* cb = static_cast<ChunkBase*>(bases);
+    uint8_t* fl = static_cast<uint8_t*>(flags);
+    int64_t* li = static_cast<int64_t*>(list);
+    BFS_CUDA_TRY(cudaMemsetAsync(nlist, 0, sizeof(unsigned long long), st));
+    const int64_t total = (int64_t)a.nslots * cps;
+    const int fgrid = (int)std::min<int64_t>((total + kNT - 1) / kNT, grid);
+    if (wah_bits == 32) {
+        enc_chunk_flags<uint32_t><<<fgrid, kNT, 0, st>>>(a, cps, fl, li, nlist);
+        enc_chunk_sums<uint32_t><<<grid, kNT, 0, st>>>(a, cs, cps, li, nlist, setbits);
+        enc_chunk_scan<uint32_t><<<a.nslots, 32, 0, st>>>(a, cs, fl, cb, cps, setbits);
+        enc_chunk_write<uint32_t><<<grid, kNT, 0, st>>>(a, cb, cps, li, nlist);
+    } else {
+        enc_chunk_flags<unsigned long long><<<fgrid, kNT, 0, st>>>(a, cps, fl, li, nlist);
+        enc_chunk_sums<unsigned long long><<<grid, kNT, 0, st>>>(a, cs, cps, li, nlist, setbits);
+        enc_chunk_scan<unsigned long long><<<a.nslots, 32, 0, st>>>(a, cs, fl, cb, cps, setbits);
+        enc_chunk_write<unsigned long long><<<grid, kNT, 0, st>>>(a, cb, cps, li, nlist);
+    }
+    BFS_CUDA_TRY(cudaGetLastError());
+    return BFS_OK;
+}
+
+size_t parallel_encode_sum_bytes() { return sizeof(ChunkSum); }
+size_t parallel_encode_base_bytes() { return sizeof(ChunkBase); }
 
 bfs_status launch_wah_decode_bitmap(const DecodeArgs& a, int wah_bits, cudaStream_t st) {
     if (wah_bits == 32)
