@@ -341,7 +341,9 @@ def main():
                 agg["wah_bytes"] += ls["wah_bytes"]
                 agg["hits"] += ls["column_hits"]
                 agg["n"] += 1
-    launches_per_bfs = {0: 3, 1: 5, 2: 5}[args.mode]
+    # per level: flag, sum, scan and write passes of the encoder, unit plan, expansion,
+    # hub pieces, reduction (PLAIN: expansion, hub pieces, reduction); per search: init, root
+    launches_per_bfs = {0: 3, 1: 8, 2: 8}[args.mode]
     gpu_launches = sum(2 + launches_per_bfs * st.n_levels for sts in stats_cs for st in sts)
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))

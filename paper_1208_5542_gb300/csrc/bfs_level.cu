@@ -95,6 +95,8 @@ struct LevelArgs {
     uint32_t* rowbuf;                   // rowbuf_slots x rowbuf_cap 32-bit WAH words
     int64_t rowbuf_cap;
     int64_t rowbuf_slots;
+    int sweep;                          // all CTAs start at row 0 (rows in turn)
+    int dedup;                          // read the parent before updating it
     unsigned long long* rowbuf_count;   // slots used in this level
     int32_t* rowbuf_row;                // block-row of each slot
     int64_t* rowbuf_words;              // words in each slot
@@ -117,35 +119,60 @@ struct Visitor {
     const uint32_t* s_pi;
     uint32_t* s_t;
     int64_t rb;     // first vertex of the row
-    __device__ __forceinline__ void operator()(const LevelArgs& a, int32_t v, int32_t u) const {
+    // The visited word of v (loads of several entries are issued before
+    // their visits, so that their latencies overlap).
+    __device__ __forceinline__ uint32_t probe(const LevelArgs& a, int32_t v) const {
+        if (WIN) return s_pi[(uint32_t)(v - rb) >> 5];
+        return __ldg(a.pi + ((uint32_t)v >> 5));
+    }
+    __device__ __forceinline__ bool fresh(int32_t v, uint32_t piw) const {
+        const uint32_t b = WIN ? (uint32_t)(v - rb) : (uint32_t)v;
+        return !(piw & (1u << (b & 31u)));
+    }
+    // The parent recorded so far for a fresh v (possibly an older value: the
+    // parent only decreases during a level, from -1 = the largest unsigned).
+    __device__ __forceinline__ uint32_t seen(const LevelArgs& a, int32_t v) const {
+        return __ldcg(reinterpret_cast<const unsigned int*>(a.parent) + v);
+    }
+    // Visit of a fresh v from u, given an earlier read pv of its parent: when
+    // pv <= u the visit changes nothing (pv != -1 means v already has a
+    // visitor in this level, which set the next bit); otherwise lower the
+    // parent, and the visitor that read -1 sets the next bit.  The visitor of
+    // the first update read -1, so the bit is always set.
+    __device__ __forceinline__ void mark(const LevelArgs& a, int32_t v, int32_t u, uint32_t pv) const {
+        if (pv <= (uint32_t)u) return;
+        atomicMin(reinterpret_cast<unsigned int*>(a.parent) + v, (unsigned int)u);
+        if (pv != 0xffffffffu) return;
         if (WIN) {
             const uint32_t vl = (uint32_t)(v - rb);
-            const uint32_t w = vl >> 5, m = 1u << (vl & 31u);
-            if (s_pi[w] & m) return;
-            atomicMin(reinterpret_cast<unsigned int*>(a.parent) + v, (unsigned int)u);   // -1 is the largest unsigned
-            atomicOr(s_t + w, m);
+            atomicOr(s_t + (vl >> 5), 1u << (vl & 31u));
         } else {
-            const uint32_t w = (uint32_t)v >> 5, m = 1u << ((uint32_t)v & 31u);
-            if (__ldg(a.pi + w) & m) return;
-            atomicMin(reinterpret_cast<unsigned int*>(a.parent) + v, (unsigned int)u);
-            atomicOr(a.t + w, m);
+            atomicOr(a.t + ((uint32_t)v >> 5), 1u << ((uint32_t)v & 31u));
         }
     }
 };
 
-// All 32 lanes expand one column: 32 consecutive entries per step.
+// Entries per lane whose loads are in flight together.
+constexpr int kIlp = 4;
+
+// All 32 lanes expand one column: kIlp x 32 consecutive entries per step.
 template <bool WIN>
 __device__ __forceinline__ void warp_column(const LevelArgs& a, const Visitor<WIN>& vis, int32_t u, int64_t beg,
                                             uint32_t len) {
     const int32_t* col = a.ir + beg;
-    uint32_t e = lane_id();
-    for (; e + 32 < len; e += 64) {
-        const int32_t v0 = __ldg(col + e);
-        const int32_t v1 = __ldg(col + e + 32);
-        vis(a, v0, u);
-        vis(a, v1, u);
+    for (uint32_t e = lane_id(); e < len; e += 32 * kIlp) {
+        int32_t v[kIlp];
+        uint32_t w[kIlp];
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) v[k] = (e + 32 * k < len) ? __ldg(col + e + 32 * k) : -1;
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0) ? vis.probe(a, v[k]) : 0u;
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0 && vis.fresh(v[k], w[k])) ? (a.dedup ? vis.seen(a, v[k]) : 0xffffffffu) : 0u;
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k)
+            if (v[k] >= 0) vis.mark(a, v[k], u, w[k]);
     }
-    if (e < len) vis(a, __ldg(col + e), u);
 }
 
 // Expand one item per lane (u, offset of its column in ir, length; length 0 =
@@ -190,19 +217,31 @@ __device__ __forceinline__ void warp_expand(const LevelArgs& a, const Visitor<WI
     const uint32_t incl = warp_incl_sum(len);
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     const uint32_t excl = incl - len;
-    for (uint32_t e0 = 0; e0 < total; e0 += 32) {
-        const uint32_t e = e0 + lane;
-        int lo = 0, hi = 31;                       // owner: first lane whose inclusive count exceeds e
+    for (uint32_t e0 = 0; e0 < total; e0 += 32 * kIlp) {
+        int32_t v[kIlp], ou[kIlp];
+        uint32_t w[kIlp];
 #pragma unroll
-        for (int step = 0; step < 5; ++step) {
-            const int mid = (lo + hi) >> 1;
-            const uint32_t im = __shfl_sync(0xffffffffu, incl, mid);
-            if (im > e) hi = mid; else lo = mid + 1;
+        for (int k = 0; k < kIlp; ++k) {
+            const uint32_t e = e0 + 32 * k + lane;
+            int lo = 0, hi = 31;                   // owner: first lane whose inclusive count exceeds e
+#pragma unroll
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (lo + hi) >> 1;
+                const uint32_t im = __shfl_sync(0xffffffffu, incl, mid);
+                if (im > e) hi = mid; else lo = mid + 1;
+            }
+            const int64_t ob = __shfl_sync(0xffffffffu, beg, lo);
+            const uint32_t oe = __shfl_sync(0xffffffffu, excl, lo);
+            ou[k] = __shfl_sync(0xffffffffu, u, lo);
+            v[k] = (e < total) ? __ldg(a.ir + ob + (int64_t)(e - oe)) : -1;
         }
-        const int64_t ob = __shfl_sync(0xffffffffu, beg, lo);
-        const uint32_t oe = __shfl_sync(0xffffffffu, excl, lo);
-        const int32_t ou = __shfl_sync(0xffffffffu, u, lo);
-        if (e < total) vis(a, __ldg(a.ir + ob + (int64_t)(e - oe)), ou);
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0) ? vis.probe(a, v[k]) : 0u;
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0 && vis.fresh(v[k], w[k])) ? (a.dedup ? vis.seen(a, v[k]) : 0xffffffffu) : 0u;
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k)
+            if (v[k] >= 0) vis.mark(a, v[k], ou[k], w[k]);
     }
 }
 
@@ -383,7 +422,7 @@ __device__ __forceinline__ void row_affine(const LevelArgs& a, unsigned long lon
                                            int* s_row) {
     const int p = a.p;
     int tried = 0;
-    int start = blockIdx.x % p;
+    int start = a.sweep ? 0 : blockIdx.x % p;
     auto pick = [&](int from) -> int {          // thread 0: next row with units, or -1
         while (tried < p) {
             const int r = from;
@@ -582,32 +621,6 @@ __global__ void __launch_bounds__(kXT, 1) expand_pieces(LevelArgs a) {
     row_affine<WIN>(a, a.row_piece_next, 1, units_in_row, do_unit, s_pi, s_t, s_row);
 }
 
-// Per stream: group base of every chunk of 32 words.  One CTA per stream;
-// thread t holds 4 consecutive words of a 1024-word tile, so threads 8m..8m+7
-// cover chunk m of the tile and thread 8m's exclusive prefix is its base.
-template <typename W>
-__global__ void __launch_bounds__(kNT) stream_chunks(LevelArgs a, int nstreams) {
-    __shared__ unsigned long long red[kNT / 32 + 1];
-    const int s = blockIdx.x;
-    if (s >= nstreams) return;
-    const W* in = static_cast<const W*>(a.xbuf) + (int64_t)s * a.slot_cap;
-    const int64_t count = a.xcount[s];
-    unsigned long long gpos = 0;
-    for (int64_t t0 = 0; t0 < count; t0 += 4 * kNT) {
-        const int64_t x0 = t0 + 4 * (int64_t)threadIdx.x;
-        unsigned long long g = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (x0 + k < count) g += word_groups<W>(in[x0 + k]);
-        unsigned long long tot;
-        const unsigned long long ex = block_excl_scan<kNT>(g, 0ull, OpSum(), red, &tot);
-        if ((threadIdx.x & 7) == 0 && x0 < count)
-            a.chunk_base[(int64_t)s * a.chunks_per_slot + x0 / 32] = (int64_t)(gpos + ex);
-        gpos += tot;
-    }
-    if (threadIdx.x == 0) atomicAdd(a.ctr + C_WAH_WORDS, (unsigned long long)count);
-}
-
 // Units of every slot (block (i,j) decodes stream s = i*p+j, or stream j in
 // COMPRESS mode): exclusive scan of 32-word chunk counts over the slots, row-major.
 __global__ void __launch_bounds__(kNT) plan_units(LevelArgs a) {
@@ -761,6 +774,17 @@ int sm_count() {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
         cached = v > 0 ? v : 1;
+    }
+    return cached;
+}
+
+int64_t l2_bytes() {
+    static int64_t cached = 0;
+    if (!cached) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev);
+        cached = v > 0 ? v : (64ll << 20);
     }
     return cached;
 }
@@ -948,6 +972,11 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     a.plain_upb = (L.nb + 1023) / 1024;               // 32 raw words per PLAIN unit
     a.win_words = W.win_words;
     a.row_exchange = rowx ? 1 : 0;
+    // Without a window the visited test, the next bit and the parent update
+    // go through L2.  When the parent array does not fit in half of L2, all
+    // CTAs take the block-rows in turn, so that only one row's slice of it
+    // (and of pi and t) is being updated at a time.
+    a.sweep = (!win && 4 * L.n > l2_bytes() / 2) ? 1 : 0;
     a.rowbuf = W.rowbuf.as<uint32_t>();
     a.rowbuf_cap = W.rowbuf_cap;
     a.rowbuf_slots = W.rowbuf_slots;
@@ -968,10 +997,14 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     ea.out = W.xbuf.ptr;
     ea.slot_cap = slot_cap;
     ea.counts = W.xcount.as<int64_t>();
+    ea.unit_base = W.chunk_base.as<int64_t>();      // the decoder's unit bases, written by the encoder
+    ea.unit_stride = W.chunks_per_slot;
+    ea.wah_words = ctr + C_WAH_WORDS;
 
     uint32_t* f = W.fa.as<uint32_t>();
     uint32_t* t = W.fb.as<uint32_t>();
     int64_t frontier = 1;
+    int64_t visited = 1;
     int64_t raw_bytes = 0;
     for (int j = 0; j < p; ++j) raw_bytes += 4 * ((L.range_len(j) + 31) / 32);
     raw_bytes *= p;
@@ -987,6 +1020,11 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         // PLAIN scans every raw word of every block: hand out many units at a
         // time on sparse levels (few items each), few on dense ones (balance)
         a.plain_batch = (frontier * 64 < L.n) ? 32 : 2;
+        // While few vertices are visited, most entries lead to fresh vertices,
+        // each reached from many frontier vertices: reading the parent first
+        // turns most of those visits into one L2 read instead of two atomics.
+        // With a window the next bit is a shared-memory atomic: not worth it.
+        a.dedup = (!win && visited * 16 < L.n) ? 1 : 0;
         ea.frontier = f;
         if (timing) cudaEventRecord(W.ev[0], st);
         if (mode == BFS_MODE_PLAIN) {
@@ -998,9 +1036,6 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             BFS_TRY(launch_wah_encode_parallel(ea, wbits, W.enc_sums.ptr, W.enc_bases.ptr, W.enc_cps,
                                                W.enc_flags.ptr, W.enc_list.ptr, ctr + C_ENC_LIST, ctr + C_EXCHANGED,
                                                sm_count() * 8, st));
-            if (wbits == 32) stream_chunks<uint32_t><<<nslots, kNT, 0, st>>>(a, nslots);
-            else stream_chunks<unsigned long long><<<nslots, kNT, 0, st>>>(a, nslots);
-            BFS_CUDA_TRY(cudaGetLastError());
             plan_units<<<1, kNT, 0, st>>>(a);
             BFS_CUDA_TRY(cudaGetLastError());
             if (timing) cudaEventRecord(W.ev[1], st);
@@ -1070,6 +1105,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             if (tracing) stats->trace_used = (int64_t)h[C_TRACE_USED];
         }
         frontier = (int64_t)h[C_NEXT_COUNT];
+        visited += frontier;
         if (frontier == 0) break;
         std::swap(f, t);
     }

@@ -159,6 +159,9 @@ struct EncodeArgs {
     void* out;
     int64_t slot_cap;
     int64_t* counts;
+    int64_t* unit_base;         // or nullptr: group start of every word 32k of slot s at [s * unit_stride + k]
+    int64_t unit_stride;
+    unsigned long long* wah_words;   // or nullptr: words of all slots are added here
 };
 bfs_status launch_wah_encode(const EncodeArgs& a, int wah_bits, cudaStream_t st);
 

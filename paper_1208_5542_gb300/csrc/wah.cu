@@ -205,16 +205,79 @@ __global__ void __launch_bounds__(kNT) wah_encode_kernel(EncodeArgs a, unsigned 
 // (slot, chunk of kTile groups):
 //   0. enc_chunk_flags: one thread per chunk tests the frontier summary and
 //      appends the chunks with any frontier bit to a work list;
-//   1. enc_chunk_sums: per listed chunk, its head count (its first group
-//      counted as a head), first and last group type and last head position;
+//   1. enc_chunk_sums: one warp per listed chunk, 32 groups per step: its
+//      head count (its first group counted as a head), first and last group
+//      type and last head position, from ballots of the head flags;
 //   2. enc_chunk_scan: per slot, one warp scans the chunk sums (an all-zero
 //      chunk is one zero run): a chunk whose first group continues the previous
 //      chunk's fill run merges with it; this gives every chunk its first word
 //      index and the start of the run it opens with, the slot's word count and
 //      the active word, and writes the fill word of every zero run that ends
 //      in an all-zero chunk;
-//   3. enc_chunk_write: per listed chunk, the tile body of the sequential
-//      encoder with the carry taken from pass 2.
+//   3. enc_chunk_write: one warp per listed chunk writes its words, each
+//      lane's word index and run start taken from the ballot of the head flags
+//      and the chunk's carry from pass 2.
+// With unit_base set, the group at which every 32nd word opens is recorded
+// as the word is written (the decoder's unit bases).
+constexpr int kU = 8;             // 32-group steps whose loads a warp issues together
+
+// Groups gb + 32k + lane (k < kU) of a slot, 0 at and beyond group G.  For
+// 31-bit groups a step of 32 groups is exactly 31 words of the directory and
+// at most 32 words of the frontier: every lane loads one word of each
+// (coalesced), and its group is funnel-shifted from the two words it spans,
+// fetched by shuffles.  The directory is not read when the frontier words of
+// all kU steps are zero.  63-bit groups are read per lane.
+template <typename W>
+__device__ __forceinline__ void warp_groups(const EncodeArgs& a, const SlotGeom& sg, int64_t gb, int64_t G,
+                                            W (&x)[kU]) {
+    const int lane = (int)lane_id();
+    if constexpr (sizeof(W) == 4) {
+        uint32_t fw[kU], dw[kU];
+        const int64_t last = G * 31;                                // bits of the full groups
+        const int64_t fmax = last > 0 ? (sg.src0 + last - 1) >> 5 : -1;
+        const int64_t dmax = last > 0 ? (last - 1) >> 5 : -1;
+        const int64_t p0 = sg.src0 + gb * 31;
+        const uint32_t sh0 = (uint32_t)(p0 & 31);
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int64_t w = (p0 >> 5) + 31 * k + lane;
+            fw[k] = (w <= fmax) ? __ldg(a.frontier + w) : 0u;
+            any |= fw[k] != 0u;
+        }
+        const bool sieve = sg.dirb != nullptr;
+        const bool need_dir = sieve && __any_sync(0xffffffffu, any);
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int64_t w = ((gb * 31) >> 5) + 31 * k + lane;
+            dw[k] = (need_dir && lane < 31 && w <= dmax) ? __ldg(sg.dirb + w) : 0u;
+        }
+        const uint32_t rel = 31u * (uint32_t)lane + sh0;
+        const int fa = (int)(rel >> 5), fb = fa + 1 < 32 ? fa + 1 : 31;
+        const int da = (31 * lane) >> 5;
+        const uint32_t dsh = (31u * (uint32_t)lane) & 31u;
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const uint32_t lo = __shfl_sync(0xffffffffu, fw[k], fa);
+            const uint32_t hi = __shfl_sync(0xffffffffu, fw[k], fb);
+            uint32_t v = __funnelshift_r(lo, hi, rel & 31u) & 0x7fffffffu;
+            if (sieve) {
+                const uint32_t dlo = __shfl_sync(0xffffffffu, dw[k], da);
+                const uint32_t dhi = __shfl_sync(0xffffffffu, dw[k], da + 1);
+                v &= __funnelshift_r(dlo, dhi, dsh) & 0x7fffffffu;
+            }
+            x[k] = (gb + 32 * k + lane < G) ? (W)v : W(0);
+        }
+    } else {
+        const SlotGeom g = sg;
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int64_t gi = gb + 32 * k + lane;
+            x[k] = (gi < G) ? load_group<W>(a, g, gi) : W(0);
+        }
+    }
+}
+
 struct ChunkSum {
     uint32_t heads;
     uint32_t types;        // first type | last type << 8
@@ -263,12 +326,12 @@ __global__ void __launch_bounds__(kNT) enc_chunk_sums(EncodeArgs a, ChunkSum* su
                                                       unsigned long long* setbits) {
     using T = Wah<W>;
     constexpr int GB = T::GB;
-    __shared__ uint8_t sm_last[kNT];
-    __shared__ int64_t sm64[kNT / 32 + 1];
-    __shared__ unsigned long long smu[kNT / 32 + 1];
-    __shared__ int sm_first_type, sm_last_type;
     const unsigned long long n = *nlist;
-    for (unsigned long long li = blockIdx.x; li < n; li += gridDim.x) {
+    const int lane = (int)lane_id();
+    const unsigned long long wid = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long ones = 0;
+    for (unsigned long long li = wid; li < n; li += nw) {
         const int64_t q = list[li];
         const int s = (int)(q / cps);
         const int64_t c = q % cps;
@@ -276,46 +339,40 @@ __global__ void __launch_bounds__(kNT) enc_chunk_sums(EncodeArgs a, ChunkSum* su
         const int64_t G = sg.nbits / GB;
         const int64_t tb = c * kTile;
         const int64_t tend = (tb + kTile < G) ? tb + kTile : G;
-        const int64_t g0 = tb + (int64_t)threadIdx.x * kK;
-        int ty[kK];
-        unsigned long long ones = 0;
+        int prev = -1, first = G_NONE;
+        uint32_t heads = 0;
+        int64_t last_head = -1;
+        for (int64_t gb = tb; gb < tend; gb += 32 * kU) {
+            W x[kU];                  // the loads of kU steps are issued together
+            warp_groups<W>(a, sg, gb, tend, x);
 #pragma unroll
-        for (int k = 0; k < kK; ++k) {
-            const int64_t g = g0 + k;
-            if (g < tend) {
-                const W x = load_group<W>(a, sg, g);
-                ty[k] = group_type<W>(x);
-                ones += (unsigned long long)T::popc(x);
-                if (g == tb) sm_first_type = ty[k];
-                if (g + 1 == tend) sm_last_type = ty[k];
-            } else {
-                ty[k] = G_NONE;
+            for (int k = 0; k < kU; ++k) {
+                const int64_t g0 = gb + 32 * k;
+                if (g0 >= tend) break;
+                const bool valid = g0 + lane < tend;
+                const int ty = valid ? group_type<W>(x[k]) : G_NONE;
+                ones += (unsigned long long)T::popc(x[k]);
+                int pt = __shfl_up_sync(0xffffffffu, ty, 1);
+                if (lane == 0) pt = prev;
+                const uint32_t b = __ballot_sync(0xffffffffu, valid && (ty == G_LIT || ty != pt));
+                heads += __popc(b);
+                if (b) last_head = g0 + 31 - __clz(b);
+                if (g0 == tb) first = __shfl_sync(0xffffffffu, ty, 0);
+                const int lv = (tend - g0 < 32) ? (int)(tend - g0 - 1) : 31;
+                prev = __shfl_sync(0xffffffffu, ty, lv);
             }
         }
-        sm_last[threadIdx.x] = (uint8_t)ty[kK - 1];
-        __syncthreads();
-        int pt = (threadIdx.x == 0) ? -1 : (int)sm_last[threadIdx.x - 1];
-        int64_t hc = 0, lastpos = -1;
-#pragma unroll
-        for (int k = 0; k < kK; ++k) {
-            const bool h = (ty[k] != G_NONE) && (ty[k] == G_LIT || ty[k] != pt);
-            if (h) { ++hc; lastpos = g0 + k; }
-            pt = ty[k];
-        }
-        int64_t heads, lasth;
-        block_excl_scan<kNT>(hc, (int64_t)0, OpSum(), sm64, &heads);
-        block_excl_scan<kNT>(lastpos, (int64_t)-1, OpMax(), sm64, &lasth);
-        unsigned long long tot_ones;
-        block_excl_scan<kNT>(ones, 0ull, OpSum(), smu, &tot_ones);
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             ChunkSum cs;
-            cs.heads = (uint32_t)heads;
-            cs.types = (uint32_t)sm_first_type | ((uint32_t)sm_last_type << 8);
-            cs.last_head = lasth;
+            cs.heads = heads;
+            cs.types = (uint32_t)first | ((uint32_t)prev << 8);
+            cs.last_head = last_head;
             sums[q] = cs;
-            if (setbits && tot_ones) atomicAdd(setbits, tot_ones);
         }
-        __syncthreads();
+    }
+    if (setbits) {
+        ones = warp_sum(ones);
+        if (lane == 0 && ones) atomicAdd(setbits, ones);
     }
 }
 
@@ -332,6 +389,7 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
     const int64_t nch = (G + kTile - 1) / kTile;
     const int lane = (int)lane_id();
     W* out = static_cast<W*>(a.out) + (int64_t)s * a.slot_cap;
+    int64_t* ub = a.unit_base ? a.unit_base + (int64_t)s * a.unit_stride : nullptr;
     auto sum_of = [&](int64_t c) -> ChunkSum {
         ChunkSum cs;
         if (flags[(int64_t)s * cps + c]) return sums[(int64_t)s * cps + c];
@@ -375,11 +433,14 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
             else if (lane == 31) nxt = (int)(sum_of(c + 1).types & 0xff);
             cb.next_type = nxt;
             bases[(int64_t)s * cps + c] = cb;
-            if (!flags[(int64_t)s * cps + c] && nxt != G_ZERO) {
-                // the zero run through this all-zero chunk ends at its last group
-                const int64_t tend = ((c + 1) * kTile < G) ? (c + 1) * kTile : G;
-                const int64_t start = merge ? cb.run_start : c * kTile;
-                out[merge ? cb.words - 1 : cb.words] = fill_word<W>(G_ZERO, (uint64_t)(tend - start));
+            if (!flags[(int64_t)s * cps + c]) {
+                // an all-zero chunk: its zero run opens a word here unless it merges
+                if (!merge && ub && (cb.words & 31) == 0) ub[cb.words >> 5] = c * kTile;
+                if (nxt != G_ZERO) {     // the run ends at the chunk's last group
+                    const int64_t tend = ((c + 1) * kTile < G) ? (c + 1) * kTile : G;
+                    const int64_t start = merge ? cb.run_start : c * kTile;
+                    out[merge ? cb.words - 1 : cb.words] = fill_word<W>(G_ZERO, (uint64_t)(tend - start));
+                }
             }
         }
         words += __shfl_sync(0xffffffffu, incl, 31);
@@ -395,9 +456,11 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
             W y = T::tail(a.frontier, pos, r);
             if (sg.dirb && y) y &= T::tail(sg.dirb, (uint64_t)(G * GB), r);
             if (setbits && y) atomicAdd(setbits, (unsigned long long)T::popc(y));
+            if (ub && (total & 31) == 0) ub[total >> 5] = G;
             out[total++] = T::to_active(y, r);
         }
         a.counts[s] = total;
+        if (a.wah_words) atomicAdd(a.wah_words, (unsigned long long)total);
     }
 }
 
@@ -406,10 +469,12 @@ __global__ void __launch_bounds__(kNT) enc_chunk_write(EncodeArgs a, const Chunk
                                                        const int64_t* list, const unsigned long long* nlist) {
     using T = Wah<W>;
     constexpr int GB = T::GB;
-    __shared__ int64_t sm64[kNT / 32 + 1];
-    __shared__ uint8_t sm_first[kNT], sm_last[kNT];
     const unsigned long long n = *nlist;
-    for (unsigned long long li = blockIdx.x; li < n; li += gridDim.x) {
+    const int lane = (int)lane_id();
+    const uint32_t le_mask = 0xffffffffu >> (31 - lane);        // lanes 0..lane
+    const unsigned long long wid = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long li = wid; li < n; li += nw) {
         const int64_t q = list[li];
         const int s = (int)(q / cps);
         const int64_t c = q % cps;
@@ -419,52 +484,45 @@ __global__ void __launch_bounds__(kNT) enc_chunk_write(EncodeArgs a, const Chunk
         const int64_t tend = (tb + kTile < G) ? tb + kTile : G;
         const ChunkBase cb = bases[q];
         W* out = static_cast<W*>(a.out) + (int64_t)s * a.slot_cap;
-        const int64_t g0 = tb + (int64_t)threadIdx.x * kK;
-        W x[kK];
-        int ty[kK];
+        int64_t* ub = a.unit_base ? a.unit_base + (int64_t)s * a.unit_stride : nullptr;
+        int64_t base = cb.words;          // next word to open
+        int64_t run_start = cb.run_start;
+        int prev = cb.prev_type;
+        for (int64_t gb = tb; gb < tend; gb += 32 * kU) {
+            W x[kU];
+            int tys[kU];
+            warp_groups<W>(a, sg, gb, tend, x);
 #pragma unroll
-        for (int k = 0; k < kK; ++k) {
-            const int64_t g = g0 + k;
-            if (g < tend) {
-                x[k] = load_group<W>(a, sg, g);
-                ty[k] = group_type<W>(x[k]);
-            } else {
-                x[k] = W(0);
-                ty[k] = G_NONE;
+            for (int k = 0; k < kU; ++k) tys[k] = (gb + 32 * k + lane < tend) ? group_type<W>(x[k]) : G_NONE;
+#pragma unroll
+            for (int k = 0; k < kU; ++k) {
+                const int64_t g0 = gb + 32 * k;
+                if (g0 >= tend) break;
+                const int64_t g = g0 + lane;
+                const bool valid = g < tend;
+                const int ty = tys[k];
+                int pt = __shfl_up_sync(0xffffffffu, ty, 1);
+                if (lane == 0) pt = prev;
+                const bool h = valid && (ty == G_LIT || ty != pt);
+                const uint32_t b = __ballot_sync(0xffffffffu, h);
+                int nt = __shfl_down_sync(0xffffffffu, ty, 1);
+                const int nt31 = (k + 1 < kU) ? __shfl_sync(0xffffffffu, tys[k + 1 < kU ? k + 1 : k], 0) : G_NONE;
+                if (valid) {
+                    const uint32_t bl = b & le_mask;
+                    const int64_t widx = base + __popc(bl) - 1;
+                    const int64_t start = bl ? g0 + 31 - __clz(bl) : run_start;
+                    if (g + 1 == tend) nt = cb.next_type;
+                    else if (lane == 31) nt = (k + 1 < kU) ? nt31 : group_type<W>(load_group<W>(a, sg, g + 1));
+                    if (ty == G_LIT) out[widx] = T::to_payload(x[k]);
+                    else if (nt != ty) out[widx] = fill_word<W>(ty, (uint64_t)(g - start + 1));
+                    if (h && ub && (widx & 31) == 0) ub[widx >> 5] = g;
+                }
+                base += __popc(b);
+                if (b) run_start = g0 + 31 - __clz(b);
+                const int lv = (tend - g0 < 32) ? (int)(tend - g0 - 1) : 31;
+                prev = __shfl_sync(0xffffffffu, ty, lv);
             }
         }
-        sm_first[threadIdx.x] = (uint8_t)ty[0];
-        sm_last[threadIdx.x] = (uint8_t)ty[kK - 1];
-        __syncthreads();
-        const int prev0 = (threadIdx.x == 0) ? cb.prev_type : (int)sm_last[threadIdx.x - 1];
-        bool h[kK];
-        int hc = 0;
-        int64_t lastpos = -1;
-        int pt = prev0;
-#pragma unroll
-        for (int k = 0; k < kK; ++k) {
-            h[k] = (ty[k] != G_NONE) && (ty[k] == G_LIT || ty[k] != pt);
-            if (h[k]) { ++hc; lastpos = g0 + k; }
-            pt = ty[k];
-        }
-        int64_t tot_h, dummy;
-        const int64_t excl_h = block_excl_scan<kNT>((int64_t)hc, (int64_t)0, OpSum(), sm64, &tot_h);
-        const int64_t excl_pos = block_excl_scan<kNT>(lastpos, (int64_t)-1, OpMax(), sm64, &dummy);
-        int64_t cur_start = excl_pos > cb.run_start ? excl_pos : cb.run_start;
-        int64_t widx = cb.words + excl_h - 1;
-#pragma unroll
-        for (int k = 0; k < kK; ++k) {
-            const int64_t g = g0 + k;
-            if (ty[k] == G_NONE) break;
-            if (h[k]) { cur_start = g; ++widx; }
-            int nt;
-            if (k + 1 < kK) nt = ty[k + 1];
-            else nt = (threadIdx.x + 1 < kNT) ? (int)sm_first[threadIdx.x + 1] : G_NONE;
-            if (g + 1 == tend) nt = cb.next_type;
-            if (ty[k] == G_LIT) out[widx] = T::to_payload(x[k]);
-            else if (nt != ty[k]) out[widx] = fill_word<W>(ty[k], (uint64_t)(g - cur_start + 1));
-        }
-        __syncthreads();
     }
 }
 
