@@ -40,8 +40,7 @@ bfs_status launch_wah_encode_counted(const EncodeArgs& a, int wah_bits, unsigned
                                      cudaStream_t st);
 int64_t parallel_encode_chunks(int64_t max_nbits, int wah_bits);
 bfs_status launch_wah_encode_parallel(const EncodeArgs& a, int wah_bits, void* sums, void* bases, int64_t cps,
-                                      void* flags, void* list, unsigned long long* nlist, unsigned long long* setbits,
-                                      int grid, cudaStream_t st);
+                                      void* flags, unsigned long long* setbits, int grid, cudaStream_t st);
 size_t parallel_encode_sum_bytes();
 size_t parallel_encode_base_bytes();
 
@@ -621,30 +620,6 @@ __global__ void __launch_bounds__(kXT, 1) expand_pieces(LevelArgs a) {
     row_affine<WIN>(a, a.row_piece_next, 1, units_in_row, do_unit, s_pi, s_t, s_row);
 }
 
-// Units of every slot (block (i,j) decodes stream s = i*p+j, or stream j in
-// COMPRESS mode): exclusive scan of 32-word chunk counts over the slots, row-major.
-__global__ void __launch_bounds__(kNT) plan_units(LevelArgs a) {
-    __shared__ unsigned long long red[kNT / 32 + 1];
-    const int64_t nslots = (int64_t)a.p * a.p;
-    unsigned long long carry = 0;
-    for (int64_t s0 = 0; s0 < nslots; s0 += kNT) {
-        const int64_t s = s0 + threadIdx.x;
-        unsigned long long nch = 0;
-        if (s < nslots) {
-            const int64_t stream = (a.mode == BFS_MODE_COMPRESS_SIEVE) ? s : s % a.p;
-            nch = (unsigned long long)((a.xcount[stream] + 31) / 32);
-        }
-        unsigned long long tot;
-        const unsigned long long ex = block_excl_scan<kNT>(nch, 0ull, OpSum(), red, &tot);
-        if (s < nslots) a.slot_unit_base[s] = (int64_t)(carry + ex);
-        carry += tot;
-    }
-    if (threadIdx.x == 0) {
-        a.slot_unit_base[nslots] = (int64_t)carry;
-        a.ctr[C_UNITS] = carry;
-    }
-}
-
 // The fold of the compressed row exchange: one CTA per row buffer OR-decodes it
 // into t at its row's first bit.
 __global__ void __launch_bounds__(kXT) fold_rows(LevelArgs a) {
@@ -828,7 +803,8 @@ bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
     BFS_TRY(W.enc_sums.alloc(parallel_encode_sum_bytes() * p2 * W.enc_cps));
     BFS_TRY(W.enc_bases.alloc(parallel_encode_base_bytes() * p2 * W.enc_cps));
     BFS_TRY(W.enc_flags.alloc(p2 * W.enc_cps));
-    BFS_TRY(W.enc_list.alloc(sizeof(int64_t) * p2 * W.enc_cps));
+    BFS_TRY(W.enc_done.alloc(sizeof(unsigned int)));
+    BFS_CUDA_TRY(cudaMemset(W.enc_done.ptr, 0, sizeof(unsigned int)));
     BFS_TRY(W.counters.alloc(sizeof(unsigned long long) * C_NUM));
     // pieces: per row, sum over long columns of ceil(len/kPiece) <= nnz_row/kPiece + nnz_row/kHub
     std::vector<int64_t> meta(2 * (size_t)p);
@@ -876,7 +852,7 @@ void free_workspace(bfs_graph* g) {
     W.xcount.release(); W.chunk_base.release(); W.units.release(); W.counters.release(); W.pieces.release();
     W.level_scratch.release(); W.row_meta.release();
     W.rowbuf.release(); W.rowbuf_row.release(); W.rowbuf_words.release();
-    W.enc_sums.release(); W.enc_bases.release(); W.enc_flags.release(); W.enc_list.release();
+    W.enc_sums.release(); W.enc_bases.release(); W.enc_flags.release(); W.enc_done.release();
     W.tmp_parent.release(); W.tmp_level.release();
     if (W.h_counters) cudaFreeHost(W.h_counters);
     W.h_counters = nullptr;
@@ -1000,6 +976,10 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     ea.unit_base = W.chunk_base.as<int64_t>();      // the decoder's unit bases, written by the encoder
     ea.unit_stride = W.chunks_per_slot;
     ea.wah_words = ctr + C_WAH_WORDS;
+    ea.plan_base = W.units.as<int64_t>();            // the unit plan, laid out by the encoder's scan
+    ea.plan_units = ctr + C_UNITS;
+    ea.plan_done = W.enc_done.as<unsigned int>();
+    ea.frontier_words = W.bm_words;
 
     uint32_t* f = W.fa.as<uint32_t>();
     uint32_t* t = W.fb.as<uint32_t>();
@@ -1034,10 +1014,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             BFS_CUDA_TRY(cudaGetLastError());
         } else {
             BFS_TRY(launch_wah_encode_parallel(ea, wbits, W.enc_sums.ptr, W.enc_bases.ptr, W.enc_cps,
-                                               W.enc_flags.ptr, W.enc_list.ptr, ctr + C_ENC_LIST, ctr + C_EXCHANGED,
-                                               sm_count() * 8, st));
-            plan_units<<<1, kNT, 0, st>>>(a);
-            BFS_CUDA_TRY(cudaGetLastError());
+                                               W.enc_flags.ptr, ctr + C_EXCHANGED, sm_count() * 6, st));
             if (timing) cudaEventRecord(W.ev[1], st);
             if (tracing && k < stats->capacity_levels) {
                 const int u32pw = wbits / 32;

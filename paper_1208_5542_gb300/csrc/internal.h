@@ -89,7 +89,6 @@ enum Counter : int {
     C_EXCHANGED,         // set bits carried by the exchange
     C_PIECES,            // pieces of long columns queued for the piece kernel
     C_ROW_WORDS,         // WAH words of the compressed row exchange
-    C_ENC_LIST,          // chunks listed for the parallel encoder
     C_DBG,               // first failed invariant: 6 slots of context (see bfs_level.cu)
     C_NUM = C_DBG + 6
 };
@@ -111,7 +110,8 @@ struct Workspace {
     int64_t win_words = 0;      // shared-memory row window of the expansion (0: none)
     DevBuf rowbuf, rowbuf_row, rowbuf_words;   // compressed row exchange
     DevBuf enc_sums, enc_bases;  // chunk summaries of the parallel encoder
-    DevBuf enc_flags, enc_list;  // chunks with frontier bits, and their list
+    DevBuf enc_flags;            // chunks with frontier bits
+    DevBuf enc_done;             // slots finished by the encoder's scan
     int64_t enc_cps = 0;         // encoder chunks per slot
     int64_t rowbuf_cap = 0, rowbuf_slots = 0;
     DevBuf tmp_parent, tmp_level;      // for searches with host outputs
@@ -149,6 +149,7 @@ void free_workspace(bfs_graph* g);
 // wah.cu
 struct EncodeArgs {
     const uint32_t* frontier;   // bitmap read by the encoder
+    int64_t frontier_words;     // its readable words (a multiple of 4)
     const uint32_t* dir;        // directories (sieve) or nullptr
     int64_t dir_stride;
     int p;
@@ -162,6 +163,9 @@ struct EncodeArgs {
     int64_t* unit_base;         // or nullptr: group start of every word 32k of slot s at [s * unit_stride + k]
     int64_t unit_stride;
     unsigned long long* wah_words;   // or nullptr: words of all slots are added here
+    int64_t* plan_base;         // or nullptr: the decoder's units per block, p*p + 1 entries
+    unsigned long long* plan_units;  // their total
+    unsigned int* plan_done;    // slots finished (zero between uses)
 };
 bfs_status launch_wah_encode(const EncodeArgs& a, int wah_bits, cudaStream_t st);
 

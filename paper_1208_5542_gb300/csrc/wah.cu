@@ -201,20 +201,21 @@ __global__ void __launch_bounds__(kNT) wah_encode_kernel(EncodeArgs a, unsigned 
 }
 
 // ------------------------------------------------- parallel slot encoder --
-// The same stream as wah_encode_kernel, built in data-parallel passes over
-// (slot, chunk of kTile groups):
-//   0. enc_chunk_flags: one thread per chunk tests the frontier summary and
-//      appends the chunks with any frontier bit to a work list;
-//   1. enc_chunk_sums: one warp per listed chunk, 32 groups per step: its
-//      head count (its first group counted as a head), first and last group
-//      type and last head position, from ballots of the head flags;
+// The same stream as wah_encode_kernel, built in three data-parallel passes
+// over (slot, chunk of kTile groups):
+//   1. enc_chunk_sums: one warp per chunk tests the frontier summary (a chunk
+//      without frontier bits is flagged all-zero and not read) and, for the
+//      others, takes 32 groups per step: head count (its first group counted
+//      as a head), first and last group type and last head position, from
+//      ballots of the head flags;
 //   2. enc_chunk_scan: per slot, one warp scans the chunk sums (an all-zero
 //      chunk is one zero run): a chunk whose first group continues the previous
 //      chunk's fill run merges with it; this gives every chunk its first word
 //      index and the start of the run it opens with, the slot's word count and
 //      the active word, and writes the fill word of every zero run that ends
-//      in an all-zero chunk;
-//   3. enc_chunk_write: one warp per listed chunk writes its words, each
+//      in an all-zero chunk.  The last slot to finish (a counter, no waiting)
+//      lays out the decoder's units over all slots;
+//   3. enc_chunk_write: one warp per flagged chunk writes its words, each
 //      lane's word index and run start taken from the ballot of the head flags
 //      and the chunk's carry from pass 2.
 // With unit_base set, the group at which every 32nd word opens is recorded
@@ -278,6 +279,77 @@ __device__ __forceinline__ void warp_groups(const EncodeArgs& a, const SlotGeom&
     }
 }
 
+// 31-bit groups of a whole chunk, staged in shared memory: the warp copies
+// the chunk's frontier words and directory words with asynchronous 16-byte
+// copies (all in flight together; one round trip per chunk), then every
+// group is two shared-memory words funnel-shifted.
+constexpr int kEW = 128;          // threads per staging encoder CTA (4 warps)
+constexpr int kStageWords = 1060; // >= the words of one chunk (1024 x 31 bits) + alignment and funnel slack,
+                                  // and >= the padded output words of a chunk (the frontier buffer is reused)
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+struct Stage32 {
+    const uint32_t* f;     // frontier words from a 16-byte boundary at or before group tb
+    const uint32_t* d;     // directory words from group tb (or nullptr: no sieve)
+    uint32_t off;          // bit of group tb in f
+    int64_t tb;
+};
+
+__device__ __forceinline__ Stage32 stage_chunk(const EncodeArgs& a, const SlotGeom& sg, int64_t tb, int64_t tend,
+                                               uint32_t* fbuf, uint32_t* dbuf) {
+    const int lane = (int)lane_id();
+    const int64_t fbit0 = sg.src0 + 31 * tb;
+    const int64_t fw0 = (fbit0 >> 5) & ~(int64_t)3;
+    const int64_t flast = ((sg.src0 + 31 * tend - 1) >> 5) + 1;    // the upper funnel word of the last group
+    int64_t fend = (flast + 1 + 3) & ~(int64_t)3;
+    if (fend > a.frontier_words) fend = a.frontier_words;
+    for (int64_t i = lane; 4 * i < fend - fw0; i += 32) cp_async16(fbuf + 4 * i, a.frontier + fw0 + 4 * i);
+    Stage32 st;
+    st.f = fbuf;
+    st.off = (uint32_t)(fbit0 - 32 * fw0);
+    st.tb = tb;
+    st.d = nullptr;
+    if (sg.dirb) {
+        const int64_t dw0 = (31 * tb) >> 5;                          // tb is a multiple of 1024: 16-byte aligned
+        const int64_t dlast = ((31 * tend - 1) >> 5) + 1;
+        int64_t dend = (dlast + 1 + 3) & ~(int64_t)3;
+        if (dend > a.dir_stride) dend = a.dir_stride;
+        for (int64_t i = lane; 4 * i < dend - dw0; i += 32) cp_async16(dbuf + 4 * i, sg.dirb + dw0 + 4 * i);
+        st.d = dbuf;
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+    return st;
+}
+
+__device__ __forceinline__ uint32_t staged_group(const Stage32& st, int64_t g) {
+    const uint32_t r = (uint32_t)(g - st.tb) * 31u;
+    const uint32_t fr = st.off + r;
+    uint32_t x = __funnelshift_r(st.f[fr >> 5], st.f[(fr >> 5) + 1], fr & 31u) & 0x7fffffffu;
+    if (st.d) x &= __funnelshift_r(st.d[r >> 5], st.d[(r >> 5) + 1], r & 31u);
+    return x;
+}
+
+// Groups gb + 32k + lane (k < kU) of the chunk, 0 at and beyond tend.
+template <typename W>
+__device__ __forceinline__ void chunk_groups(const EncodeArgs& a, const SlotGeom& sg, const Stage32& st, int64_t gb,
+                                             int64_t tend, W (&x)[kU]) {
+    if constexpr (sizeof(W) == 4) {
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int64_t g = gb + 32 * k + lane_id();
+            x[k] = (g < tend) ? (W)staged_group(st, g) : W(0);
+        }
+    } else {
+        warp_groups<W>(a, sg, gb, tend, x);
+    }
+}
+
 struct ChunkSum {
     uint32_t heads;
     uint32_t types;        // first type | last type << 8
@@ -291,60 +363,51 @@ struct ChunkBase {
 };
 
 template <typename W>
-__global__ void enc_chunk_flags(EncodeArgs a, int64_t cps, uint8_t* flags, int64_t* list,
-                                unsigned long long* nlist) {
-    constexpr int GB = Wah<W>::GB;
-    const int64_t total = (int64_t)a.nslots * cps;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q - (int64_t)lane_id() < total;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        bool live = false;
-        if (q < total) {
-            const int s = (int)(q / cps);
-            const int64_t c = q % cps;
-            const SlotGeom sg = slot_geom(a, s);
-            const int64_t G = sg.nbits / GB;
-            const int64_t tb = c * kTile;
-            if (tb < G) {
-                const int64_t tend = (tb + kTile < G) ? tb + kTile : G;
-                live = !a.fsum || !fsum_zero(a.fsum, (sg.src0 + tb * GB) >> 10, (sg.src0 + tend * GB - 1) >> 10);
-            }
-            flags[q] = live ? 1 : 0;
-        }
-        const uint32_t ball = __ballot_sync(0xffffffffu, live);
-        if (ball) {
-            unsigned long long base = 0;
-            if (lane_id() == 0) base = atomicAdd(nlist, (unsigned long long)__popc(ball));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (live) list[base + __popc(ball & ((1u << lane_id()) - 1u))] = q;
-        }
-    }
-}
-
-template <typename W>
-__global__ void __launch_bounds__(kNT) enc_chunk_sums(EncodeArgs a, ChunkSum* sums, int64_t cps,
-                                                      const int64_t* list, const unsigned long long* nlist,
+__global__ void __launch_bounds__(kEW) enc_chunk_sums(EncodeArgs a, ChunkSum* sums, uint8_t* flags, int64_t cps,
                                                       unsigned long long* setbits) {
     using T = Wah<W>;
     constexpr int GB = T::GB;
-    const unsigned long long n = *nlist;
+    __shared__ __align__(16) uint32_t s_f[kEW / 32][sizeof(W) == 4 ? kStageWords : 4];
+    __shared__ __align__(16) uint32_t s_d[kEW / 32][sizeof(W) == 4 ? kStageWords : 4];
+    const int64_t n = (int64_t)a.nslots * cps;
     const int lane = (int)lane_id();
-    const unsigned long long wid = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long ones = 0;
-    for (unsigned long long li = wid; li < n; li += nw) {
-        const int64_t q = list[li];
+    for (int64_t q = wid; q < n; q += nw) {
         const int s = (int)(q / cps);
         const int64_t c = q % cps;
         const SlotGeom sg = slot_geom(a, s);
         const int64_t G = sg.nbits / GB;
         const int64_t tb = c * kTile;
-        const int64_t tend = (tb + kTile < G) ? tb + kTile : G;
+        bool live = false;
+        int64_t tend = tb;
+        if (tb < G) {      // the chunk's summary bytes, one 32-bit word per lane
+            tend = (tb + kTile < G) ? tb + kTile : G;
+            bool nz = true;
+            if (a.fsum) {
+                const int64_t q0 = (sg.src0 + tb * GB) >> 10, q1 = (sg.src0 + tend * GB - 1) >> 10;
+                const int64_t w = (q0 >> 2) + lane;
+                uint32_t x = 0;
+                if (w <= (q1 >> 2)) {
+                    x = __ldcg(reinterpret_cast<const uint32_t*>(a.fsum) + w);
+                    if (w == (q0 >> 2)) x &= 0xffffffffu << (8 * (q0 & 3));
+                    if (w == (q1 >> 2)) x &= 0xffffffffu >> (8 * (3 - (q1 & 3)));
+                }
+                nz = x != 0u;
+            }
+            live = __any_sync(0xffffffffu, nz);
+        }
+        if (lane == 0) flags[q] = live ? 1 : 0;
+        if (!live) continue;
         int prev = -1, first = G_NONE;
         uint32_t heads = 0;
         int64_t last_head = -1;
+        Stage32 stg{};
+        if constexpr (sizeof(W) == 4) stg = stage_chunk(a, sg, tb, tend, s_f[threadIdx.x >> 5], s_d[threadIdx.x >> 5]);
         for (int64_t gb = tb; gb < tend; gb += 32 * kU) {
-            W x[kU];                  // the loads of kU steps are issued together
-            warp_groups<W>(a, sg, gb, tend, x);
+            W x[kU];
+            chunk_groups<W>(a, sg, stg, gb, tend, x);
 #pragma unroll
             for (int k = 0; k < kU; ++k) {
                 const int64_t g0 = gb + 32 * k;
@@ -369,6 +432,7 @@ __global__ void __launch_bounds__(kNT) enc_chunk_sums(EncodeArgs a, ChunkSum* su
             cs.last_head = last_head;
             sums[q] = cs;
         }
+        __syncwarp();           // the staging buffers are reused by the next chunk
     }
     if (setbits) {
         ones = warp_sum(ones);
@@ -462,20 +526,57 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
         a.counts[s] = total;
         if (a.wah_words) atomicAdd(a.wah_words, (unsigned long long)total);
     }
+    if (!a.plan_base) return;
+    // The last slot to finish lays out the decoder's units: block (i,j) of the
+    // p x p grid (row-major) decodes stream s = i*p+j (sieved) or j, in chunks
+    // of 32 words; plan_base is the exclusive scan of the chunk counts.
+    __shared__ bool s_last;
+    if (lane == 0) {
+        __threadfence();
+        s_last = atomicAdd(a.plan_done, 1u) == (unsigned)(a.nslots - 1);
+    }
+    __syncwarp();
+    if (!s_last) return;
+    __threadfence();
+    const int64_t nblocks = (int64_t)a.p * a.p;
+    unsigned long long carry = 0;
+    for (int64_t b0 = 0; b0 < nblocks; b0 += 32) {
+        const int64_t b = b0 + lane;
+        unsigned long long nch = 0;
+        if (b < nblocks) {
+            const int64_t stream = a.sieve ? b : b % a.p;
+            nch = (unsigned long long)((__ldcg(a.counts + stream) + 31) / 32);
+        }
+        unsigned long long incl = nch;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        if (b < nblocks) a.plan_base[b] = (int64_t)(carry + incl - nch);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) {
+        a.plan_base[nblocks] = (int64_t)carry;
+        *a.plan_units = carry;
+        *a.plan_done = 0u;                       // ready for the next level
+    }
 }
 
 template <typename W>
-__global__ void __launch_bounds__(kNT) enc_chunk_write(EncodeArgs a, const ChunkBase* bases, int64_t cps,
-                                                       const int64_t* list, const unsigned long long* nlist) {
+__global__ void __launch_bounds__(kEW) enc_chunk_write(EncodeArgs a, const ChunkBase* bases, const uint8_t* flags,
+                                                       int64_t cps) {
     using T = Wah<W>;
     constexpr int GB = T::GB;
-    const unsigned long long n = *nlist;
+    __shared__ __align__(16) uint32_t s_f[kEW / 32][sizeof(W) == 4 ? kStageWords : 4];
+    __shared__ __align__(16) uint32_t s_d[kEW / 32][sizeof(W) == 4 ? kStageWords : 4];
+    const int64_t n = (int64_t)a.nslots * cps;
     const int lane = (int)lane_id();
     const uint32_t le_mask = 0xffffffffu >> (31 - lane);        // lanes 0..lane
-    const unsigned long long wid = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
-    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-    for (unsigned long long li = wid; li < n; li += nw) {
-        const int64_t q = list[li];
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = wid; q < n; q += nw) {
+        if (!flags[q]) continue;
         const int s = (int)(q / cps);
         const int64_t c = q % cps;
         const SlotGeom sg = slot_geom(a, s);
@@ -488,10 +589,12 @@ __global__ void __launch_bounds__(kNT) enc_chunk_write(EncodeArgs a, const Chunk
         int64_t base = cb.words;          // next word to open
         int64_t run_start = cb.run_start;
         int prev = cb.prev_type;
+        Stage32 stg{};
+        if constexpr (sizeof(W) == 4) stg = stage_chunk(a, sg, tb, tend, s_f[threadIdx.x >> 5], s_d[threadIdx.x >> 5]);
         for (int64_t gb = tb; gb < tend; gb += 32 * kU) {
             W x[kU];
             int tys[kU];
-            warp_groups<W>(a, sg, gb, tend, x);
+            chunk_groups<W>(a, sg, stg, gb, tend, x);
 #pragma unroll
             for (int k = 0; k < kU; ++k) tys[k] = (gb + 32 * k + lane < tend) ? group_type<W>(x[k]) : G_NONE;
 #pragma unroll
@@ -512,7 +615,11 @@ __global__ void __launch_bounds__(kNT) enc_chunk_write(EncodeArgs a, const Chunk
                     const int64_t widx = base + __popc(bl) - 1;
                     const int64_t start = bl ? g0 + 31 - __clz(bl) : run_start;
                     if (g + 1 == tend) nt = cb.next_type;
-                    else if (lane == 31) nt = (k + 1 < kU) ? nt31 : group_type<W>(load_group<W>(a, sg, g + 1));
+                    else if (lane == 31) {
+                        if (k + 1 < kU) nt = nt31;
+                        else if constexpr (sizeof(W) == 4) nt = group_type<W>((W)staged_group(stg, g + 1));
+                        else nt = group_type<W>(load_group<W>(a, sg, g + 1));
+                    }
                     if (ty == G_LIT) out[widx] = T::to_payload(x[k]);
                     else if (nt != ty) out[widx] = fill_word<W>(ty, (uint64_t)(g - start + 1));
                     if (h && ub && (widx & 31) == 0) ub[widx >> 5] = g;
@@ -523,6 +630,234 @@ __global__ void __launch_bounds__(kNT) enc_chunk_write(EncodeArgs a, const Chunk
                 prev = __shfl_sync(0xffffffffu, ty, lv);
             }
         }
+        __syncwarp();           // the staging buffers are reused by the next chunk
+    }
+}
+
+// 31-bit groups, lane-sequential: the chunk is staged in shared memory; lane
+// l takes groups 32l .. 32l+31, combining their words into c = f & V (in
+// registers, aligned to its first group), a group being two words of c
+// funnel-shifted; its groups are classified into zero / one masks, from which
+// head, run-end and word-index masks follow by bit operations, and the lanes'
+// partial results are combined by warp scans.  Same sums and the same words
+// as the batched kernels.
+// The lane's 32 combined words c[k] = bits 32k.. of the sieved groups
+// 32*lane .. 32*lane+31 of the chunk (c = f & V aligned to the chunk's first
+// group; c[31] is past the lane's 992 bits).  Lanes read 31 words apart: no
+// bank conflicts.
+__device__ __forceinline__ void lane_cwords(const Stage32& st, uint32_t (&c)[32]) {
+    const int lane = (int)lane_id();
+    const uint32_t sh = st.off & 31u;
+    const uint32_t* f = st.f + 31 * lane + (st.off >> 5);
+    if (st.d) {
+        const uint32_t* d = st.d + 31 * lane;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) c[k] = __funnelshift_r(f[k], f[k + 1], sh) & d[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) c[k] = __funnelshift_r(f[k], f[k + 1], sh);
+    }
+}
+
+// Group i (0..31) of the lane (it starts at bit 31i: word (31i)/32, shift (31i)%32).
+__device__ __forceinline__ uint32_t lane_group(const uint32_t (&c)[32], int i) {
+    const int b = 31 * i;
+    return __funnelshift_r(c[b >> 5], c[(b >> 5) + 1], (uint32_t)(b & 31)) & 0x7fffffffu;
+}
+
+// Zero / one / valid masks of the lane's groups (bit i = group 32*lane + i).
+__device__ __forceinline__ void lane_masks(const uint32_t (&c)[32], int ng, uint32_t& zm, uint32_t& om,
+                                           uint32_t& vm) {
+    const int nv = ng - 32 * (int)lane_id();
+    vm = nv >= 32 ? 0xffffffffu : (nv > 0 ? (1u << nv) - 1u : 0u);
+    zm = 0u;
+    om = 0u;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const uint32_t x = lane_group(c, i);
+        zm |= (x == 0u ? 1u : 0u) << i;
+        om |= (x == 0x7fffffffu ? 1u : 0u) << i;
+    }
+    zm &= vm;
+    om &= vm;
+}
+
+__device__ __forceinline__ int mask_type(uint32_t zm, uint32_t om, int i) {
+    return ((zm >> i) & 1u) ? G_ZERO : (((om >> i) & 1u) ? G_ONE : G_LIT);
+}
+
+__global__ void __launch_bounds__(kEW) enc_chunk_sums32(EncodeArgs a, ChunkSum* sums, uint8_t* flags, int64_t cps,
+                                                        unsigned long long* setbits) {
+    __shared__ __align__(16) uint32_t s_f[kEW / 32][kStageWords];
+    __shared__ __align__(16) uint32_t s_d[kEW / 32][kStageWords];
+    const int64_t n = (int64_t)a.nslots * cps;
+    const int lane = (int)lane_id();
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long ones = 0;
+    for (int64_t q = wid; q < n; q += nw) {
+        const int s = (int)(q / cps);
+        const int64_t c = q % cps;
+        const SlotGeom sg = slot_geom(a, s);
+        const int64_t G = sg.nbits / 31;
+        const int64_t tb = c * kTile;
+        bool live = false;
+        int64_t tend = tb;
+        if (tb < G) {
+            tend = (tb + kTile < G) ? tb + kTile : G;
+            bool nz = true;
+            if (a.fsum) {
+                const int64_t q0 = (sg.src0 + tb * 31) >> 10, q1 = (sg.src0 + tend * 31 - 1) >> 10;
+                const int64_t w = (q0 >> 2) + lane;
+                uint32_t x = 0;
+                if (w <= (q1 >> 2)) {
+                    x = __ldcg(reinterpret_cast<const uint32_t*>(a.fsum) + w);
+                    if (w == (q0 >> 2)) x &= 0xffffffffu << (8 * (q0 & 3));
+                    if (w == (q1 >> 2)) x &= 0xffffffffu >> (8 * (3 - (q1 & 3)));
+                }
+                nz = x != 0u;
+            }
+            live = __any_sync(0xffffffffu, nz);
+        }
+        if (lane == 0) flags[q] = live ? 1 : 0;
+        if (!live) continue;
+        const Stage32 st = stage_chunk(a, sg, tb, tend, s_f[threadIdx.x >> 5], s_d[threadIdx.x >> 5]);
+        const int ng = (int)(tend - tb);
+        uint32_t cwd[32];
+        lane_cwords(st, cwd);
+        // set bits of the lane's groups: its 31 words, the last lane's cut at the chunk end
+        {
+            const int nv = ng - 32 * lane;
+            if (nv >= 32) {
+                uint32_t cnt = 0;
+#pragma unroll
+                for (int k = 0; k < 31; ++k) cnt += __popc(cwd[k]);
+                ones += cnt;
+            } else if (nv > 0) {
+                const int nbits = nv * 31;
+                uint32_t cnt = 0;
+#pragma unroll
+                for (int k = 0; k < 31; ++k) {
+                    const int left = nbits - 32 * k;
+                    const uint32_t m = left >= 32 ? 0xffffffffu : (left > 0 ? (1u << left) - 1u : 0u);
+                    cnt += __popc(cwd[k] & m);
+                }
+                ones += cnt;
+            }
+        }
+        uint32_t zm, om, vm;
+        lane_masks(cwd, ng, zm, om, vm);
+        uint32_t pz = __shfl_up_sync(0xffffffffu, zm, 1) >> 31, po = __shfl_up_sync(0xffffffffu, om, 1) >> 31;
+        if (lane == 0) { pz = 0u; po = 0u; }              // the chunk's first group counts as a head
+        const uint32_t hm = (vm & ~(zm | om)) | (zm & ~((zm << 1) | pz)) | (om & ~((om << 1) | po));
+        const int heads = warp_sum(__popc(hm));
+        int lh = hm ? 32 * lane + 31 - __clz(hm) : -1;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) { const int y = __shfl_xor_sync(0xffffffffu, lh, d); lh = y > lh ? y : lh; }
+        const int lastl = (ng - 1) >> 5;                       // the lane holding the chunk's last group
+        const int lastty = mask_type(__shfl_sync(0xffffffffu, zm, lastl), __shfl_sync(0xffffffffu, om, lastl),
+                                     (ng - 1) & 31);
+        if (lane == 0) {
+            ChunkSum cs;
+            cs.heads = (uint32_t)heads;
+            cs.types = (uint32_t)mask_type(zm, om, 0) | ((uint32_t)lastty << 8);
+            cs.last_head = lh >= 0 ? tb + lh : -1;
+            sums[q] = cs;
+        }
+        __syncwarp();           // the staging buffers are reused by the next chunk
+    }
+    if (setbits) {
+        ones = warp_sum(ones);
+        if (lane == 0 && ones) atomicAdd(setbits, ones);
+    }
+}
+
+constexpr int kOutWords = kTile + 2;     // the chunk's words, from the one before its first head
+// Local word k sits at k + k/32: consecutive lanes write 32 apart without
+// bank conflicts.
+__device__ __forceinline__ int opad(int k) { return k + (k >> 5); }
+
+__global__ void __launch_bounds__(kEW) enc_chunk_write32(EncodeArgs a, const ChunkBase* bases, const uint8_t* flags,
+                                                         int64_t cps) {
+    __shared__ __align__(16) uint32_t s_f[kEW / 32][kStageWords];
+    __shared__ __align__(16) uint32_t s_d[kEW / 32][kStageWords];
+    static_assert(kOutWords + kOutWords / 32 + 1 <= kStageWords, "output words overflow the frontier buffer");
+    const int64_t n = (int64_t)a.nslots * cps;
+    const int lane = (int)lane_id();
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t* ob = s_f[threadIdx.x >> 5];      // the words, once the frontier words are in registers
+    for (int64_t q = wid; q < n; q += nw) {
+        if (!flags[q]) continue;
+        const int s = (int)(q / cps);
+        const int64_t c = q % cps;
+        const SlotGeom sg = slot_geom(a, s);
+        const int64_t G = sg.nbits / 31;
+        const int64_t tb = c * kTile;
+        const int64_t tend = (tb + kTile < G) ? tb + kTile : G;
+        const ChunkBase cb = bases[q];
+        uint32_t* out = static_cast<uint32_t*>(a.out) + (int64_t)s * a.slot_cap;
+        int64_t* ub = a.unit_base ? a.unit_base + (int64_t)s * a.unit_stride : nullptr;
+        const Stage32 st = stage_chunk(a, sg, tb, tend, s_f[threadIdx.x >> 5], s_d[threadIdx.x >> 5]);
+        const int ng = (int)(tend - tb);
+        uint32_t cwd[32];
+        lane_cwords(st, cwd);
+        __syncwarp();           // the frontier buffer now takes the output words
+        uint32_t zm, om, vm;
+        lane_masks(cwd, ng, zm, om, vm);
+        const int r0 = 32 * lane;
+        const int nv = ng - r0;
+        // types around the lane's groups: the one before (the previous lane's
+        // last group, or the chunk's carry) and the one after
+        uint32_t pz = __shfl_up_sync(0xffffffffu, zm, 1) >> 31, po = __shfl_up_sync(0xffffffffu, om, 1) >> 31;
+        if (lane == 0) { pz = cb.prev_type == G_ZERO; po = cb.prev_type == G_ONE; }
+        uint32_t nz = __shfl_down_sync(0xffffffffu, zm, 1) & 1u, no = __shfl_down_sync(0xffffffffu, om, 1) & 1u;
+        if (nv <= 32) { nz = cb.next_type == G_ZERO; no = cb.next_type == G_ONE; }
+        const uint32_t lit = vm & ~(zm | om);
+        const uint32_t hm = lit | (zm & ~((zm << 1) | pz)) | (om & ~((om << 1) | po));
+        const int last = nv >= 32 ? 31 : nv - 1;                 // the lane's last group (if any)
+        const uint32_t zend = nv > 0 ? zm & ~((zm >> 1) | (nz << last)) : 0u;
+        const uint32_t oend = nv > 0 ? om & ~((om >> 1) | (no << last)) : 0u;
+        const int hc = __popc(hm);
+        int incl = hc, hmax = hm ? r0 + 31 - __clz(hm) : -1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            const int z = __shfl_up_sync(0xffffffffu, hmax, d);
+            if (lane >= d) { incl += y; hmax = z > hmax ? z : hmax; }
+        }
+        const int H = __shfl_sync(0xffffffffu, incl, 31);
+        int hprev = __shfl_up_sync(0xffffffffu, hmax, 1);
+        if (lane == 0) hprev = -1;
+        const int li0 = incl - hc;                    // local index of the word open before this lane's groups
+        const int64_t st0 = hprev >= 0 ? tb + hprev : cb.run_start;   // start of the run open before them
+        bool wrote0 = false, wroteH = false;
+        if (nv > 0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const uint32_t bit = 1u << i;
+                const uint32_t hb = hm & (i == 31 ? 0xffffffffu : (bit << 1) - 1u);   // heads up to group i
+                const int li = li0 + __popc(hb);
+                if (lit & bit) {
+                    ob[opad(li)] = __brev(lane_group(cwd, i)) >> 1;
+                    wroteH |= li == H;
+                } else if ((zend | oend) & bit) {
+                    const int64_t start = hb ? tb + r0 + 31 - __clz(hb) : st0;
+                    ob[opad(li)] = 0x80000000u | ((oend & bit) ? 0x40000000u : 0u) | (uint32_t)(tb + r0 + i - start + 1);
+                    wrote0 |= li == 0;
+                    wroteH |= li == H;
+                }
+                if ((hm & bit) && ub && ((cb.words + li - 1) & 31) == 0) ub[(cb.words + li - 1) >> 5] = tb + r0 + i;
+            }
+        }
+        const bool w0 = __any_sync(0xffffffffu, wrote0), wH = __any_sync(0xffffffffu, wroteH);
+        __syncwarp();
+        // words cb.words .. cb.words + H - 2 are always complete here; the one
+        // before (a run carried in) and the last one (a run carried out) only
+        // when their run ends in this chunk
+        const int lo = w0 ? 0 : 1, hi = wH ? H : H - 1;
+        for (int k = lo + lane; k <= hi; k += 32) out[cb.words - 1 + k] = ob[opad(k)];
+        __syncwarp();           // the staging buffers are reused by the next chunk
     }
 }
 
@@ -564,26 +899,19 @@ int64_t parallel_encode_chunks(int64_t max_nbits, int wah_bits) {
 }
 
 bfs_status launch_wah_encode_parallel(const EncodeArgs& a, int wah_bits, void* sums, void* bases, int64_t cps,
-                                      void* flags, void* list, unsigned long long* nlist, unsigned long long* setbits,
-                                      int grid, cudaStream_t st) {
+                                      void* flags, unsigned long long* setbits, int grid, cudaStream_t st) {
     if (a.nslots <= 0) return BFS_OK;
     ChunkSum* cs = static_cast<ChunkSum*>(sums);
     ChunkBase* cb = static_cast<ChunkBase*>(bases);
     uint8_t* fl = static_cast<uint8_t*>(flags);
-    int64_t* li = static_cast<int64_t*>(list);
-    BFS_CUDA_TRY(cudaMemsetAsync(nlist, 0, sizeof(unsigned long long), st));
-    const int64_t total = (int64_t)a.nslots * cps;
-    const int fgrid = (int)std::min<int64_t>((total + kNT - 1) / kNT, grid);
     if (wah_bits == 32) {
-        enc_chunk_flags<uint32_t><<<fgrid, kNT, 0, st>>>(a, cps, fl, li, nlist);
-        enc_chunk_sums<uint32_t><<<grid, kNT, 0, st>>>(a, cs, cps, li, nlist, setbits);
+        enc_chunk_sums32<<<grid, kEW, 0, st>>>(a, cs, fl, cps, setbits);
         enc_chunk_scan<uint32_t><<<a.nslots, 32, 0, st>>>(a, cs, fl, cb, cps, setbits);
-        enc_chunk_write<uint32_t><<<grid, kNT, 0, st>>>(a, cb, cps, li, nlist);
+        enc_chunk_write32<<<grid, kEW, 0, st>>>(a, cb, fl, cps);
     } else {
-        enc_chunk_flags<unsigned long long><<<fgrid, kNT, 0, st>>>(a, cps, fl, li, nlist);
-        enc_chunk_sums<unsigned long long><<<grid, kNT, 0, st>>>(a, cs, cps, li, nlist, setbits);
+        enc_chunk_sums<unsigned long long><<<grid, kEW, 0, st>>>(a, cs, fl, cps, setbits);
         enc_chunk_scan<unsigned long long><<<a.nslots, 32, 0, st>>>(a, cs, fl, cb, cps, setbits);
-        enc_chunk_write<unsigned long long><<<grid, kNT, 0, st>>>(a, cb, cps, li, nlist);
+        enc_chunk_write<unsigned long long><<<grid, kEW, 0, st>>>(a, cb, fl, cps);
     }
     BFS_CUDA_TRY(cudaGetLastError());
     return BFS_OK;
