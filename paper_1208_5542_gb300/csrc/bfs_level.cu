@@ -495,8 +495,9 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
         const int64_t count = a.xcount[stream];
         const int64_t xw = k * 32 + lane_id();
         const W y = (xw < count) ? in[xw] : W(0);
-        const uint64_t glen = (xw < count) ? word_groups<W>(y) : 0ull;
-        const uint64_t gincl = warp_incl_sum(glen);
+        // groups of a slot fit in 32 bits (n < 2^31)
+        const uint32_t glen = (xw < count) ? (uint32_t)word_groups<W>(y) : 0u;
+        const uint32_t gincl = warp_incl_sum(glen);
         const int64_t gs = a.chunk_base[stream * a.chunks_per_slot + k] + (int64_t)(gincl - glen);
         uint32_t c = 0;
         if (xw < count) {
@@ -528,16 +529,6 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
                 if (g0 >= G) ul = G * GB + T::select(T::from_active(yy, r), kk);
                 else if (is_fill<W>(yy)) ul = g0 * GB + kk;
                 else ul = g0 * GB + T::select(T::from_payload(yy), kk);
-                if (a.mode == BFS_MODE_COMPRESS_SIEVE &&
-                    !(__ldg(bv.dir + (ul >> 5)) & (1u << (ul & 31))) &&
-                    atomicCAS(a.ctr + C_DBG, 0ull, 1ull + (unsigned long long)s) == 0ull) {
-                    // context of the first decoded vertex without a column
-                    a.ctr[C_DBG + 1] = (unsigned long long)k;
-                    a.ctr[C_DBG + 2] = (unsigned long long)(k * 32 + o);
-                    a.ctr[C_DBG + 3] = (unsigned long long)yy;
-                    a.ctr[C_DBG + 4] = (unsigned long long)g0;
-                    a.ctr[C_DBG + 5] = (unsigned long long)ul;
-                }
                 column_of(a, bv, ul, a.mode != BFS_MODE_COMPRESS_SIEVE, &begin, &len);
                 u = (int32_t)(jb + ul);
             }
@@ -1053,13 +1044,8 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         const uint64_t* h = W.h_counters;
         if (h[C_ERROR] & 2ull) return set_error(BFS_ERR_INVALID_ARG, "trace capacity exceeded");
         if (h[C_ERROR])
-            return set_error(BFS_ERR_CORRUPT,
-                             "device invariant check failed (code %llu) at level %d; slot %lld chunk %llu word %llu "
-                             "value %llx group %llu vertex %llu",
-                             (unsigned long long)h[C_ERROR], k, (long long)h[C_DBG] - 1,
-                             (unsigned long long)h[C_DBG + 1], (unsigned long long)h[C_DBG + 2],
-                             (unsigned long long)h[C_DBG + 3], (unsigned long long)h[C_DBG + 4],
-                             (unsigned long long)h[C_DBG + 5]);
+            return set_error(BFS_ERR_CORRUPT, "device invariant check failed (code %llu) at level %d",
+                             (unsigned long long)h[C_ERROR], k);
         if (stats) {
             if (stats->levels && k < stats->capacity_levels) {
                 bfs_level_stats& ls = stats->levels[k];

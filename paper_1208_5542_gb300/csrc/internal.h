@@ -89,8 +89,7 @@ enum Counter : int {
     C_EXCHANGED,         // set bits carried by the exchange
     C_PIECES,            // pieces of long columns queued for the piece kernel
     C_ROW_WORDS,         // WAH words of the compressed row exchange
-    C_DBG,               // first failed invariant: 6 slots of context (see bfs_level.cu)
-    C_NUM = C_DBG + 6
+    C_NUM
 };
 
 // Per-search workspace (owned by the graph, reused by every search).
