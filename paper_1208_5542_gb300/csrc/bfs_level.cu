@@ -278,6 +278,17 @@ __device__ __forceinline__ void column_of(const LevelArgs& a, const BlockView& b
     *len = c1 - c0;
 }
 
+// Bring the L2 lines of a short column's entries on chip ahead of their use
+// (long columns are read by the whole warp, coalesced).
+__device__ __forceinline__ void prefetch_column(const LevelArgs& a, int64_t begin, uint32_t len) {
+    if (len == 0 || len >= kCoop) return;
+    const int32_t* p0 = a.ir + begin;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p0));
+    const int32_t* p1 = p0 + (len - 1);
+    if ((reinterpret_cast<uintptr_t>(p0) >> 7) != (reinterpret_cast<uintptr_t>(p1) >> 7))
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p1));
+}
+
 __device__ __forceinline__ void flush_counts(const LevelArgs& a, unsigned long long edges, unsigned long long hits,
                                              unsigned long long items) {
     edges = warp_sum(edges);
@@ -514,15 +525,18 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
         nitems += c;
         const BlockView bv = block_view(a, s);
         const Visitor<WIN> vis{s_pi, s_t, range_begin(a, row)};
-        for (uint32_t q0 = 0; q0 < items; q0 += 32) {
+        // items q0 .. q0+31, one per lane: decode, look up the column and
+        // prefetch its entries; the next batch's lookups and prefetches are
+        // issued before this batch is expanded
+        auto item = [&](uint32_t q0, int32_t& u, int64_t& begin, uint32_t& len) {
             const uint32_t q = q0 + lane_id();
             const int o = owner_lane(cexcl, q < items ? q : items - 1);
             const W yy = __shfl_sync(0xffffffffu, y, o);
             const int64_t g0 = __shfl_sync(0xffffffffu, gs, o);
             const uint32_t oex = __shfl_sync(0xffffffffu, cexcl, o);
-            int32_t u = 0;
-            int64_t begin = 0;
-            uint32_t len = 0;
+            u = 0;
+            begin = 0;
+            len = 0;
             if (q < items) {
                 const int kk = (int)(q - oex);
                 int64_t ul;
@@ -531,8 +545,22 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
                 else ul = g0 * GB + T::select(T::from_payload(yy), kk);
                 column_of(a, bv, ul, a.mode != BFS_MODE_COMPRESS_SIEVE, &begin, &len);
                 u = (int32_t)(jb + ul);
+                prefetch_column(a, begin, len);
             }
+        };
+        int32_t u;
+        int64_t begin;
+        uint32_t len;
+        item(0, u, begin, len);
+        for (uint32_t q0 = 0; q0 < items; q0 += 32) {
+            int32_t un = 0;
+            int64_t bn = 0;
+            uint32_t ln = 0;
+            if (q0 + 32 < items) item(q0 + 32, un, bn, ln);
             warp_expand<WIN>(a, vis, row, u, begin, len, edges, hits);
+            u = un;
+            begin = bn;
+            len = ln;
         }
     };
     row_affine<WIN>(a, a.row_next, 2, units_in_row, do_unit, s_pi, s_t, s_row);
@@ -573,20 +601,34 @@ __global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
         nitems += cnt;
         const BlockView bv = block_view(a, b);
         const Visitor<WIN> vis{s_pi, s_t, range_begin(a, row)};
-        for (uint32_t q0 = 0; q0 < items; q0 += 32) {
+        auto item = [&](uint32_t q0, int32_t& u, int64_t& begin, uint32_t& len) {
             const uint32_t q = q0 + lane_id();
             const int o = owner_lane(cexcl, q < items ? q : items - 1);
             const uint32_t ob = __shfl_sync(0xffffffffu, bits, o);
             const uint32_t oex = __shfl_sync(0xffffffffu, cexcl, o);
-            int32_t u = 0;
-            int64_t begin = 0;
-            uint32_t len = 0;
+            u = 0;
+            begin = 0;
+            len = 0;
             if (q < items) {
                 const int64_t ul = (c * 32 + o) * 32 + select32(ob, (int)(q - oex));
                 column_of(a, bv, ul, false, &begin, &len);
                 u = (int32_t)(jb + ul);
+                prefetch_column(a, begin, len);
             }
+        };
+        int32_t u;
+        int64_t begin;
+        uint32_t len;
+        item(0, u, begin, len);
+        for (uint32_t q0 = 0; q0 < items; q0 += 32) {
+            int32_t un = 0;
+            int64_t bn = 0;
+            uint32_t ln = 0;
+            if (q0 + 32 < items) item(q0 + 32, un, bn, ln);
             warp_expand<WIN>(a, vis, row, u, begin, len, edges, hits);
+            u = un;
+            begin = bn;
+            len = ln;
         }
     };
     row_affine<WIN>(a, a.row_next, a.plain_batch, units_in_row, do_unit, s_pi, s_t, s_row);
