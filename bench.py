@@ -82,9 +82,10 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def ncu_traffic(workload, mode_name):
-    """Per-launch DRAM bytes of the expansion kernel from the committed ncu summary,
-    or None if none was taken for this workload or the kernel changed since."""
+def ncu_traffic(workload, mode_name, algorithmic_bytes):
+    """Per-launch DRAM bytes of the expansion kernel: the DRAM / algorithmic byte
+    ratio of the committed ncu summary times this launch's algorithmic bytes, or
+    None if none was taken for this workload or the kernel changed since."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
@@ -94,7 +95,7 @@ def ncu_traffic(workload, mode_name):
     ent = data.get(f"{workload}:{mode_name}")
     if not ent or ent.get("kernel_hash") != kernel_hash():
         return None
-    return ent.get("dram_bytes_per_launch")
+    return round(ent["dram_over_algorithmic"] * algorithmic_bytes)
 
 
 class ClockSampler:
@@ -341,14 +342,14 @@ def main():
                 agg["wah_bytes"] += ls["wah_bytes"]
                 agg["hits"] += ls["column_hits"]
                 agg["n"] += 1
-    # per level: flag, sum, scan and write passes of the encoder, unit plan, expansion,
-    # hub pieces, reduction (PLAIN: expansion, hub pieces, reduction); per search: init, root
-    launches_per_bfs = {0: 3, 1: 8, 2: 8}[args.mode]
+    # per level: sum, scan and write passes of the encoder, expansion, hub pieces,
+    # reduction (PLAIN: expansion, hub pieces, reduction); per search: init, root
+    launches_per_bfs = {0: 3, 1: 6, 2: 6}[args.mode]
     gpu_launches = sum(2 + launches_per_bfs * st.n_levels for sts in stats_cs for st in sts)
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = (ex_bytes / launches) / (ex_ms / launches / 1e3) / 1e9 if launches and ex_ms > 0 else 0.0
-    traffic = ncu_traffic(args.workload, MODE_NAMES[args.mode])
+    traffic = ncu_traffic(args.workload, MODE_NAMES[args.mode], ex_bytes / launches if launches else 0)
     exch = []
     for k in sorted(per_level):
         a = per_level[k]
@@ -456,6 +457,8 @@ def main():
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4) if peak else None,
                      "peak_source": peak_src, "traffic": traffic,
+                     "traffic_source": ("DRAM/algorithmic ratio of an ncu capture at scale 24 (same 16x16 grid and "
+                                        "visiting path) times this launch's algorithmic bytes") if traffic else None,
                      "algorithmic_bytes_per_launch": round(ex_bytes / launches) if launches else 0,
                      "avg_launch_ms": round(ex_ms / launches, 5) if launches else 0, "launches": launches},
         "phases_ms_per_search": phases,
