@@ -277,3 +277,45 @@ def test_compressed_row_exchange_never_changes_the_result(mode, scale, p):
     parent, level, st = _run(g, int(r), stats=True)
     assert (level == lv).all() and (parent == pa).all()
     assert sum(ls["row_wah_bytes"] for ls in st.levels) == 0
+
+
+def test_scale22_grid8_64bit_words_streams_bit_exact():
+    """The scale-22 configuration: Kronecker scale 22, 8x8 grid, COMPRESS_SIEVE
+    with 64-bit WAH words.  Levels and parents of two roots, and every exchanged
+    stream of the first, bit-exact with the oracle's Alg. 3."""
+    bfs = _lib()
+    n, src, dst = graphgen.edges(22, 16)
+    go = oracle.csr(n, src, dst)
+    p, wah = 8, 64
+    g = bfs.Graph.from_edges(n, src, dst, p=p, mode=2, wah_bits=wah)
+    roots = graphgen.pick_roots(n, src, dst, 2)
+    cap = 32 * (2 * p * p + n * p // (wah - 1) + 8)
+    lv, pa, tr = oracle.dist_bfs(go, p, int(roots[0]), mode=oracle.COMPRESS_SIEVE, w=wah, trace=True,
+                                 max_levels=32, trace_cap=cap)
+    parent, level, st = _run(g, int(roots[0]), stats=True, trace_capacity=cap * 2)
+    assert (level == lv).all() and (parent == pa).all()
+    _check_trace(_unpack_trace(st, wah), tr)
+    lv, pa = oracle.bfs(go, int(roots[1]))
+    parent, level, _ = _run(g, int(roots[1]))
+    assert (level == lv).all() and (parent == pa).all()
+
+
+def test_scale26_grid16_bench_configuration_one_root():
+    """The bench's workload and launch configuration: Kronecker scale 26 (67M
+    vertices, 2.1G entries), 16x16 grid, COMPRESS_SIEVE, 32-bit words, the
+    global-memory visiting path with rows in turn.  One seeded root: all levels
+    and parents bit-exact with the oracle; the PLAIN search agrees."""
+    bfs = _lib()
+    n, src, dst = graphgen.edges(26, 16)
+    g = bfs.Graph.from_edges(n, src, dst, p=16, mode=2)
+    r = int(graphgen.pick_roots(n, src, dst, 1)[0])
+    parent, level, _ = _run(g, r)
+    g.set_mode(0)
+    parent0, level0, _ = _run(g, r)
+    del g
+    torch.cuda.empty_cache()
+    go = oracle.csr(n, src, dst)
+    del src, dst
+    lv, pa = oracle.bfs(go, r)
+    assert (level == lv).all() and (parent == pa).all()
+    assert (level0 == lv).all() and (parent0 == pa).all()
