@@ -54,6 +54,17 @@ constexpr uint32_t kHub = 1024;     // columns longer than this are cut into pie
 constexpr uint32_t kPiece = 1024;   // entries per piece
 constexpr int64_t kSmemLimit = 227 * 1024;
 
+// Per-level values that the device keeps from level to level, so that one
+// level is the same launch sequence every time (and a CUDA graph can repeat it).
+struct LevelCtl {
+    int64_t frontier;      // vertices of the current frontier
+    int64_t visited;       // vertices visited so far
+    int32_t level;         // current level k
+    int32_t plain_batch;   // PLAIN units per hand-out
+    int32_t dedup;         // read the parent before updating it
+    int32_t go;            // 1 while another level follows
+};
+
 struct LevelArgs {
     // layout
     const uint32_t* dir;
@@ -87,7 +98,6 @@ struct LevelArgs {
     unsigned long long* ctr;
     int mode;
     int64_t plain_upb;                  // PLAIN units per block
-    int64_t plain_batch;                // PLAIN units per hand-out (set per level)
     int64_t win_words;                  // words of the shared-memory row window (0: none)
     // compressed row exchange (2D fold): row buffers of the partial next bits
     int row_exchange;
@@ -95,7 +105,7 @@ struct LevelArgs {
     int64_t rowbuf_cap;
     int64_t rowbuf_slots;
     int sweep;                          // all CTAs start at row 0 (rows in turn)
-    int dedup;                          // read the parent before updating it
+    const LevelCtl* ctl;                // this level's values
     unsigned long long* rowbuf_count;   // slots used in this level
     int32_t* rowbuf_row;                // block-row of each slot
     int64_t* rowbuf_words;              // words in each slot
@@ -113,7 +123,7 @@ __device__ __forceinline__ int64_t range_begin(const LevelArgs& a, int64_t b) {
 // and the next bit live in shared memory; without, the visited word is read
 // through the read-only path (pi does not change during the expansion) and
 // the next bit is a reduction at L2.
-template <bool WIN>
+template <bool WIN, bool DEDUP>
 struct Visitor {
     const uint32_t* s_pi;
     uint32_t* s_t;
@@ -155,8 +165,8 @@ struct Visitor {
 constexpr int kIlp = 4;
 
 // All 32 lanes expand one column: kIlp x 32 consecutive entries per step.
-template <bool WIN>
-__device__ __forceinline__ void warp_column(const LevelArgs& a, const Visitor<WIN>& vis, int32_t u, int64_t beg,
+template <bool WIN, bool DEDUP>
+__device__ __forceinline__ void warp_column(const LevelArgs& a, const Visitor<WIN, DEDUP>& vis, int32_t u, int64_t beg,
                                             uint32_t len) {
     const int32_t* col = a.ir + beg;
     for (uint32_t e = lane_id(); e < len; e += 32 * kIlp) {
@@ -167,7 +177,7 @@ __device__ __forceinline__ void warp_column(const LevelArgs& a, const Visitor<WI
 #pragma unroll
         for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0) ? vis.probe(a, v[k]) : 0u;
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0 && vis.fresh(v[k], w[k])) ? (a.dedup ? vis.seen(a, v[k]) : 0xffffffffu) : 0u;
+        for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0 && vis.fresh(v[k], w[k])) ? (DEDUP ? vis.seen(a, v[k]) : 0xffffffffu) : 0u;
 #pragma unroll
         for (int k = 0; k < kIlp; ++k)
             if (v[k] >= 0) vis.mark(a, v[k], u, w[k]);
@@ -179,8 +189,8 @@ __device__ __forceinline__ void warp_column(const LevelArgs& a, const Visitor<WI
 // least kCoop entries are expanded by the whole warp one after the other; the
 // short ones share the warp through a load-balanced search over their entry
 // counts, 32 consecutive entries of the concatenated columns per step.
-template <bool WIN>
-__device__ __forceinline__ void warp_expand(const LevelArgs& a, const Visitor<WIN>& vis, int row, int32_t u,
+template <bool WIN, bool DEDUP>
+__device__ __forceinline__ void warp_expand(const LevelArgs& a, const Visitor<WIN, DEDUP>& vis, int row, int32_t u,
                                             int64_t beg, uint32_t len, unsigned long long& edges,
                                             unsigned long long& hits) {
     const uint32_t lane = lane_id();
@@ -209,7 +219,7 @@ __device__ __forceinline__ void warp_expand(const LevelArgs& a, const Visitor<WI
     while (coop) {
         const int src = __ffs(coop) - 1;
         coop &= coop - 1;
-        warp_column<WIN>(a, vis, __shfl_sync(0xffffffffu, u, src), __shfl_sync(0xffffffffu, beg, src),
+        warp_column<WIN, DEDUP>(a, vis, __shfl_sync(0xffffffffu, u, src), __shfl_sync(0xffffffffu, beg, src),
                          __shfl_sync(0xffffffffu, len, src));
     }
     if (len >= kCoop) len = 0;
@@ -237,7 +247,7 @@ __device__ __forceinline__ void warp_expand(const LevelArgs& a, const Visitor<WI
 #pragma unroll
         for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0) ? vis.probe(a, v[k]) : 0u;
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0 && vis.fresh(v[k], w[k])) ? (a.dedup ? vis.seen(a, v[k]) : 0xffffffffu) : 0u;
+        for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0 && vis.fresh(v[k], w[k])) ? (DEDUP ? vis.seen(a, v[k]) : 0xffffffffu) : 0u;
 #pragma unroll
         for (int k = 0; k < kIlp; ++k)
             if (v[k] >= 0) vis.mark(a, v[k], ou[k], w[k]);
@@ -475,8 +485,9 @@ __device__ __forceinline__ void row_affine(const LevelArgs& a, unsigned long lon
 // one stream, decoded by one warp: a warp scan of run lengths from the
 // chunk's group base places every word, a scan of item counts numbers the
 // decoded vertices, and the warp expands them 32 at a time.
-template <typename W, bool WIN>
+template <typename W, bool WIN, bool DEDUP>
 __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
+    if (a.ctl->dedup != (DEDUP ? 1 : 0)) return;   // the other variant expands this level
     using T = Wah<W>;
     constexpr int GB = T::GB;
     extern __shared__ uint32_t s_win[];                   // s_pi | s_t (WIN only)
@@ -524,7 +535,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
         const uint32_t items = __shfl_sync(0xffffffffu, cincl, 31);
         nitems += c;
         const BlockView bv = block_view(a, s);
-        const Visitor<WIN> vis{s_pi, s_t, range_begin(a, row)};
+        const Visitor<WIN, DEDUP> vis{s_pi, s_t, range_begin(a, row)};
         // items q0 .. q0+31, one per lane: decode, look up the column and
         // prefetch its entries; the next batch's lookups and prefetches are
         // issued before this batch is expanded
@@ -557,7 +568,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
             int64_t bn = 0;
             uint32_t ln = 0;
             if (q0 + 32 < items) item(q0 + 32, un, bn, ln);
-            warp_expand<WIN>(a, vis, row, u, begin, len, edges, hits);
+            warp_expand<WIN, DEDUP>(a, vis, row, u, begin, len, edges, hits);
             u = un;
             begin = bn;
             len = ln;
@@ -571,8 +582,9 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
 // of range j), one warp: lane l keeps word l's bits whose column is nonempty
 // (word-wise AND with V_{i,j}, the block's column index) and the warp expands
 // them 32 at a time.
-template <bool WIN>
+template <bool WIN, bool DEDUP>
 __global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
+    if (a.ctl->dedup != (DEDUP ? 1 : 0)) return;   // the other variant expands this level
     extern __shared__ uint32_t s_win[];
     __shared__ int s_row[2];
     uint32_t* s_pi = s_win;
@@ -600,7 +612,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
         if (items == 0) return;
         nitems += cnt;
         const BlockView bv = block_view(a, b);
-        const Visitor<WIN> vis{s_pi, s_t, range_begin(a, row)};
+        const Visitor<WIN, DEDUP> vis{s_pi, s_t, range_begin(a, row)};
         auto item = [&](uint32_t q0, int32_t& u, int64_t& begin, uint32_t& len) {
             const uint32_t q = q0 + lane_id();
             const int o = owner_lane(cexcl, q < items ? q : items - 1);
@@ -625,19 +637,20 @@ __global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
             int64_t bn = 0;
             uint32_t ln = 0;
             if (q0 + 32 < items) item(q0 + 32, un, bn, ln);
-            warp_expand<WIN>(a, vis, row, u, begin, len, edges, hits);
+            warp_expand<WIN, DEDUP>(a, vis, row, u, begin, len, edges, hits);
             u = un;
             begin = bn;
             len = ln;
         }
     };
-    row_affine<WIN>(a, a.row_next, a.plain_batch, units_in_row, do_unit, s_pi, s_t, s_row);
+    row_affine<WIN>(a, a.row_next, a.ctl->plain_batch, units_in_row, do_unit, s_pi, s_t, s_row);
     flush_counts(a, edges, hits, nitems);
 }
 
 // Pieces of long columns, row by row: one warp per piece.
-template <bool WIN>
+template <bool WIN, bool DEDUP>
 __global__ void __launch_bounds__(kXT, 1) expand_pieces(LevelArgs a) {
+    if (a.ctl->dedup != (DEDUP ? 1 : 0)) return;   // the other variant expands this level
     extern __shared__ uint32_t s_win[];
     __shared__ int s_row[2];
     uint32_t* s_pi = s_win;
@@ -647,8 +660,8 @@ __global__ void __launch_bounds__(kXT, 1) expand_pieces(LevelArgs a) {
     };
     auto do_unit = [&](int row, int64_t x) {
         const Item it = a.pieces[a.row_piece_base[row] + x];
-        const Visitor<WIN> vis{s_pi, s_t, range_begin(a, row)};
-        warp_column<WIN>(a, vis, it.u, it.begin, it.len);
+        const Visitor<WIN, DEDUP> vis{s_pi, s_t, range_begin(a, row)};
+        warp_column<WIN, DEDUP>(a, vis, it.u, it.begin, it.len);
     };
     row_affine<WIN>(a, a.row_piece_next, 1, units_in_row, do_unit, s_pi, s_t, s_row);
 }
@@ -676,12 +689,13 @@ __global__ void __launch_bounds__(kXT) fold_rows(LevelArgs a) {
 }
 
 // ---------------------------------------------------------------- reduce --
-// t = t & ~pi; pi |= t; level of the new vertices; |t|; clear the old
-// frontier (it becomes the next t); frontier summary of t.
+// x = t & ~pi; pi |= x; level of the new vertices; |x|; the next frontier f = x
+// and t cleared for the next level; frontier summary of x.
 __global__ void __launch_bounds__(kNT) reduce_level(uint32_t* __restrict__ t, uint32_t* __restrict__ pi,
-                                                    uint32_t* __restrict__ f_old, uint8_t* __restrict__ fsum,
+                                                    uint32_t* __restrict__ f, uint8_t* __restrict__ fsum,
                                                     int64_t words, int64_t n, int32_t* __restrict__ level,
-                                                    int32_t next_level, unsigned long long* ctr) {
+                                                    const LevelCtl* __restrict__ ctl, unsigned long long* ctr) {
+    const int32_t next_level = ctl->level + 1;
     const int64_t nwarps = (words + 31) / 32;
     const int64_t gw0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t gstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -700,8 +714,8 @@ __global__ void __launch_bounds__(kNT) reduce_level(uint32_t* __restrict__ t, ui
                     if (v < n) level[v] = next_level;
                 }
             }
-            t[w] = x;
-            f_old[w] = 0u;
+            f[w] = x;
+            t[w] = 0u;
         }
         const uint32_t any = __ballot_sync(0xffffffffu, x != 0u);
         const int cnt = warp_sum(__popc(x));
@@ -710,6 +724,37 @@ __global__ void __launch_bounds__(kNT) reduce_level(uint32_t* __restrict__ t, ui
             if (cnt) atomicAdd(ctr + C_NEXT_COUNT, (unsigned long long)cnt);
         }
     }
+}
+
+// One thread: the values of the next level, and whether it runs (the
+// frontier is not empty, no invariant failed, fewer than max_levels levels).
+// In a CUDA graph the decision drives the conditional WHILE node.
+__global__ void level_next(LevelCtl* c, const unsigned long long* ctr, int64_t n, int win, int32_t max_levels,
+                           cudaGraphConditionalHandle handle, int use_handle) {
+    const int64_t f = (int64_t)ctr[C_NEXT_COUNT];
+    c->frontier = f;
+    c->visited += f;
+    c->level += 1;
+    // PLAIN scans every raw word of every block: many units per hand-out on
+    // sparse levels (few items each), few on dense ones (balance)
+    c->plain_batch = (f * 64 < n) ? 32 : 2;
+    // While few vertices are visited, most entries lead to fresh vertices,
+    // each reached from many frontier vertices: reading the parent first turns
+    // most of those visits into one L2 read instead of two atomics.  With a
+    // window the next bit is a shared-memory atomic: not worth it.
+    c->dedup = (!win && c->visited * 16 < n) ? 1 : 0;
+    const int go = (f > 0 && ctr[C_ERROR] == 0 && c->level < max_levels) ? 1 : 0;
+    c->go = go;
+    if (use_handle) cudaGraphSetConditional(handle, go ? 1u : 0u);
+}
+
+__global__ void level_first(LevelCtl* c, int64_t n, int win) {
+    c->frontier = 1;
+    c->visited = 1;
+    c->level = 0;
+    c->plain_batch = (64 < n) ? 32 : 2;
+    c->dedup = (!win && 16 < n) ? 1 : 0;
+    c->go = 1;
 }
 
 __global__ void init_search(int32_t* __restrict__ level, int32_t* __restrict__ parent, int64_t n,
@@ -837,6 +882,7 @@ bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
     BFS_TRY(W.enc_bases.alloc(parallel_encode_base_bytes() * p2 * W.enc_cps));
     BFS_TRY(W.enc_flags.alloc(p2 * W.enc_cps));
     BFS_TRY(W.enc_done.alloc(sizeof(unsigned int)));
+    BFS_TRY(W.ctl.alloc(sizeof(LevelCtl)));
     BFS_CUDA_TRY(cudaMemset(W.enc_done.ptr, 0, sizeof(unsigned int)));
     BFS_TRY(W.counters.alloc(sizeof(unsigned long long) * C_NUM));
     // pieces: per row, sum over long columns of ceil(len/kPiece) <= nnz_row/kPiece + nnz_row/kHub
@@ -871,10 +917,10 @@ bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
     W.win_words = (window_bytes(win) + static_bytes <= (size_t)kSmemLimit) ? win : 0;
     if (W.win_words) {
         const size_t dyn = window_bytes(W.win_words);
-        BFS_TRY(allow_smem(expand_wah<uint32_t, true>, dyn));
-        BFS_TRY(allow_smem(expand_wah<unsigned long long, true>, dyn));
-        BFS_TRY(allow_smem(expand_plain<true>, dyn));
-        BFS_TRY(allow_smem(expand_pieces<true>, dyn));
+        BFS_TRY(allow_smem(expand_wah<uint32_t, true, false>, dyn));
+        BFS_TRY(allow_smem(expand_wah<unsigned long long, true, false>, dyn));
+        BFS_TRY(allow_smem(expand_plain<true, false>, dyn));
+        BFS_TRY(allow_smem(expand_pieces<true, false>, dyn));
     }
     return BFS_OK;
 }
@@ -885,7 +931,13 @@ void free_workspace(bfs_graph* g) {
     W.xcount.release(); W.chunk_base.release(); W.units.release(); W.counters.release(); W.pieces.release();
     W.level_scratch.release(); W.row_meta.release();
     W.rowbuf.release(); W.rowbuf_row.release(); W.rowbuf_words.release();
-    W.enc_sums.release(); W.enc_bases.release(); W.enc_flags.release(); W.enc_done.release();
+    W.enc_sums.release(); W.enc_bases.release(); W.enc_flags.release(); W.enc_done.release(); W.ctl.release();
+    for (auto& c : W.sgraph) {
+        if (c.exec) cudaGraphExecDestroy(c.exec);
+        if (c.graph) cudaGraphDestroy(c.graph);
+        c = SearchGraph();
+    }
+    W.sgraph_next = 0;
     W.tmp_parent.release(); W.tmp_level.release();
     if (W.h_counters) cudaFreeHost(W.h_counters);
     W.h_counters = nullptr;
@@ -1014,73 +1066,156 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     ea.plan_done = W.enc_done.as<unsigned int>();
     ea.frontier_words = W.bm_words;
 
-    uint32_t* f = W.fa.as<uint32_t>();
-    uint32_t* t = W.fb.as<uint32_t>();
-    int64_t frontier = 1;
-    int64_t visited = 1;
-    int64_t raw_bytes = 0;
-    for (int j = 0; j < p; ++j) raw_bytes += 4 * ((L.range_len(j) + 31) / 32);
-    raw_bytes *= p;
+    uint32_t* f = W.fa.as<uint32_t>();       // frontier of the level (reduce_level writes the next one here)
+    uint32_t* t = W.fb.as<uint32_t>();       // next bits (cleared by reduce_level)
+    LevelCtl* ctl = W.ctl.as<LevelCtl>();
+    a.f = f;
+    a.t = t;
+    a.ctl = ctl;
+    ea.frontier = f;
+    const int32_t max_levels = (int32_t)std::min<int64_t>(L.n + 1, INT32_MAX);
+    level_first<<<1, 1, 0, st>>>(ctl, L.n, win ? 1 : 0);
+    BFS_CUDA_TRY(cudaGetLastError());
 
-    for (int32_t k = 0;; ++k) {
-        if (k > 0) {   // per-level counters; the error flag and the trace cursor persist
-            BFS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * C_ERROR, st));
-            BFS_CUDA_TRY(cudaMemsetAsync(ctr + C_WAH_WORDS, 0, sizeof(unsigned long long) * (C_NUM - C_WAH_WORDS), st));
-        }
-        BFS_CUDA_TRY(cudaMemsetAsync(lvl, 0, sizeof(unsigned long long) * (3 * p + 1), st));
-        a.f = f;
-        a.t = t;
-        // PLAIN scans every raw word of every block: hand out many units at a
-        // time on sparse levels (few items each), few on dense ones (balance)
-        a.plain_batch = (frontier * 64 < L.n) ? 32 : 2;
-        // While few vertices are visited, most entries lead to fresh vertices,
-        // each reached from many frontier vertices: reading the parent first
-        // turns most of those visits into one L2 read instead of two atomics.
-        // With a window the next bit is a shared-memory atomic: not worth it.
-        a.dedup = (!win && visited * 16 < L.n) ? 1 : 0;
-        ea.frontier = f;
-        if (timing) cudaEventRecord(W.ev[0], st);
+    // One level: the same launch sequence every time.  `host` adds the
+    // statistics, the trace and the phase events (and k is known on the host).
+    auto level_body = [&](cudaStream_t s, bool host, int32_t k, cudaGraphConditionalHandle handle) -> bfs_status {
+        // per-level counters; the error flag and the trace cursor persist
+        BFS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * C_ERROR, s));
+        BFS_CUDA_TRY(cudaMemsetAsync(ctr + C_WAH_WORDS, 0, sizeof(unsigned long long) * (C_NUM - C_WAH_WORDS), s));
+        BFS_CUDA_TRY(cudaMemsetAsync(lvl, 0, sizeof(unsigned long long) * (3 * p + 1), s));
+        if (host && timing) cudaEventRecord(W.ev[0], s);
         if (mode == BFS_MODE_PLAIN) {
-            if (timing) { cudaEventRecord(W.ev[1], st); cudaEventRecord(W.ev[2], st); }
-            if (win) expand_plain<true><<<xgrid, kXT, dyn, st>>>(a);
-            else expand_plain<false><<<xgrid, kXT, 0, st>>>(a);
+            if (host && timing) { cudaEventRecord(W.ev[1], s); cudaEventRecord(W.ev[2], s); }
+            if (win) {
+                expand_plain<true, false><<<xgrid, kXT, dyn, s>>>(a);
+            } else {
+                expand_plain<false, true><<<xgrid, kXT, 0, s>>>(a);
+                expand_plain<false, false><<<xgrid, kXT, 0, s>>>(a);
+            }
             BFS_CUDA_TRY(cudaGetLastError());
         } else {
             BFS_TRY(launch_wah_encode_parallel(ea, wbits, W.enc_sums.ptr, W.enc_bases.ptr, W.enc_cps,
-                                               W.enc_flags.ptr, ctr + C_EXCHANGED, sm_count() * 6, st));
-            if (timing) cudaEventRecord(W.ev[1], st);
-            if (tracing && k < stats->capacity_levels) {
+                                               W.enc_flags.ptr, ctr + C_EXCHANGED, sm_count() * 6, s));
+            if (host && timing) cudaEventRecord(W.ev[1], s);
+            if (host && tracing && k < stats->capacity_levels) {
                 const int u32pw = wbits / 32;
-                trace_offsets<<<1, kNT, 0, st>>>(W.xcount.as<int64_t>(), nslots, u32pw, slot_off.as<int64_t>(),
-                                                 stats->trace_counts + (int64_t)k * nslots, ctr,
-                                                 stats->trace_capacity);
+                trace_offsets<<<1, kNT, 0, s>>>(W.xcount.as<int64_t>(), nslots, u32pw, slot_off.as<int64_t>(),
+                                                stats->trace_counts + (int64_t)k * nslots, ctr,
+                                                stats->trace_capacity);
                 dim3 tg(8, nslots);
-                trace_copy<<<tg, kNT, 0, st>>>(W.xbuf.as<uint32_t>(), slot_cap * u32pw, W.xcount.as<int64_t>(), u32pw,
-                                               slot_off.as<int64_t>(), stats->trace_words, stats->trace_capacity);
+                trace_copy<<<tg, kNT, 0, s>>>(W.xbuf.as<uint32_t>(), slot_cap * u32pw, W.xcount.as<int64_t>(), u32pw,
+                                              slot_off.as<int64_t>(), stats->trace_words, stats->trace_capacity);
                 BFS_CUDA_TRY(cudaGetLastError());
             }
-            if (timing) cudaEventRecord(W.ev[2], st);
+            if (host && timing) cudaEventRecord(W.ev[2], s);
             if (wbits == 32) {
-                if (win) expand_wah<uint32_t, true><<<xgrid, kXT, dyn, st>>>(a);
-                else expand_wah<uint32_t, false><<<xgrid, kXT, 0, st>>>(a);
+                if (win) {
+                    expand_wah<uint32_t, true, false><<<xgrid, kXT, dyn, s>>>(a);
+                } else {
+                    expand_wah<uint32_t, false, true><<<xgrid, kXT, 0, s>>>(a);
+                    expand_wah<uint32_t, false, false><<<xgrid, kXT, 0, s>>>(a);
+                }
             } else {
-                if (win) expand_wah<unsigned long long, true><<<xgrid, kXT, dyn, st>>>(a);
-                else expand_wah<unsigned long long, false><<<xgrid, kXT, 0, st>>>(a);
+                if (win) {
+                    expand_wah<unsigned long long, true, false><<<xgrid, kXT, dyn, s>>>(a);
+                } else {
+                    expand_wah<unsigned long long, false, true><<<xgrid, kXT, 0, s>>>(a);
+                    expand_wah<unsigned long long, false, false><<<xgrid, kXT, 0, s>>>(a);
+                }
             }
             BFS_CUDA_TRY(cudaGetLastError());
         }
-        if (win) expand_pieces<true><<<xgrid, kXT, dyn, st>>>(a);
-        else expand_pieces<false><<<xgrid, kXT, 0, st>>>(a);
+        if (win) {
+            expand_pieces<true, false><<<xgrid, kXT, dyn, s>>>(a);
+        } else {
+            expand_pieces<false, true><<<xgrid, kXT, 0, s>>>(a);
+            expand_pieces<false, false><<<xgrid, kXT, 0, s>>>(a);
+        }
         BFS_CUDA_TRY(cudaGetLastError());
         if (rowx) {
-            fold_rows<<<xgrid, kXT, 0, st>>>(a);
+            fold_rows<<<xgrid, kXT, 0, s>>>(a);
             BFS_CUDA_TRY(cudaGetLastError());
         }
-        if (timing) cudaEventRecord(W.ev[3], st);
-        reduce_level<<<std::min<int64_t>((W.bm_words + 255) / 256 + 1, sm_count() * 16), kNT, 0, st>>>(
-            t, W.pi.as<uint32_t>(), f, W.fsum.as<uint8_t>(), W.bm_words, L.n, level, k + 1, ctr);
+        if (host && timing) cudaEventRecord(W.ev[3], s);
+        reduce_level<<<std::min<int64_t>((W.bm_words + 255) / 256 + 1, sm_count() * 16), kNT, 0, s>>>(
+            t, W.pi.as<uint32_t>(), f, W.fsum.as<uint8_t>(), W.bm_words, L.n, level, ctl, ctr);
         BFS_CUDA_TRY(cudaGetLastError());
-        if (timing) cudaEventRecord(W.ev[4], st);
+        if (host && timing) cudaEventRecord(W.ev[4], s);
+        level_next<<<1, 1, 0, s>>>(ctl, ctr, L.n, win ? 1 : 0, max_levels, handle, host ? 0 : 1);
+        BFS_CUDA_TRY(cudaGetLastError());
+        return BFS_OK;
+    };
+
+    if (!stats) {
+        // The whole level loop as one CUDA-graph launch: a conditional WHILE
+        // node repeats the level while level_next says so.  No host round
+        // trip per level; the graph is built once per configuration and output
+        // buffers and reused.
+        SearchGraph* sg = nullptr;
+        for (auto& c : W.sgraph)
+            if (c.exec && c.mode == mode && c.wbits == wbits && c.rowx == (int)rowx && c.parent == parent &&
+                c.level == level)
+                sg = &c;
+        if (!sg) {
+            SearchGraph& c = W.sgraph[W.sgraph_next];
+            W.sgraph_next = (W.sgraph_next + 1) % (int)(sizeof(W.sgraph) / sizeof(W.sgraph[0]));
+            if (c.exec) { cudaGraphExecDestroy(c.exec); c.exec = nullptr; }
+            if (c.graph) { cudaGraphDestroy(c.graph); c.graph = nullptr; }
+            cudaGraph_t graph = nullptr;
+            BFS_CUDA_TRY(cudaGraphCreate(&graph, 0));
+            cudaGraphConditionalHandle handle;
+            BFS_CUDA_TRY(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = handle;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cond = nullptr;
+            cudaError_t ce = cudaGraphAddNode(&cond, graph, nullptr, nullptr, 0, &cp);
+            if (ce != cudaSuccess) { cudaGraphDestroy(graph); return cuda_error(ce, "conditional node", __FILE__, __LINE__); }
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            cudaStream_t cs = nullptr;
+            BFS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            ce = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+            bfs_status bs = BFS_OK;
+            if (ce == cudaSuccess) bs = level_body(cs, false, 0, handle);
+            cudaError_t ce2 = cudaStreamEndCapture(cs, &body);
+            cudaStreamDestroy(cs);
+            if (ce != cudaSuccess || ce2 != cudaSuccess || bs != BFS_OK) {
+                cudaGraphDestroy(graph);
+                if (bs != BFS_OK) return bs;
+                return cuda_error(ce != cudaSuccess ? ce : ce2, "capture of the level body", __FILE__, __LINE__);
+            }
+            cudaGraphExec_t exec = nullptr;
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            if (ce != cudaSuccess) { cudaGraphDestroy(graph); return cuda_error(ce, "cudaGraphInstantiate(search)", __FILE__, __LINE__); }
+            c.graph = graph;
+            c.exec = exec;
+            c.mode = mode;
+            c.wbits = wbits;
+            c.rowx = rowx ? 1 : 0;
+            c.parent = parent;
+            c.level = level;
+            sg = &c;
+        }
+        BFS_CUDA_TRY(cudaGraphLaunch(sg->exec, st));
+        BFS_CUDA_TRY(cudaMemcpyAsync(W.h_counters, ctr, sizeof(uint64_t) * C_NUM, cudaMemcpyDeviceToHost, st));
+        BFS_CUDA_TRY(cudaStreamSynchronize(st));
+        const uint64_t* h = W.h_counters;
+        if (h[C_ERROR] & 2ull) return set_error(BFS_ERR_INVALID_ARG, "trace capacity exceeded");
+        if (h[C_ERROR])
+            return set_error(BFS_ERR_CORRUPT, "device invariant check failed (code %llu)",
+                             (unsigned long long)h[C_ERROR]);
+        return BFS_OK;
+    }
+
+    int64_t frontier = 1;
+    int64_t raw_bytes = 0;
+    for (int j = 0; j < p; ++j) raw_bytes += 4 * ((L.range_len(j) + 31) / 32);
+    raw_bytes *= p;
+    for (int32_t k = 0;; ++k) {
+        BFS_TRY(level_body(st, true, k, cudaGraphConditionalHandle{}));
         BFS_CUDA_TRY(cudaMemcpyAsync(W.h_counters, ctr, sizeof(uint64_t) * C_NUM, cudaMemcpyDeviceToHost, st));
         BFS_CUDA_TRY(cudaStreamSynchronize(st));
         const uint64_t* h = W.h_counters;
@@ -1088,31 +1223,27 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         if (h[C_ERROR])
             return set_error(BFS_ERR_CORRUPT, "device invariant check failed (code %llu) at level %d",
                              (unsigned long long)h[C_ERROR], k);
-        if (stats) {
-            if (stats->levels && k < stats->capacity_levels) {
-                bfs_level_stats& ls = stats->levels[k];
-                memset(&ls, 0, sizeof(ls));
-                ls.frontier_vertices = frontier;
-                ls.exchanged_vertices = (mode == BFS_MODE_COMPRESS_SIEVE) ? (int64_t)h[C_EXCHANGED] : p * frontier;
-                ls.column_hits = (int64_t)h[C_HITS];
-                ls.raw_bytes = raw_bytes;
-                ls.wah_bytes = (mode == BFS_MODE_PLAIN) ? 0 : (int64_t)h[C_WAH_WORDS] * (wbits / 8);
-                ls.edges_scanned = (int64_t)h[C_EDGES];
-                ls.row_wah_bytes = (int64_t)h[C_ROW_WORDS] * 4;
-                if (timing) {
-                    ls.ms_compress_sieve = elapsed(W.ev[0], W.ev[1]);
-                    ls.ms_communication = elapsed(W.ev[1], W.ev[2]);
-                    ls.ms_traversing = elapsed(W.ev[2], W.ev[3]);
-                    ls.ms_reducing = elapsed(W.ev[3], W.ev[4]);
-                }
+        if (stats->levels && k < stats->capacity_levels) {
+            bfs_level_stats& ls = stats->levels[k];
+            memset(&ls, 0, sizeof(ls));
+            ls.frontier_vertices = frontier;
+            ls.exchanged_vertices = (mode == BFS_MODE_COMPRESS_SIEVE) ? (int64_t)h[C_EXCHANGED] : p * frontier;
+            ls.column_hits = (int64_t)h[C_HITS];
+            ls.raw_bytes = raw_bytes;
+            ls.wah_bytes = (mode == BFS_MODE_PLAIN) ? 0 : (int64_t)h[C_WAH_WORDS] * (wbits / 8);
+            ls.edges_scanned = (int64_t)h[C_EDGES];
+            ls.row_wah_bytes = (int64_t)h[C_ROW_WORDS] * 4;
+            if (timing) {
+                ls.ms_compress_sieve = elapsed(W.ev[0], W.ev[1]);
+                ls.ms_communication = elapsed(W.ev[1], W.ev[2]);
+                ls.ms_traversing = elapsed(W.ev[2], W.ev[3]);
+                ls.ms_reducing = elapsed(W.ev[3], W.ev[4]);
             }
-            stats->n_levels = k + 1;
-            if (tracing) stats->trace_used = (int64_t)h[C_TRACE_USED];
         }
+        stats->n_levels = k + 1;
+        if (tracing) stats->trace_used = (int64_t)h[C_TRACE_USED];
         frontier = (int64_t)h[C_NEXT_COUNT];
-        visited += frontier;
-        if (frontier == 0) break;
-        std::swap(f, t);
+        if (frontier == 0 || k + 1 >= max_levels) break;
     }
     return BFS_OK;
 }

@@ -92,6 +92,16 @@ enum Counter : int {
     C_NUM
 };
 
+// The level loop of one search configuration as an instantiated CUDA graph
+// (a conditional WHILE node around one level).
+struct SearchGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int mode = -1, wbits = 0, rowx = 0;
+    int32_t* parent = nullptr;
+    int32_t* level = nullptr;
+};
+
 // Per-search workspace (owned by the graph, reused by every search).
 struct Workspace {
     int64_t bm_words = 0;       // uint32 words of an n-bit bitmap (padded)
@@ -111,6 +121,9 @@ struct Workspace {
     DevBuf enc_sums, enc_bases;  // chunk summaries of the parallel encoder
     DevBuf enc_flags;            // chunks with frontier bits
     DevBuf enc_done;             // slots finished by the encoder's scan
+    DevBuf ctl;                  // the level values kept on the device
+    SearchGraph sgraph[2];       // level loops as CUDA graphs, most recent configurations
+    int sgraph_next = 0;
     int64_t enc_cps = 0;         // encoder chunks per slot
     int64_t rowbuf_cap = 0, rowbuf_slots = 0;
     DevBuf tmp_parent, tmp_level;      // for searches with host outputs
