@@ -52,7 +52,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="s26", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="s26", choices=sorted(WORKLOADS) + ["msbfs20", "serve"],
+                    help="s12..s26er: single searches; msbfs20: one 64-root batch on scale 20; "
+                         "serve: Poisson query stream over 8 resident graphs")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="length of the serving stream")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrivals per second of the serving stream")
     ap.add_argument("--mode", type=int, default=2, help="0 plain, 1 compress, 2 compress+sieve")
     ap.add_argument("--wah-bits", type=int, default=32)
     ap.add_argument("--roots", type=int, default=0, help="override the number of roots")
@@ -211,6 +215,123 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------- our arm --
+
+# ------------------------------------------------------- batch and serving --
+def bench_batch(args, bfs, graphgen, torch, dev):
+    """64 roots as one bit-parallel batch (bfs_run_batch, one CUDA-graph launch)
+    on Kronecker scale 20, 8x8 grid: aggregate GTEPS = sum of m_r / batch time,
+    beside the same 64 roots searched one by one."""
+    n, src, dst = graphgen.edges(20, 16)
+    roots = graphgen.pick_roots(n, src, dst, 64)
+    g = bfs.Graph.from_edges(n, src, dst, p=8, mode=2)
+    deg = (torch.bincount(torch.from_numpy(src).to(dev).long(), minlength=n)
+           + torch.bincount(torch.from_numpy(dst).to(dev).long(), minlength=n))
+    shape = g.batch_autotune(roots)
+    levels = torch.empty((64, n), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        g.run_batch(roots, levels=levels)
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.run_batch(roots, levels=levels)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    m = [int((deg * (levels[r] >= 0)).sum().item()) // 2 for r in range(64)]
+    t_batch = sum(times) / len(times)
+    # the same roots one by one (device outputs, no statistics)
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    level = torch.empty(n, dtype=torch.int32, device=dev)
+    for r in roots[:4]:
+        g.run(int(r), parent, level)
+    t_single = 0.0
+    for r in roots:
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.run(int(r), parent, level)
+        e1.record()
+        e1.synchronize()
+        t_single += e0.elapsed_time(e1) / 1e3
+    # the batch's level rows equal the single searches' (both bit-exact with the
+    # oracle in the -m gpu tests)
+    exact = 0
+    for k in range(0, 64, 16):
+        g.run(int(roots[k]), parent, level)
+        exact += int(bool(torch.equal(level, levels[k])))
+    line = {"metric": "aggregate GTEPS of one 64-root bit-parallel batch", "value": round(sum(m) / t_batch / 1e9, 3),
+            "unit": "GTEPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * t_batch, 3), "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "kronecker-s20-ef16-grid8x8-batch64", "launch": "one CUDA graph per batch",
+                       "autotuned_shape": {"threads": shape[0], "ctas_per_sm": shape[1]},
+                       "l2": "flushed (256 MiB write) before every batch"},
+            "single_searches": {"value": round(sum(m) / t_single / 1e9, 3), "unit": "GTEPS",
+                                "ms_for_64": round(1e3 * t_single, 3)},
+            "validation": {"batch_rows_equal_single_searches": exact, "checked": 4}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_serve(args, bfs, graphgen, torch, dev):
+    """Continuous batching: a seeded Poisson stream (2,000 queries/s) of
+    single-root searches over 8 resident Kronecker graphs (scales 16-22 and 24),
+    each graph with up to 64 lanes; latency percentiles from the server and
+    aggregate GTEPS over the stream."""
+    import numpy as np
+    scales = [16, 17, 18, 19, 20, 21, 22, 24]
+    srv = bfs.Server(hbm_budget_bytes=48 << 30, max_lanes=64)
+    graphs = []
+    for sc in scales:
+        n, src, dst = graphgen.edges(sc, 16)
+        p = 4 if sc <= 18 else (8 if sc <= 22 else 16)
+        g = bfs.Graph.from_edges(n, src, dst, p=p)
+        deg = (torch.bincount(torch.from_numpy(src).to(dev).long(), minlength=n)
+               + torch.bincount(torch.from_numpy(dst).to(dev).long(), minlength=n))
+        graphs.append((srv.add_graph(g), n, g, deg, graphgen.pick_roots(n, src, dst, 256, seed=7 + sc)))
+    rng = np.random.default_rng(11)
+    rate = args.serve_rate
+    # warm-up: a few queries per graph
+    for gid, n, _, _, rts in graphs:
+        for r in rts[:4]:
+            srv.wait(srv.submit(gid, int(r)), n)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * args.serve_seconds * 1.2) + 16))
+    arrivals = arrivals[arrivals < args.serve_seconds]
+    which = rng.integers(0, len(graphs), size=len(arrivals))
+    pick = rng.integers(0, 256, size=len(arrivals))
+    base = srv.stats()
+    tickets = []
+    t0 = time.perf_counter()
+    for a_t, k, q in zip(arrivals, which, pick):
+        now = time.perf_counter() - t0
+        if a_t > now:
+            time.sleep(a_t - now)
+        gid, n, _, _, rts = graphs[k]
+        tickets.append((k, srv.submit(gid, int(rts[q]))))
+    edges = 0
+    for k, t in tickets:
+        gid, n, _, deg, _ = graphs[k]
+        lv = srv.wait(t, n, timeout_s=120.0)
+        edges += int((deg * (lv >= 0)).sum().item()) // 2
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    line = {"metric": f"serving: p50/p99 query latency and aggregate GTEPS (Poisson {rate:,.0f} queries/s)",
+            "value": round(edges / wall / 1e9, 3), "unit": "GTEPS", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "kronecker-s16..s22,s24-serving", "graphs": len(graphs), "rate_per_s": rate,
+                       "seconds": args.serve_seconds, "queries": len(tickets), "lanes_per_graph": 64},
+            "latency_us": {"p50": st["p50_us"], "p99": st["p99_us"], "max": st["max_us"]},
+            "server": {"completed": st["completed"] - base["completed"], "rejected": st["rejected"],
+                       "iterations": st["iterations"], "peak_lanes": st["peak_lanes"],
+                       "hbm_used_bytes": st["hbm_used_bytes"]},
+            "wall_s": round(wall, 3)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -237,6 +358,11 @@ def main():
         libbuild.build()
     if world > 1:
         dist.barrier()
+
+    if args.workload == "msbfs20":
+        return bench_batch(args, bfs, graphgen, torch, dev)
+    if args.workload == "serve":
+        return bench_serve(args, bfs, graphgen, torch, dev)
 
     scale, ef, p, kind, nroots, desc = WORKLOADS[args.workload]
     if args.roots:

@@ -70,7 +70,19 @@ struct MsState {
     // continuous batching (server): lane r's level of v is (iteration + 1) - lane_start[r]
     int32_t lane_start[64];
     unsigned long long alive;        // lanes that reached a new vertex in this iteration
+    int64_t nnz;                     // entries of the layout
+    unsigned long long err;          // first failed bounds check: code, then two values
+    unsigned long long err_a, err_b;
 };
+
+// A bounds check failed: keep the first one's code and values (the access is skipped).
+__device__ __forceinline__ void ms_fault(MsState* S, unsigned long long code, unsigned long long x,
+                                         unsigned long long y) {
+    if (atomicCAS(&S->err, 0ull, code) == 0ull) {
+        S->err_a = x;
+        S->err_b = y;
+    }
+}
 
 __device__ __forceinline__ int64_t ms_range_begin(const MsState& s, int64_t b) {
     const int64_t x = b * s.nb;
@@ -90,6 +102,9 @@ __global__ void ms_reset(MsState* S) {
     S->piece_next = 0;
     S->edges = 0;
     S->levels_done = 0;
+    S->err = 0;
+    S->err_a = 0;
+    S->err_b = 0;
 }
 
 __global__ void ms_clear(MsState* S) {
@@ -129,6 +144,7 @@ __global__ void ms_roots(MsState* S) {
 struct MsVisit {
     const MsState* s;
     __device__ __forceinline__ void operator()(int32_t v, int32_t u, unsigned long long fu) const {
+        if ((uint64_t)(uint32_t)v >= (uint64_t)s->n) { ms_fault(const_cast<MsState*>(s), 2, (uint32_t)v, (uint32_t)u); return; }
         const unsigned long long nb = fu & ~__ldg(s->vis + v);     // vis does not change during the expansion
         if (!nb) return;
         atomicOr(s->nxt + v, nb);
@@ -219,7 +235,8 @@ __global__ void ms_expand(MsState* S) {
         int64_t j = 0, ul = 0;
         if (q < nact) {
             u = act[q];
-            fu = f[u];
+            if ((uint64_t)(uint32_t)u >= (uint64_t)s.n) { ms_fault(S, 1, q, (uint32_t)u); u = 0; }
+            else fu = f[u];
             j = u / s.nb;
             ul = u - j * s.nb;
         }
@@ -257,6 +274,10 @@ __global__ void ms_pieces(MsState* S) {
         pc = __shfl_sync(0xffffffffu, pc, 0);
         if (pc >= np) break;
         const Item it = s.pieces[pc];
+        if ((uint64_t)(uint32_t)it.u >= (uint64_t)s.n || it.begin < 0 || it.begin + (int64_t)it.len > s.nnz) {
+            if (lane_id() == 0) ms_fault(S, 6, pc, (uint64_t)it.begin);
+            continue;
+        }
         ms_column(vis, s.ir, it.u, f[it.u], it.begin, it.len);
     }
 }
@@ -300,7 +321,11 @@ __global__ void __launch_bounds__(kMT) ms_reduce(MsState* S) {
             unsigned long long base = 0;
             if (lane_id() == 0) base = atomicAdd(&s.act_count[nxt_i], (unsigned long long)__popc(ball));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (nv) actn[base + __popc(ball & ((1u << lane_id()) - 1u))] = (int32_t)v;
+            const unsigned long long at = base + __popc(ball & ((1u << lane_id()) - 1u));
+            if (nv) {
+                if (at < (unsigned long long)s.n) actn[at] = (int32_t)v;
+                else ms_fault(S, 3, at, (uint64_t)v);
+            }
         }
     }
 }
@@ -348,6 +373,7 @@ __global__ void ms_admit_clear(MsState* S, unsigned long long mask, const int32_
     const int64_t total = (int64_t)nlanes * s.n;
     for (int64_t x = tid; x < total; x += stride) {
         const int r = lanes[x / s.n];
+        if (r < 0 || r >= 64) { ms_fault(S, 7, (uint64_t)x, (uint64_t)r); continue; }
         s.levels[(int64_t)r * s.n + x % s.n] = -1;
     }
     if (tid == 0) s.alive = 0;
@@ -360,6 +386,7 @@ __global__ void ms_admit_roots(MsState* S, const int32_t* lanes, const int32_t* 
     if (q >= nlanes) return;
     const int r = lanes[q];
     const int32_t v = roots[q];
+    if (r < 0 || r >= 64 || (uint64_t)(uint32_t)v >= (uint64_t)s.n) { ms_fault(S, 4, (uint64_t)r, (uint32_t)v); return; }
     const unsigned long long bit = 1ull << r;
     atomicOr(s.vis + v, bit);
     const unsigned long long old = atomicOr(s.f[s.cur] + v, bit);
@@ -367,7 +394,8 @@ __global__ void ms_admit_roots(MsState* S, const int32_t* lanes, const int32_t* 
     s.lane_start[r] = s.level;
     if (old == 0ull) {
         const unsigned long long pos = atomicAdd(&s.act_count[s.cur], 1ull);
-        s.act[s.cur][pos] = v;
+        if (pos < (unsigned long long)s.n) s.act[s.cur][pos] = v;
+        else ms_fault(S, 5, pos, (uint32_t)v);
     }
 }
 
@@ -443,6 +471,7 @@ bfs_status ms_ensure(bfs_graph* g) {
     h.p = L.p;
     h.nb = L.nb;
     h.n = n;
+    h.nnz = L.nnz;
     h.vis = c->vis.as<unsigned long long>();
     h.f[0] = c->f0.as<unsigned long long>();
     h.f[1] = c->f1.as<unsigned long long>();
@@ -790,7 +819,7 @@ bool serve_pass(bfs_server* s) {
                 lk.unlock(); fail(s, "iteration launch failed"); return false;
             }
             cudaMemcpyAsync(sg->h_alive, reinterpret_cast<char*>(S) + offsetof(MsState, alive),
-                            sizeof(unsigned long long), cudaMemcpyDeviceToHost, sg->stream);
+                            sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost, sg->stream);   // alive, nnz, err, a, b
             launched.push_back({sg, sg->running});
             int lanes_now = 0;
             for (ServeGraph* x : s->graphs) lanes_now += __builtin_popcountll(x->running);
@@ -801,6 +830,14 @@ bool serve_pass(bfs_server* s) {
     for (Launch& L : launched) {
         ServeGraph* sg = L.sg;
         if (cudaStreamSynchronize(sg->stream) != cudaSuccess) { fail(s, "iteration failed on the device"); return false; }
+        if (sg->h_alive[2]) {
+            char msg[160];
+            snprintf(msg, sizeof(msg), "bounds check %llu failed on the device (%llu, %llu)",
+                     (unsigned long long)sg->h_alive[2], (unsigned long long)sg->h_alive[3],
+                     (unsigned long long)sg->h_alive[4]);
+            fail(s, msg);
+            return false;
+        }
         const unsigned long long done = L.before & ~*sg->h_alive;
         const int64_t n = sg->g->L.n;
         std::vector<std::pair<int64_t, int32_t*>> fin;
@@ -896,7 +933,7 @@ bfs_status bfs_server_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id
     if (rc == BFS_OK) rc = sg->admit.alloc(sizeof(int32_t) * 128);
     if (rc == BFS_OK && cudaMallocHost(reinterpret_cast<void**>(&sg->h_admit), sizeof(int32_t) * 128) != cudaSuccess)
         rc = set_error(BFS_ERR_OUT_OF_MEMORY, "pinned host allocation");
-    if (rc == BFS_OK && cudaMallocHost(reinterpret_cast<void**>(&sg->h_alive), sizeof(unsigned long long)) != cudaSuccess)
+    if (rc == BFS_OK && cudaMallocHost(reinterpret_cast<void**>(&sg->h_alive), sizeof(unsigned long long) * 5) != cudaSuccess)
         rc = set_error(BFS_ERR_OUT_OF_MEMORY, "pinned host allocation");
     if (rc == BFS_OK && cudaStreamCreateWithFlags(&sg->stream, cudaStreamNonBlocking) != cudaSuccess)
         rc = set_error(BFS_ERR_CUDA, "stream creation failed");
@@ -975,11 +1012,15 @@ bfs_status bfs_server_wait(bfs_server_t s, int64_t ticket, int64_t timeout_us, i
     s->results_bytes -= sizeof(int32_t) * n;
     lk.unlock();
     bfs_status rc = BFS_OK;
+    // the result was allocated stream-ordered and completed before the request
+    // was marked done: copy it out and free it stream-ordered on the legacy stream
     if (level) {
-        cudaError_t e = cudaMemcpy(level, q.result, sizeof(int32_t) * n, cudaMemcpyDefault);
+        cudaError_t e = cudaMemcpyAsync(level, q.result, sizeof(int32_t) * n, cudaMemcpyDefault, 0);
         if (e != cudaSuccess) rc = cuda_error(e, "result copy", __FILE__, __LINE__);
     }
-    cudaFree(q.result);
+    cudaFreeAsync(q.result, 0);
+    cudaError_t e = cudaStreamSynchronize(0);
+    if (rc == BFS_OK && e != cudaSuccess) rc = cuda_error(e, "result copy", __FILE__, __LINE__);
     s->cv_work.notify_one();
     return rc;
 }
@@ -1016,7 +1057,8 @@ bfs_status bfs_server_destroy(bfs_server_t s) {
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
     for (auto& kv : s->req)
-        if (kv.second.result) cudaFree(kv.second.result);
+        if (kv.second.result) cudaFreeAsync(kv.second.result, 0);
+    cudaStreamSynchronize(0);
     for (ServeGraph* sg : s->graphs) {
         release_graph(sg);
         delete sg;
