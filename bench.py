@@ -302,27 +302,47 @@ def bench_serve(args, bfs, graphgen, torch, dev):
     which = rng.integers(0, len(graphs), size=len(arrivals))
     pick = rng.integers(0, 256, size=len(arrivals))
     base = srv.stats()
-    tickets = []
+    # one client thread per graph collects that graph's results as soon as they
+    # are done, so that results do not pile up against the HBM budget
+    import queue
+    import threading
+    tqs = [queue.Queue() for _ in graphs]
+    edges = [0] * len(graphs)
+
+    def collect(k):
+        gid, n, _, deg, _ = graphs[k]
+        while True:
+            t = tqs[k].get()
+            if t is None:
+                return
+            lv = srv.wait(t, n, timeout_s=120.0)
+            edges[k] += int((deg * (lv >= 0)).sum().item()) // 2
+
+    ths = [threading.Thread(target=collect, args=(k,)) for k in range(len(graphs))]
+    for th in ths:
+        th.start()
+    nsub = 0
     t0 = time.perf_counter()
     for a_t, k, q in zip(arrivals, which, pick):
         now = time.perf_counter() - t0
         if a_t > now:
             time.sleep(a_t - now)
         gid, n, _, _, rts = graphs[k]
-        tickets.append((k, srv.submit(gid, int(rts[q]))))
-    edges = 0
-    for k, t in tickets:
-        gid, n, _, deg, _ = graphs[k]
-        lv = srv.wait(t, n, timeout_s=120.0)
-        edges += int((deg * (lv >= 0)).sum().item()) // 2
+        tqs[k].put(srv.submit(gid, int(rts[q])))
+        nsub += 1
+    for tq in tqs:
+        tq.put(None)
+    for th in ths:
+        th.join()
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
     line = {"metric": f"serving: p50/p99 query latency and aggregate GTEPS (Poisson {rate:,.0f} queries/s)",
-            "value": round(edges / wall / 1e9, 3), "unit": "GTEPS", "n_gpus": 1, "higher_is_better": True,
+            "value": round(sum(edges) / wall / 1e9, 3), "unit": "GTEPS", "n_gpus": 1, "higher_is_better": True,
             "dtype": "int32", "data": "synthetic",
             "config": {"workload": "kronecker-s16..s22,s24-serving", "graphs": len(graphs), "rate_per_s": rate,
-                       "seconds": args.serve_seconds, "queries": len(tickets), "lanes_per_graph": 64},
+                       "seconds": args.serve_seconds, "queries": nsub, "lanes_per_graph": 64,
+                       "client": "one thread per graph collects its results as they finish"},
             "latency_us": {"p50": st["p50_us"], "p99": st["p99_us"], "max": st["max_us"]},
             "server": {"completed": st["completed"] - base["completed"], "rejected": st["rejected"],
                        "iterations": st["iterations"], "peak_lanes": st["peak_lanes"],

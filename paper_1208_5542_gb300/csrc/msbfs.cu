@@ -699,6 +699,8 @@ struct ServeGraph {
     std::deque<int64_t> pending;
     int64_t footprint = 0;
     int64_t iterations = 0;
+    bool inflight = false;           // an iteration is on the stream
+    unsigned long long before = 0;   // lanes running in it
 };
 
 struct Request {
@@ -777,97 +779,119 @@ void fail(bfs_server* s, const char* what) {
     s->cv_done.notify_all();
 }
 
-// One pass of the server loop: admit, launch one iteration per graph, retire.
-bool serve_pass(bfs_server* s) {
-    struct Launch { ServeGraph* sg; unsigned long long before; };
-    std::vector<Launch> launched;
-    {
-        std::unique_lock<std::mutex> lk(s->mu);
-        for (ServeGraph* sg : s->graphs) {
-            // admission into free lanes, while the results would fit in the budget
-            int nadm = 0;
-            unsigned long long mask = 0;
-            const int64_t row = 4 * sg->g->L.n;
-            for (int r = 0; r < sg->lanes && !sg->pending.empty(); ++r) {
-                if (sg->running & (1ull << r)) continue;
-                if (s->used + s->results_bytes + row > s->budget) break;     // wait for results to be collected
-                const int64_t t = sg->pending.front();
-                sg->pending.pop_front();
-                --s->queued;
-                Request& q = s->req[t];
-                q.state = 1;
-                sg->lane_ticket[r] = t;
-                sg->running |= 1ull << r;
-                sg->h_admit[nadm] = r;
-                sg->h_admit[64 + nadm] = q.root;
-                mask |= 1ull << r;
-                ++nadm;
-            }
-            if (!sg->running) continue;
-            MsState* S = sg->g->ms->state.as<MsState>();
-            if (nadm) {
-                int32_t* d = sg->admit.as<int32_t>();
-                if (cudaMemcpyAsync(d, sg->h_admit, sizeof(int32_t) * 128, cudaMemcpyHostToDevice, sg->stream) != cudaSuccess) {
-                    lk.unlock(); fail(s, "admission copy failed"); return false;
-                }
-                ms_admit_clear<<<ms_sm_count() * 4, kMT, 0, sg->stream>>>(S, mask, d, nadm);
-                ms_admit_roots<<<1, 64, 0, sg->stream>>>(S, d, d + 64, nadm);
-            } else {
-                ms_clear_alive<<<1, 1, 0, sg->stream>>>(S);
-            }
-            if (cudaGraphLaunch(sg->step, sg->stream) != cudaSuccess) {
-                lk.unlock(); fail(s, "iteration launch failed"); return false;
-            }
-            cudaMemcpyAsync(sg->h_alive, reinterpret_cast<char*>(S) + offsetof(MsState, alive),
-                            sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost, sg->stream);   // alive, nnz, err, a, b
-            launched.push_back({sg, sg->running});
-            int lanes_now = 0;
-            for (ServeGraph* x : s->graphs) lanes_now += __builtin_popcountll(x->running);
-            if (lanes_now > s->peak_lanes) s->peak_lanes = lanes_now;
-        }
+// Every graph advances on its own: when its iteration has finished (a stream
+// query, no waiting on the other graphs) its lanes whose frontier emptied are
+// retired, queued requests are admitted into free lanes, and the next
+// iteration is launched.  Returns whether any graph made progress.
+bool finish_iteration(bfs_server* s, ServeGraph* sg) {
+    if (sg->h_alive[2]) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "bounds check %llu failed on the device (%llu, %llu)",
+                 (unsigned long long)sg->h_alive[2], (unsigned long long)sg->h_alive[3],
+                 (unsigned long long)sg->h_alive[4]);
+        fail(s, msg);
+        return false;
     }
-    if (launched.empty()) return false;
-    for (Launch& L : launched) {
-        ServeGraph* sg = L.sg;
-        if (cudaStreamSynchronize(sg->stream) != cudaSuccess) { fail(s, "iteration failed on the device"); return false; }
-        if (sg->h_alive[2]) {
-            char msg[160];
-            snprintf(msg, sizeof(msg), "bounds check %llu failed on the device (%llu, %llu)",
-                     (unsigned long long)sg->h_alive[2], (unsigned long long)sg->h_alive[3],
-                     (unsigned long long)sg->h_alive[4]);
-            fail(s, msg);
-            return false;
-        }
-        const unsigned long long done = L.before & ~*sg->h_alive;
-        const int64_t n = sg->g->L.n;
-        std::vector<std::pair<int64_t, int32_t*>> fin;
-        for (int r = 0; r < sg->lanes; ++r) {
-            if (!(done & (1ull << r))) continue;
-            void* buf = nullptr;
-            if (cudaMallocAsync(&buf, sizeof(int32_t) * n, sg->stream) != cudaSuccess) { fail(s, "result allocation failed"); return false; }
-            cudaMemcpyAsync(buf, sg->levels.as<int32_t>() + (int64_t)r * n, sizeof(int32_t) * n,
-                            cudaMemcpyDeviceToDevice, sg->stream);
-            fin.push_back({sg->lane_ticket[r], static_cast<int32_t*>(buf)});
-            sg->lane_ticket[r] = -1;
-        }
-        if (!fin.empty() && cudaStreamSynchronize(sg->stream) != cudaSuccess) { fail(s, "result copy failed"); return false; }
-        std::lock_guard<std::mutex> lk(s->mu);
-        sg->running &= ~done;
-        ++sg->iterations;
-        ++s->iterations;
-        const auto now = std::chrono::steady_clock::now();
-        for (auto& f : fin) {
-            Request& q = s->req[f.first];
-            q.state = 2;
-            q.result = f.second;
-            q.t_done = now;
-            s->results_bytes += sizeof(int32_t) * n;
-            ++s->completed;
-            s->lat_us.push_back(std::chrono::duration<double, std::micro>(now - q.t_submit).count());
-        }
-        if (!fin.empty()) s->cv_done.notify_all();
+    const unsigned long long done = sg->before & ~sg->h_alive[0];
+    const int64_t n = sg->g->L.n;
+    std::vector<std::pair<int64_t, int32_t*>> fin;
+    for (int r = 0; r < sg->lanes; ++r) {
+        if (!(done & (1ull << r))) continue;
+        void* buf = nullptr;
+        if (cudaMallocAsync(&buf, sizeof(int32_t) * n, sg->stream) != cudaSuccess) { fail(s, "result allocation failed"); return false; }
+        cudaMemcpyAsync(buf, sg->levels.as<int32_t>() + (int64_t)r * n, sizeof(int32_t) * n,
+                        cudaMemcpyDeviceToDevice, sg->stream);
+        fin.push_back({sg->lane_ticket[r], static_cast<int32_t*>(buf)});
+        sg->lane_ticket[r] = -1;
     }
+    if (!fin.empty() && cudaStreamSynchronize(sg->stream) != cudaSuccess) { fail(s, "result copy failed"); return false; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    sg->running &= ~done;
+    ++sg->iterations;
+    ++s->iterations;
+    const auto now = std::chrono::steady_clock::now();
+    for (auto& f : fin) {
+        Request& q = s->req[f.first];
+        q.state = 2;
+        q.result = f.second;
+        q.t_done = now;
+        s->results_bytes += sizeof(int32_t) * n;
+        ++s->completed;
+        s->lat_us.push_back(std::chrono::duration<double, std::micro>(now - q.t_submit).count());
+    }
+    if (!fin.empty()) s->cv_done.notify_all();
     return true;
+}
+
+bool launch_iteration(bfs_server* s, ServeGraph* sg) {
+    std::unique_lock<std::mutex> lk(s->mu);
+    // admission into free lanes, while the results would fit in the budget
+    int nadm = 0;
+    unsigned long long mask = 0;
+    const int64_t row = 4 * sg->g->L.n;
+    for (int r = 0; r < sg->lanes && !sg->pending.empty(); ++r) {
+        if (sg->running & (1ull << r)) continue;
+        if (s->used + s->results_bytes + row > s->budget) break;     // wait for results to be collected
+        const int64_t t = sg->pending.front();
+        sg->pending.pop_front();
+        --s->queued;
+        Request& q = s->req[t];
+        q.state = 1;
+        sg->lane_ticket[r] = t;
+        sg->running |= 1ull << r;
+        sg->h_admit[nadm] = r;
+        sg->h_admit[64 + nadm] = q.root;
+        mask |= 1ull << r;
+        ++nadm;
+    }
+    if (!sg->running) return false;
+    MsState* S = sg->g->ms->state.as<MsState>();
+    if (nadm) {
+        int32_t* d = sg->admit.as<int32_t>();
+        if (cudaMemcpyAsync(d, sg->h_admit, sizeof(int32_t) * 128, cudaMemcpyHostToDevice, sg->stream) != cudaSuccess) {
+            lk.unlock(); fail(s, "admission copy failed"); return false;
+        }
+        ms_admit_clear<<<ms_sm_count() * 4, kMT, 0, sg->stream>>>(S, mask, d, nadm);
+        ms_admit_roots<<<1, 64, 0, sg->stream>>>(S, d, d + 64, nadm);
+    } else {
+        ms_clear_alive<<<1, 1, 0, sg->stream>>>(S);
+    }
+    if (cudaGraphLaunch(sg->step, sg->stream) != cudaSuccess) {
+        lk.unlock(); fail(s, "iteration launch failed"); return false;
+    }
+    cudaMemcpyAsync(sg->h_alive, reinterpret_cast<char*>(S) + offsetof(MsState, alive),
+                    sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost, sg->stream);   // alive, nnz, err, a, b
+    sg->before = sg->running;
+    sg->inflight = true;
+    int lanes_now = 0;
+    for (ServeGraph* x : s->graphs) lanes_now += __builtin_popcountll(x->running);
+    if (lanes_now > s->peak_lanes) s->peak_lanes = lanes_now;
+    return true;
+}
+
+bool serve_pass(bfs_server* s) {
+    std::vector<ServeGraph*> gs;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        gs = s->graphs;
+    }
+    bool progressed = false;
+    for (ServeGraph* sg : gs) {
+        if (sg->inflight) {
+            const cudaError_t q = cudaStreamQuery(sg->stream);
+            if (q == cudaErrorNotReady) continue;
+            sg->inflight = false;
+            if (q != cudaSuccess) { fail(s, "iteration failed on the device"); return false; }
+            if (!finish_iteration(s, sg)) return false;
+            progressed = true;
+        }
+        if (launch_iteration(s, sg)) progressed = true;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->failed) return false;
+        }
+    }
+    return progressed;
 }
 
 void serve_loop(bfs_server* s) {
@@ -875,14 +899,26 @@ void serve_loop(bfs_server* s) {
     for (;;) {
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            if (s->stop || s->failed) return;
+            if (s->stop || s->failed) break;
             bool work = false;
-            for (ServeGraph* sg : s->graphs) work |= (sg->running != 0) || !sg->pending.empty();
+            for (ServeGraph* sg : s->graphs) work |= sg->inflight || (sg->running != 0) || !sg->pending.empty();
             if (!work) s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
-            if (s->stop) return;
+            if (s->stop) break;
         }
-        serve_pass(s);
+        if (!serve_pass(s)) {            // iterations in flight and nothing finished yet
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (s->stop || s->failed) break;
+            s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        }
     }
+    // leave no iteration in flight
+    std::vector<ServeGraph*> gs;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        gs = s->graphs;
+    }
+    for (ServeGraph* sg : gs)
+        if (sg->inflight) { cudaStreamSynchronize(sg->stream); sg->inflight = false; }
 }
 
 }  // namespace
