@@ -467,6 +467,7 @@ def main():
 
     # roofline of the expansion kernel (algorithmic bytes per launch / event time per launch)
     ex_bytes = ex_ms = 0.0
+    ex_entries = 0
     launches = 0
     levels_tot = 0
     per_level = {}
@@ -480,6 +481,7 @@ def main():
                 # + streams decoded + one parent word per discovered vertex
                 ex_bytes += 4 * ls["edges_scanned"] + 12 * ls["column_hits"] + wah_read + 4 * discovered
                 ex_ms += ls["ms_traversing"]
+                ex_entries += ls["edges_scanned"]
                 launches += 1
                 agg = per_level.setdefault(k, {"frontier": 0, "exchanged": 0, "raw_bytes": 0, "wah_bytes": 0,
                                                 "hits": 0, "n": 0})
@@ -498,6 +500,14 @@ def main():
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = (ex_bytes / launches) / (ex_ms / launches / 1e3) / 1e9 if launches and ex_ms > 0 else 0.0
+    # the bound that binds the expansion on its L1/L2 path: one scattered read
+    # (the visited test) per entry, against this GPU's measured scattered-read
+    # rate on a region the size of one block-row's visited bits
+    scatter_region = max(4096, (n // p + 7) // 8)
+    scatter_peak = bfs.measure_scatter_reads(scatter_region) / 1e9
+    scatter_achieved = ex_entries / (ex_ms / 1e3) / 1e9 if ex_ms > 0 else 0.0
+    nb_range = -(-n // p)
+    window = 8 * -(-nb_range // 32) + 4096 <= 227 * 1024      # the library's row-window rule
     traffic = ncu_traffic(args.workload, MODE_NAMES[args.mode], ex_bytes / launches if launches else 0)
     exch = []
     for k in sorted(per_level):
@@ -609,7 +619,14 @@ def main():
                      "traffic_source": ("DRAM/algorithmic ratio of an ncu capture at scale 24 (same 16x16 grid and "
                                         "visiting path) times this launch's algorithmic bytes") if traffic else None,
                      "algorithmic_bytes_per_launch": round(ex_bytes / launches) if launches else 0,
-                     "avg_launch_ms": round(ex_ms / launches, 5) if launches else 0, "launches": launches},
+                     "avg_launch_ms": round(ex_ms / launches, 5) if launches else 0, "launches": launches,
+                     "scattered": {"bound": "scattered 4-byte reads (one visited test per entry)",
+                                   "achieved": round(scatter_achieved, 1), "peak": round(scatter_peak, 1),
+                                   "unit": "G entries/s vs G reads/s", "frac": round(scatter_achieved / scatter_peak, 4)
+                                   if scatter_peak else None, "region_bytes": scatter_region,
+                                   "peak_source": "measured in this run (bfs_measure_scatter_reads)",
+                                   "visited_test": "shared-memory row window (this bound does not apply)" if window
+                                   else "through L1/L2, one scattered read per entry"}},
         "phases_ms_per_search": phases,
         "exchange_per_level": exch,
         "cpu_baseline": cpu,

@@ -343,6 +343,25 @@ BFS_API bfs_status bfs_wah_decode(const void *words, int64_t nwords, int64_t nbi
 BFS_API bfs_status bfs_wah_decode_static(const void *words, int64_t nwords, int64_t nbits, int32_t word_bits,
                                          uint32_t *bits, void *cuda_stream);
 
+/* ------------------------------------------------------------ diagnostics -- */
+
+/* bfs_measure_scatter_reads -- the rate of scattered 4-byte reads of this GPU,
+ * the bound of the expansion's visited test when it goes through L1/L2 (one
+ * read at a random address per adjacency entry).  The paper has no counterpart:
+ * it is a measurement the library offers so that a caller can set the
+ * expansion's entry rate against the rate the memory system serves.
+ *   region_bytes   size of the region read (>= 4096 and <= 1 GiB; the
+ *                  expansion reads its visited bitmap slice: n/p/8 bytes)
+ *   iterations     reads per thread (>= 1; 4096 is enough for a stable rate)
+ *   reads_per_s    out: reads per second (one 1024-thread CTA per SM, every
+ *                  thread reading `iterations` words at hashed addresses)
+ *   cuda_stream    stream for the launches (NULL: legacy default stream)
+ * The region is allocated and freed by the call.  Synchronises `cuda_stream`.
+ * Errors: BFS_ERR_INVALID_ARG (NULL output, sizes outside the ranges),
+ * BFS_ERR_OUT_OF_MEMORY, BFS_ERR_CUDA. */
+BFS_API bfs_status bfs_measure_scatter_reads(int64_t region_bytes, int32_t iterations, double *reads_per_s,
+                                             void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

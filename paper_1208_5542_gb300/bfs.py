@@ -280,3 +280,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def measure_scatter_reads(region_bytes: int = 512 << 10, iterations: int = 4096, stream=None) -> float:
+    """Scattered 4-byte reads per second of this GPU (``bfs_measure_scatter_reads``)."""
+    out = ctypes.c_double()
+    check(native.lib().bfs_measure_scatter_reads(int(region_bytes), int(iterations), ctypes.byref(out),
+                                                 _stream_ptr(stream)))
+    return float(out.value)

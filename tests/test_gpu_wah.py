@@ -72,3 +72,14 @@ def test_decode_rejects_malformed_streams():
     # the oracle rejects the same streams
     for bad, nb in ((good[:-1], len(bits)), ([0x80000001, 0b1000], 34)):
         assert oracle.wah_decode(np.asarray(bad, np.uint64), nb) is None
+
+
+def test_scatter_read_measurement():
+    """The diagnostic entry point returns a plausible positive rate and rejects bad sizes."""
+    from paper_1208_5542_gb300 import bfs, build
+    from paper_1208_5542_gb300.native import BfsError
+    build.build()
+    r = bfs.measure_scatter_reads(512 << 10, 256)
+    assert 1e9 < r < 1e14
+    with pytest.raises(BfsError):
+        bfs.measure_scatter_reads(100, 256)
