@@ -831,7 +831,6 @@ __global__ void __launch_bounds__(kEW) enc_chunk_write32(EncodeArgs a, const Chu
         if (lane == 0) hprev = -1;
         const int li0 = incl - hc;                    // local index of the word open before this lane's groups
         const int64_t st0 = hprev >= 0 ? tb + hprev : cb.run_start;   // start of the run open before them
-        bool wrote0 = false, wroteH = false;
         if (nv > 0) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
@@ -840,17 +839,29 @@ __global__ void __launch_bounds__(kEW) enc_chunk_write32(EncodeArgs a, const Chu
                 const int li = li0 + __popc(hb);
                 if (lit & bit) {
                     ob[opad(li)] = __brev(lane_group(cwd, i)) >> 1;
-                    wroteH |= li == H;
                 } else if ((zend | oend) & bit) {
                     const int64_t start = hb ? tb + r0 + 31 - __clz(hb) : st0;
                     ob[opad(li)] = 0x80000000u | ((oend & bit) ? 0x40000000u : 0u) | (uint32_t)(tb + r0 + i - start + 1);
-                    wrote0 |= li == 0;
-                    wroteH |= li == H;
                 }
-                if ((hm & bit) && ub && ((cb.words + li - 1) & 31) == 0) ub[(cb.words + li - 1) >> 5] = tb + r0 + i;
+            }
+            // the decoder's unit base: the lane's heads open words cb.words + li0 .. + hc - 1;
+            // at most one of them is a multiple of 32
+            if (ub && hc > 0) {
+                int j = (int)((1 - cb.words - li0) & 31);          // head ordinal (1-based) whose word is 32k
+                if (j == 0) j = 32;
+                if (j <= hc) ub[(cb.words - 1 + li0 + j) >> 5] = tb + r0 + select32(hm, j - 1);
             }
         }
-        const bool w0 = __any_sync(0xffffffffu, wrote0), wH = __any_sync(0xffffffffu, wroteH);
+        // word 0 (a run carried in) is written here when the chunk's first group
+        // continues it and the run ends in the chunk; word H (the last opened)
+        // when the chunk's last group is a literal or ends its run
+        const uint32_t hm0 = __shfl_sync(0xffffffffu, hm, 0);
+        const int lastl = (ng - 1) >> 5, lastb = (ng - 1) & 31;
+        const uint32_t lit_l = __shfl_sync(0xffffffffu, lit, lastl);
+        const uint32_t end_l = __shfl_sync(0xffffffffu, zend | oend, lastl);
+        const bool last_lit = (lit_l >> lastb) & 1u, last_end = (end_l >> lastb) & 1u;
+        const bool w0 = !(hm0 & 1u) && (H > 0 || last_end);
+        const bool wH = H > 0 ? (last_lit || last_end) : w0;         // with no head, word H is word 0
         __syncwarp();
         // words cb.words .. cb.words + H - 2 are always complete here; the one
         // before (a run carried in) and the last one (a run carried out) only
