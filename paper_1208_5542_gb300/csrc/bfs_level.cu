@@ -1095,8 +1095,9 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             }
             BFS_CUDA_TRY(cudaGetLastError());
         } else {
+            // the exchanged-vertex count is a statistic: only the stepwise loop asks for it
             BFS_TRY(launch_wah_encode_parallel(ea, wbits, W.enc_sums.ptr, W.enc_bases.ptr, W.enc_cps,
-                                               W.enc_flags.ptr, ctr + C_EXCHANGED, sm_count() * 6, s));
+                                               W.enc_flags.ptr, host ? ctr + C_EXCHANGED : nullptr, sm_count() * 6, s));
             if (host && timing) cudaEventRecord(W.ev[1], s);
             if (host && tracing && k < stats->capacity_levels) {
                 const int u32pw = wbits / 32;

@@ -462,57 +462,75 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
         cs.last_head = c * kTile;
         return cs;
     };
-    int64_t words = 0, hmax = -1;
-    int prev_last = -1;
-    for (int64_t c0 = 0; c0 < nch; c0 += 32) {
-        const int64_t c = c0 + lane;
-        ChunkSum cs;
-        cs.heads = 0;
-        cs.types = G_NONE | (G_NONE << 8);
-        cs.last_head = -1;
-        if (c < nch) cs = sum_of(c);
-        const int first = (int)(cs.types & 0xff), last = (int)((cs.types >> 8) & 0xff);
-        int before = __shfl_up_sync(0xffffffffu, last, 1);
-        if (lane == 0) before = prev_last;
-        const bool merge = (c < nch) && before == first && first != G_LIT && before >= 0;
-        const int64_t eff = (c < nch) ? (int64_t)cs.heads - (merge ? 1 : 0) : 0;
-        const int64_t h = (c < nch) ? ((merge && cs.heads == 1) ? (int64_t)-1 : cs.last_head) : (int64_t)-1;
-        int64_t incl = eff, hin = h;
+    // Lane l takes chunks [l*K, (l+1)*K) in order.  Pass 1: the lane's summary
+    // (words, last head, first and last type) with the merges between its own
+    // chunks applied; a scan over the lanes with the merge rule gives every lane
+    // what comes before it; pass 2 walks the chunks again with that carry.
+    struct Agg { int64_t w, h; int f, l; };       // f, l < 0: no chunk
+    auto combine = [](const Agg& A, const Agg& B) -> Agg {   // A then B
+        if (B.f < 0) return A;
+        if (A.f < 0) return B;
+        const bool m = A.l == B.f && B.f != G_LIT;           // B's first group continues A's last run
+        Agg R;
+        R.w = A.w + B.w - (m ? 1 : 0);
+        R.h = (m && B.w == 1) ? A.h : (A.h > B.h ? A.h : B.h);
+        R.f = A.f;
+        R.l = B.l;
+        return R;
+    };
+    const int64_t K = (nch + 31) / 32;
+    const int64_t c_lo = (int64_t)lane * K, c_hi = (c_lo + K < nch) ? c_lo + K : nch;
+    Agg mine{0, -1, -1, -1};
+    for (int64_t c = c_lo; c < c_hi; ++c) {
+        const ChunkSum cs = sum_of(c);
+        Agg one{(int64_t)cs.heads, cs.last_head, (int)(cs.types & 0xff), (int)((cs.types >> 8) & 0xff)};
+        mine = combine(mine, one);
+    }
+    Agg incl = mine;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, incl, d);
-            const int64_t z = __shfl_up_sync(0xffffffffu, hin, d);
-            if (lane >= d) { incl += y; hin = z > hin ? z : hin; }
-        }
-        int64_t hex = __shfl_up_sync(0xffffffffu, hin, 1);
-        if (lane == 0) hex = -1;
-        hex = hex > hmax ? hex : hmax;
-        int nxt = __shfl_down_sync(0xffffffffu, first, 1);
-        if (c < nch) {
-            ChunkBase cb;
-            cb.words = words + incl - eff;
-            cb.run_start = merge ? hex : c * kTile;
-            cb.prev_type = before;
-            if (c + 1 >= nch) nxt = G_NONE;
-            else if (lane == 31) nxt = (int)(sum_of(c + 1).types & 0xff);
-            cb.next_type = nxt;
-            bases[(int64_t)s * cps + c] = cb;
-            if (!flags[(int64_t)s * cps + c]) {
-                // an all-zero chunk: its zero run opens a word here unless it merges
-                if (!merge && ub && (cb.words & 31) == 0) ub[cb.words >> 5] = c * kTile;
-                if (nxt != G_ZERO) {     // the run ends at the chunk's last group
-                    const int64_t tend = ((c + 1) * kTile < G) ? (c + 1) * kTile : G;
-                    const int64_t start = merge ? cb.run_start : c * kTile;
-                    out[merge ? cb.words - 1 : cb.words] = fill_word<W>(G_ZERO, (uint64_t)(tend - start));
-                }
+    for (int d = 1; d < 32; d <<= 1) {
+        Agg y;
+        y.w = __shfl_up_sync(0xffffffffu, incl.w, d);
+        y.h = __shfl_up_sync(0xffffffffu, incl.h, d);
+        y.f = __shfl_up_sync(0xffffffffu, incl.f, d);
+        y.l = __shfl_up_sync(0xffffffffu, incl.l, d);
+        if (lane >= d) incl = combine(y, incl);
+    }
+    Agg before_me;
+    before_me.w = __shfl_up_sync(0xffffffffu, incl.w, 1);
+    before_me.h = __shfl_up_sync(0xffffffffu, incl.h, 1);
+    before_me.f = __shfl_up_sync(0xffffffffu, incl.f, 1);
+    before_me.l = __shfl_up_sync(0xffffffffu, incl.l, 1);
+    if (lane == 0) before_me = Agg{0, -1, -1, -1};
+    int64_t words = before_me.w, hmax = before_me.h;
+    int prev_last = before_me.l;
+    for (int64_t c = c_lo; c < c_hi; ++c) {
+        const ChunkSum cs = sum_of(c);
+        const int first = (int)(cs.types & 0xff), last = (int)((cs.types >> 8) & 0xff);
+        const bool merge = prev_last >= 0 && prev_last == first && first != G_LIT;
+        const int64_t eff = (int64_t)cs.heads - (merge ? 1 : 0);
+        const int64_t h = (merge && cs.heads == 1) ? (int64_t)-1 : cs.last_head;
+        ChunkBase cb;
+        cb.words = words;
+        cb.run_start = merge ? hmax : c * kTile;
+        cb.prev_type = prev_last;
+        const int nxt = (c + 1 < nch) ? (int)(sum_of(c + 1).types & 0xff) : G_NONE;
+        cb.next_type = nxt;
+        bases[(int64_t)s * cps + c] = cb;
+        if (!flags[(int64_t)s * cps + c]) {
+            // an all-zero chunk: its zero run opens a word here unless it merges
+            if (!merge && ub && (cb.words & 31) == 0) ub[cb.words >> 5] = c * kTile;
+            if (nxt != G_ZERO) {     // the run ends at the chunk's last group
+                const int64_t tend = ((c + 1) * kTile < G) ? (c + 1) * kTile : G;
+                const int64_t start = merge ? cb.run_start : c * kTile;
+                out[merge ? cb.words - 1 : cb.words] = fill_word<W>(G_ZERO, (uint64_t)(tend - start));
             }
         }
-        words += __shfl_sync(0xffffffffu, incl, 31);
-        const int64_t hb = __shfl_sync(0xffffffffu, hin, 31);
-        hmax = hb > hmax ? hb : hmax;
-        const int last_lane = (c0 + 32 > nch) ? (int)((nch - 1) % 32) : 31;
-        prev_last = __shfl_sync(0xffffffffu, last, last_lane);
+        words += eff;
+        hmax = h > hmax ? h : hmax;
+        prev_last = last;
     }
+    words = __shfl_sync(0xffffffffu, incl.w, 31);    // the slot's words before the active word
     if (lane == 0) {
         int64_t total = words;
         if (r > 0) {
@@ -725,8 +743,9 @@ __global__ void __launch_bounds__(kEW) enc_chunk_sums32(EncodeArgs a, ChunkSum* 
         const int ng = (int)(tend - tb);
         uint32_t cwd[32];
         lane_cwords(st, cwd);
-        // set bits of the lane's groups: its 31 words, the last lane's cut at the chunk end
-        {
+        // set bits of the lane's groups (a statistic, when asked for): its 31
+        // words, the last lane's cut at the chunk end
+        if (setbits) {
             const int nv = ng - 32 * lane;
             if (nv >= 32) {
                 uint32_t cnt = 0;
