@@ -36,8 +36,6 @@
 
 namespace bfsgb {
 
-bfs_status launch_wah_encode_counted(const EncodeArgs& a, int wah_bits, unsigned long long* setbits,
-                                     cudaStream_t st);
 int64_t parallel_encode_chunks(int64_t max_nbits, int wah_bits);
 bfs_status launch_wah_encode_parallel(const EncodeArgs& a, int wah_bits, void* sums, void* bases, int64_t cps,
                                       void* flags, unsigned long long* setbits, int grid, cudaStream_t st);

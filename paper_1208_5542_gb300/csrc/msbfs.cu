@@ -84,11 +84,6 @@ __device__ __forceinline__ void ms_fault(MsState* S, unsigned long long code, un
     }
 }
 
-__device__ __forceinline__ int64_t ms_range_begin(const MsState& s, int64_t b) {
-    const int64_t x = b * s.nb;
-    return x < s.n ? x : s.n;
-}
-
 // ------------------------------------------------------------------ init --
 __global__ void ms_reset(MsState* S) {
     for (int r = 0; r < 64; ++r) S->lane_start[r] = 0;

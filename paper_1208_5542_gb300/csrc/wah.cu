@@ -912,17 +912,6 @@ bfs_status launch_wah_encode(const EncodeArgs& a, int wah_bits, cudaStream_t st)
     return BFS_OK;
 }
 
-bfs_status launch_wah_encode_counted(const EncodeArgs& a, int wah_bits, unsigned long long* setbits,
-                                     cudaStream_t st) {
-    if (a.nslots <= 0) return BFS_OK;
-    if (wah_bits == 32)
-        wah_encode_kernel<uint32_t><<<a.nslots, kNT, 0, st>>>(a, setbits);
-    else
-        wah_encode_kernel<unsigned long long><<<a.nslots, kNT, 0, st>>>(a, setbits);
-    BFS_CUDA_TRY(cudaGetLastError());
-    return BFS_OK;
-}
-
 int64_t parallel_encode_chunks(int64_t max_nbits, int wah_bits) {
     const int64_t G = max_nbits / (wah_bits - 1);
     return (G + kTile - 1) / kTile + 1;
