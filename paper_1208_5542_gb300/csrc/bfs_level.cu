@@ -519,13 +519,20 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
         const uint32_t glen = (xw < count) ? (uint32_t)word_groups<W>(y) : 0u;
         const uint32_t gincl = warp_incl_sum(glen);
         const int64_t gs = a.chunk_base[stream * a.chunks_per_slot + k] + (int64_t)(gincl - glen);
+        // per lane: its word's vertices as (first vertex of the word, bits in
+        // group order; a 1-fill is a run, marked by an empty bit pattern)
         uint32_t c = 0;
+        W wbits = W(0);
+        int64_t wbase = 0;
         if (xw < count) {
             if (gs < G) {
+                wbase = gs * GB;
                 if (is_fill<W>(y)) c = (y & T::VAL) ? (uint32_t)(glen * GB) : 0u;
-                else c = (uint32_t)T::popc(T::from_payload(y));
+                else { wbits = T::from_payload(y); c = (uint32_t)T::popc(wbits); }
             } else if (r > 0) {
-                c = (uint32_t)T::popc(T::from_active(y, r));      // the active word
+                wbase = G * GB;
+                wbits = T::from_active(y, r);                     // the active word
+                c = (uint32_t)T::popc(wbits);
             }
         }
         const uint32_t cincl = warp_incl_sum(c);
@@ -540,18 +547,15 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
         auto item = [&](uint32_t q0, int32_t& u, int64_t& begin, uint32_t& len) {
             const uint32_t q = q0 + lane_id();
             const int o = owner_lane(cexcl, q < items ? q : items - 1);
-            const W yy = __shfl_sync(0xffffffffu, y, o);
-            const int64_t g0 = __shfl_sync(0xffffffffu, gs, o);
+            const W ob = __shfl_sync(0xffffffffu, wbits, o);
+            const int64_t obase = __shfl_sync(0xffffffffu, wbase, o);
             const uint32_t oex = __shfl_sync(0xffffffffu, cexcl, o);
             u = 0;
             begin = 0;
             len = 0;
             if (q < items) {
                 const int kk = (int)(q - oex);
-                int64_t ul;
-                if (g0 >= G) ul = G * GB + T::select(T::from_active(yy, r), kk);
-                else if (is_fill<W>(yy)) ul = g0 * GB + kk;
-                else ul = g0 * GB + T::select(T::from_payload(yy), kk);
+                const int64_t ul = obase + (ob ? T::select(ob, kk) : kk);   // empty pattern: a 1-fill
                 column_of(a, bv, ul, a.mode != BFS_MODE_COMPRESS_SIEVE, &begin, &len);
                 u = (int32_t)(jb + ul);
                 prefetch_column(a, begin, len);
