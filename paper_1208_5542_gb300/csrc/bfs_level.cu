@@ -50,6 +50,10 @@ constexpr int kXW = kXT / 32;       // warps of the expansion CTAs
 constexpr uint32_t kCoop = 32;      // columns of at least this many entries take the whole warp
 constexpr uint32_t kHub = 1024;     // columns longer than this are cut into pieces
 constexpr uint32_t kPiece = 1024;   // entries per piece
+#ifndef BFS_GUIDE
+#define BFS_GUIDE 2
+#endif
+constexpr int64_t kGuide = BFS_GUIDE;  // a grab takes 1/(kGuide * warps) of the units left in the row
 constexpr int64_t kSmemLimit = 227 * 1024;
 
 // Per-level values that the device keeps from level to level, so that one
@@ -458,14 +462,23 @@ __device__ __forceinline__ void row_affine(const LevelArgs& a, unsigned long lon
     while (row >= 0) {
         const int64_t nu = units_in_row(row);
         for (;;) {
-            int64_t x = 0;
+            // guided hand-out: a share of what is left (at least `batch`), so
+            // that early grabs are large and the last ones small
+            int64_t x = 0, b = batch;
             if (lane_id() == 0) {
-                x = ((int64_t)*reinterpret_cast<volatile unsigned long long*>(counters + row) < nu)
-                        ? (int64_t)atomicAdd(counters + row, (unsigned long long)batch) : nu;
+                const int64_t cur = (int64_t)*reinterpret_cast<volatile unsigned long long*>(counters + row);
+                if (cur < nu) {
+                    const int64_t g = (nu - cur) / (kGuide * (int64_t)gridDim.x * kXW);
+                    b = g > batch ? g : batch;
+                    x = (int64_t)atomicAdd(counters + row, (unsigned long long)b);
+                } else {
+                    x = nu;
+                }
             }
             x = __shfl_sync(0xffffffffu, x, 0);
+            b = __shfl_sync(0xffffffffu, b, 0);
             if (x >= nu) break;
-            const int64_t xe = (x + batch < nu) ? x + batch : nu;
+            const int64_t xe = (x + b < nu) ? x + b : nu;
             for (; x < xe; ++x) do_unit(row, x);
         }
         __syncthreads();
