@@ -510,16 +510,28 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
     auto units_in_row = [&](int r) -> int64_t {
         return a.slot_unit_base[(int64_t)(r + 1) * p] - a.slot_unit_base[(int64_t)r * p];
     };
+    // the slot of the previous unit: a grab hands out consecutive units, so the
+    // next one is mostly in the same slot or a few slots on
+    int last_slot = -1;
     auto do_unit = [&](int row, int64_t x) {
         // unit -> (slot, chunk): the slot s of the row with base[s] <= g < base[s+1]
-        const int64_t g = a.slot_unit_base[(int64_t)row * p] + x;
-        int64_t lo = (int64_t)row * p, hi = (int64_t)row * p + p - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (a.slot_unit_base[mid] <= g) lo = mid; else hi = mid - 1;
+        const int r0 = row * p;
+        const int64_t g = a.slot_unit_base[r0] + x;
+        int sl;
+        if (last_slot >= r0 && last_slot < r0 + p && a.slot_unit_base[last_slot] <= g) {
+            sl = last_slot;
+            while (sl + 1 < r0 + p && a.slot_unit_base[sl + 1] <= g) ++sl;
+        } else {
+            int lo = r0, hi = r0 + p - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.slot_unit_base[mid] <= g) lo = mid; else hi = mid - 1;
+            }
+            sl = lo;
         }
-        const int64_t s = lo, k = g - a.slot_unit_base[s];
-        const int64_t j = s % p;
+        last_slot = sl;
+        const int64_t s = sl, k = g - a.slot_unit_base[sl];
+        const int64_t j = sl - r0;
         const int64_t stream = (a.mode == BFS_MODE_COMPRESS_SIEVE) ? s : j;
         const int64_t jb = range_begin(a, j), jl = range_begin(a, j + 1) - jb;
         const int64_t G = jl / GB;
@@ -609,7 +621,8 @@ __global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
     const int64_t per_row = (int64_t)p * a.plain_upb;
     auto units_in_row = [&](int) -> int64_t { return per_row; };
     auto do_unit = [&](int row, int64_t x) {
-        const int64_t j = x / a.plain_upb, c = x % a.plain_upb;
+        const uint32_t xu = (uint32_t)x, upb = (uint32_t)a.plain_upb;   // p * upb units per row fit in 32 bits
+        const int64_t j = xu / upb, c = xu - (uint32_t)j * upb;
         const int64_t b = (int64_t)row * p + j;
         const int64_t jb = range_begin(a, j), jl = range_begin(a, j + 1) - jb;
         const int64_t w = c * 32 + lane_id();
