@@ -468,7 +468,7 @@ __device__ __forceinline__ void row_affine(const LevelArgs& a, unsigned long lon
             if (lane_id() == 0) {
                 const int64_t cur = (int64_t)*reinterpret_cast<volatile unsigned long long*>(counters + row);
                 if (cur < nu) {
-                    const int64_t g = (nu - cur) / (kGuide * (int64_t)gridDim.x * kXW);
+                    const int64_t g = (uint32_t)(nu - cur) / (uint32_t)(kGuide * gridDim.x * kXW);   // units of a row < 2^31
                     b = g > batch ? g : batch;
                     x = (int64_t)atomicAdd(counters + row, (unsigned long long)b);
                 } else {
@@ -534,8 +534,8 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
         const int64_t j = sl - r0;
         const int64_t stream = (a.mode == BFS_MODE_COMPRESS_SIEVE) ? s : j;
         const int64_t jb = range_begin(a, j), jl = range_begin(a, j + 1) - jb;
-        const int64_t G = jl / GB;
-        const int r = (int)(jl % GB);
+        const int64_t G = (uint32_t)jl / (uint32_t)GB;                 // a range is below 2^31 vertices
+        const int r = (int)((uint32_t)jl - (uint32_t)G * (uint32_t)GB);
         const W* in = static_cast<const W*>(a.xbuf) + stream * a.slot_cap;
         const int64_t count = a.xcount[stream];
         const int64_t xw = k * 32 + lane_id();

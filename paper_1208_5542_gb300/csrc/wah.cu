@@ -33,7 +33,7 @@ struct SlotGeom {
 };
 
 __device__ __forceinline__ SlotGeom slot_geom(const EncodeArgs& a, int s) {
-    const int j = a.sieve ? (s % a.p) : s;
+    const int j = a.sieve ? (int)((uint32_t)s % (uint32_t)a.p) : s;
     int64_t b0 = (int64_t)j * a.nb, b1 = b0 + a.nb;
     if (b0 > a.n) b0 = a.n;
     if (b1 > a.n) b1 = a.n;
@@ -375,8 +375,8 @@ __global__ void __launch_bounds__(kEW) enc_chunk_sums(EncodeArgs a, ChunkSum* su
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long ones = 0;
     for (int64_t q = wid; q < n; q += nw) {
-        const int s = (int)(q / cps);
-        const int64_t c = q % cps;
+        const int s = (int)((uint32_t)q / (uint32_t)cps);          // slots x chunks fit in 32 bits
+        const int64_t c = (int64_t)((uint32_t)q - (uint32_t)s * (uint32_t)cps);
         const SlotGeom sg = slot_geom(a, s);
         const int64_t G = sg.nbits / GB;
         const int64_t tb = c * kTile;
@@ -595,8 +595,8 @@ __global__ void __launch_bounds__(kEW) enc_chunk_write(EncodeArgs a, const Chunk
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t q = wid; q < n; q += nw) {
         if (!flags[q]) continue;
-        const int s = (int)(q / cps);
-        const int64_t c = q % cps;
+        const int s = (int)((uint32_t)q / (uint32_t)cps);          // slots x chunks fit in 32 bits
+        const int64_t c = (int64_t)((uint32_t)q - (uint32_t)s * (uint32_t)cps);
         const SlotGeom sg = slot_geom(a, s);
         const int64_t G = sg.nbits / GB;
         const int64_t tb = c * kTile;
@@ -714,8 +714,8 @@ __global__ void __launch_bounds__(kEW) enc_chunk_sums32(EncodeArgs a, ChunkSum* 
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long ones = 0;
     for (int64_t q = wid; q < n; q += nw) {
-        const int s = (int)(q / cps);
-        const int64_t c = q % cps;
+        const int s = (int)((uint32_t)q / (uint32_t)cps);          // slots x chunks fit in 32 bits
+        const int64_t c = (int64_t)((uint32_t)q - (uint32_t)s * (uint32_t)cps);
         const SlotGeom sg = slot_geom(a, s);
         const int64_t G = sg.nbits / 31;
         const int64_t tb = c * kTile;
@@ -808,8 +808,8 @@ __global__ void __launch_bounds__(kEW) enc_chunk_write32(EncodeArgs a, const Chu
     uint32_t* ob = s_f[threadIdx.x >> 5];      // the words, once the frontier words are in registers
     for (int64_t q = wid; q < n; q += nw) {
         if (!flags[q]) continue;
-        const int s = (int)(q / cps);
-        const int64_t c = q % cps;
+        const int s = (int)((uint32_t)q / (uint32_t)cps);          // slots x chunks fit in 32 bits
+        const int64_t c = (int64_t)((uint32_t)q - (uint32_t)s * (uint32_t)cps);
         const SlotGeom sg = slot_geom(a, s);
         const int64_t G = sg.nbits / 31;
         const int64_t tb = c * kTile;
