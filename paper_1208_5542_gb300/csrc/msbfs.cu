@@ -232,7 +232,7 @@ __global__ void ms_expand(MsState* S) {
             u = act[q];
             if ((uint64_t)(uint32_t)u >= (uint64_t)s.n) { ms_fault(S, 1, q, (uint32_t)u); u = 0; }
             else fu = f[u];
-            j = u / s.nb;
+            j = (uint32_t)u / (uint32_t)s.nb;                 // ids and ranges are below 2^31
             ul = u - j * s.nb;
         }
         for (int i = 0; i < s.p; ++i) {
@@ -367,9 +367,10 @@ __global__ void ms_admit_clear(MsState* S, unsigned long long mask, const int32_
     }
     const int64_t total = (int64_t)nlanes * s.n;
     for (int64_t x = tid; x < total; x += stride) {
-        const int r = lanes[x / s.n];
+        const int64_t q = x / s.n;
+        const int r = lanes[q];
         if (r < 0 || r >= 64) { ms_fault(S, 7, (uint64_t)x, (uint64_t)r); continue; }
-        s.levels[(int64_t)r * s.n + x % s.n] = -1;
+        s.levels[(int64_t)r * s.n + (x - q * s.n)] = -1;
     }
     if (tid == 0) s.alive = 0;
 }
