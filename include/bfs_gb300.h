@@ -202,10 +202,13 @@ typedef struct {
  * Outputs, length n: level[v] = hop distance from root (root 0, unreached -1);
  * parent[v] = the smallest neighbour u of v with level[u] = level[v] - 1
  * (root: root; unreached: -1).  parent/level may both be device pointers (the
- * search stays on the device and is ordered on `cuda_stream`; the call returns
- * once the last level is known, so it synchronises the stream once per level)
- * or both host pointers (results are copied back before returning).
- * `stats` may be NULL.
+ * search stays on the device and is ordered on `cuda_stream`) or both host
+ * pointers (results are copied back before returning).  With `stats` NULL the
+ * level loop runs on the device as one CUDA-graph launch (a conditional node
+ * repeats the level while the frontier is not empty; the graph is built on the
+ * first call for the graph's mode and output buffers and reused), and the call
+ * synchronises the stream once at the end; with `stats` the host steps through
+ * the levels and synchronises once per level to read the counters.
  * Errors: BFS_ERR_INVALID_ARG (root out of range, trace too small),
  * BFS_ERR_BUSY (another search on this graph is running), BFS_ERR_CORRUPT
  * (debug checks found a broken invariant), BFS_ERR_CUDA.
