@@ -257,6 +257,30 @@ def test_zero_tiles_skipped_then_set_bit_at_tile_start(gap_tiles):
         _check_trace(_unpack_trace(st, 32), tr)
 
 
+def test_sieved_away_chunk_inside_a_zero_run():
+    """A chunk of 1024 groups that holds frontier vertices (so the encoder reads
+    it) but whose vertices all have empty columns in block (0,0), so the sieve
+    clears it: it opens no word, continues the zero run carried in from the
+    previous chunk, and that run ends at its last group because the next chunk
+    starts with a sieved-in vertex.  The exchanged streams must equal Alg. 3's."""
+    bfs = _lib()
+    tile = 1024 * 31
+    n = 200_000                                   # p = 2: ranges of 100,000 vertices, 4 chunks each
+    root = 150_000
+    mid = np.arange(tile + 100, tile + 200)       # chunk 1 of range 0: edges into range 1 only
+    src = np.concatenate([[root, root, 5], np.full(len(mid), root), mid, [root, 2 * tile]]).astype(np.int32)
+    dst = np.concatenate([[5, 6, 6], mid, np.full(len(mid), root + 1), [2 * tile, 7]]).astype(np.int32)
+    go = oracle.csr(n, src, dst, symmetrize=False)
+    for mode in (1, 2):
+        g = bfs.Graph.from_edges(n, src, dst, symmetrize=False, p=2, mode=mode)
+        lv, pa, tr = oracle.dist_bfs(go, 2, root, mode=ORACLE_MODE[mode], trace=True)
+        parent, level, st = _run(g, root, stats=True, trace_capacity=1 << 18)
+        assert (level == lv).all() and (parent == pa).all()
+        _check_trace(_unpack_trace(st, 32), tr)
+        parent, level, _ = _run(g, root)          # the graph-launched loop
+        assert (level == lv).all() and (parent == pa).all()
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("scale,p", [(14, 4), (16, 8), (13, 7)])
 def test_compressed_row_exchange_never_changes_the_result(mode, scale, p):
