@@ -203,11 +203,11 @@ __global__ void __launch_bounds__(kNT) wah_encode_kernel(EncodeArgs a, unsigned 
 // ------------------------------------------------- parallel slot encoder --
 // The same stream as wah_encode_kernel, built in three data-parallel passes
 // over (slot, chunk of kTile groups):
-//   1. enc_chunk_sums: one warp per chunk tests the frontier summary (a chunk
-//      without frontier bits is flagged all-zero and not read) and, for the
-//      others, takes 32 groups per step: head count (its first group counted
-//      as a head), first and last group type and last head position, from
-//      ballots of the head flags;
+//   1. enc_chunk_sums32 / enc_chunk_sums64: one warp per chunk tests the
+//      frontier summary (a chunk without frontier bits is flagged all-zero and
+//      not read) and, for the others, stages the chunk in shared memory and
+//      takes its head count (its first group counted as a head), first and
+//      last group type and last head position;
 //   2. enc_chunk_scan: per slot, one warp scans the chunk sums (an all-zero
 //      chunk is one zero run): a chunk whose first group continues the previous
 //      chunk's fill run merges with it; this gives every chunk its first word
@@ -215,69 +215,11 @@ __global__ void __launch_bounds__(kNT) wah_encode_kernel(EncodeArgs a, unsigned 
 //      the active word, and writes the fill word of every zero run that ends
 //      in an all-zero chunk.  The last slot to finish (a counter, no waiting)
 //      lays out the decoder's units over all slots;
-//   3. enc_chunk_write: one warp per flagged chunk writes its words, each
-//      lane's word index and run start taken from the ballot of the head flags
-//      and the chunk's carry from pass 2.
+//   3. enc_chunk_write32 / enc_chunk_write64: one warp per flagged chunk
+//      writes its words, each lane's word indices and run starts taken from
+//      the scanned head masks and the chunk's carry from pass 2.
 // With unit_base set, the group at which every 32nd word opens is recorded
 // as the word is written (the decoder's unit bases).
-constexpr int kU = 8;             // 32-group steps whose loads a warp issues together
-
-// Groups gb + 32k + lane (k < kU) of a slot, 0 at and beyond group G.  For
-// 31-bit groups a step of 32 groups is exactly 31 words of the directory and
-// at most 32 words of the frontier: every lane loads one word of each
-// (coalesced), and its group is funnel-shifted from the two words it spans,
-// fetched by shuffles.  The directory is not read when the frontier words of
-// all kU steps are zero.  63-bit groups are read per lane.
-template <typename W>
-__device__ __forceinline__ void warp_groups(const EncodeArgs& a, const SlotGeom& sg, int64_t gb, int64_t G,
-                                            W (&x)[kU]) {
-    const int lane = (int)lane_id();
-    if constexpr (sizeof(W) == 4) {
-        uint32_t fw[kU], dw[kU];
-        const int64_t last = G * 31;                                // bits of the full groups
-        const int64_t fmax = last > 0 ? (sg.src0 + last - 1) >> 5 : -1;
-        const int64_t dmax = last > 0 ? (last - 1) >> 5 : -1;
-        const int64_t p0 = sg.src0 + gb * 31;
-        const uint32_t sh0 = (uint32_t)(p0 & 31);
-        bool any = false;
-#pragma unroll
-        for (int k = 0; k < kU; ++k) {
-            const int64_t w = (p0 >> 5) + 31 * k + lane;
-            fw[k] = (w <= fmax) ? __ldg(a.frontier + w) : 0u;
-            any |= fw[k] != 0u;
-        }
-        const bool sieve = sg.dirb != nullptr;
-        const bool need_dir = sieve && __any_sync(0xffffffffu, any);
-#pragma unroll
-        for (int k = 0; k < kU; ++k) {
-            const int64_t w = ((gb * 31) >> 5) + 31 * k + lane;
-            dw[k] = (need_dir && lane < 31 && w <= dmax) ? __ldg(sg.dirb + w) : 0u;
-        }
-        const uint32_t rel = 31u * (uint32_t)lane + sh0;
-        const int fa = (int)(rel >> 5), fb = fa + 1 < 32 ? fa + 1 : 31;
-        const int da = (31 * lane) >> 5;
-        const uint32_t dsh = (31u * (uint32_t)lane) & 31u;
-#pragma unroll
-        for (int k = 0; k < kU; ++k) {
-            const uint32_t lo = __shfl_sync(0xffffffffu, fw[k], fa);
-            const uint32_t hi = __shfl_sync(0xffffffffu, fw[k], fb);
-            uint32_t v = __funnelshift_r(lo, hi, rel & 31u) & 0x7fffffffu;
-            if (sieve) {
-                const uint32_t dlo = __shfl_sync(0xffffffffu, dw[k], da);
-                const uint32_t dhi = __shfl_sync(0xffffffffu, dw[k], da + 1);
-                v &= __funnelshift_r(dlo, dhi, dsh) & 0x7fffffffu;
-            }
-            x[k] = (gb + 32 * k + lane < G) ? (W)v : W(0);
-        }
-    } else {
-        const SlotGeom g = sg;
-#pragma unroll
-        for (int k = 0; k < kU; ++k) {
-            const int64_t gi = gb + 32 * k + lane;
-            x[k] = (gi < G) ? load_group<W>(a, g, gi) : W(0);
-        }
-    }
-}
 
 // 31-bit groups of a whole chunk, staged in shared memory: the warp copies
 // the chunk's frontier words and directory words with asynchronous 16-byte
@@ -327,29 +269,6 @@ __device__ __forceinline__ Stage32 stage_chunk(const EncodeArgs& a, const SlotGe
     return st;
 }
 
-__device__ __forceinline__ uint32_t staged_group(const Stage32& st, int64_t g) {
-    const uint32_t r = (uint32_t)(g - st.tb) * 31u;
-    const uint32_t fr = st.off + r;
-    uint32_t x = __funnelshift_r(st.f[fr >> 5], st.f[(fr >> 5) + 1], fr & 31u) & 0x7fffffffu;
-    if (st.d) x &= __funnelshift_r(st.d[r >> 5], st.d[(r >> 5) + 1], r & 31u);
-    return x;
-}
-
-// Groups gb + 32k + lane (k < kU) of the chunk, 0 at and beyond tend.
-template <typename W>
-__device__ __forceinline__ void chunk_groups(const EncodeArgs& a, const SlotGeom& sg, const Stage32& st, int64_t gb,
-                                             int64_t tend, W (&x)[kU]) {
-    if constexpr (sizeof(W) == 4) {
-#pragma unroll
-        for (int k = 0; k < kU; ++k) {
-            const int64_t g = gb + 32 * k + lane_id();
-            x[k] = (g < tend) ? (W)staged_group(st, g) : W(0);
-        }
-    } else {
-        warp_groups<W>(a, sg, gb, tend, x);
-    }
-}
-
 struct ChunkSum {
     uint32_t heads;
     uint32_t types;        // first type | last type << 8
@@ -362,83 +281,6 @@ struct ChunkBase {
     int32_t next_type;     // type of the group after the chunk (G_NONE at the slot end)
 };
 
-template <typename W>
-__global__ void __launch_bounds__(kEW) enc_chunk_sums(EncodeArgs a, ChunkSum* sums, uint8_t* flags, int64_t cps,
-                                                      unsigned long long* setbits) {
-    using T = Wah<W>;
-    constexpr int GB = T::GB;
-    __shared__ __align__(16) uint32_t s_f[kEW / 32][sizeof(W) == 4 ? kStageWords : 4];
-    __shared__ __align__(16) uint32_t s_d[kEW / 32][sizeof(W) == 4 ? kStageWords : 4];
-    const int64_t n = (int64_t)a.nslots * cps;
-    const int lane = (int)lane_id();
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long ones = 0;
-    for (int64_t q = wid; q < n; q += nw) {
-        const int s = (int)((uint32_t)q / (uint32_t)cps);          // slots x chunks fit in 32 bits
-        const int64_t c = (int64_t)((uint32_t)q - (uint32_t)s * (uint32_t)cps);
-        const SlotGeom sg = slot_geom(a, s);
-        const int64_t G = sg.nbits / GB;
-        const int64_t tb = c * kTile;
-        bool live = false;
-        int64_t tend = tb;
-        if (tb < G) {      // the chunk's summary bytes, one 32-bit word per lane
-            tend = (tb + kTile < G) ? tb + kTile : G;
-            bool nz = true;
-            if (a.fsum) {
-                const int64_t q0 = (sg.src0 + tb * GB) >> 10, q1 = (sg.src0 + tend * GB - 1) >> 10;
-                const int64_t w = (q0 >> 2) + lane;
-                uint32_t x = 0;
-                if (w <= (q1 >> 2)) {
-                    x = __ldcg(reinterpret_cast<const uint32_t*>(a.fsum) + w);
-                    if (w == (q0 >> 2)) x &= 0xffffffffu << (8 * (q0 & 3));
-                    if (w == (q1 >> 2)) x &= 0xffffffffu >> (8 * (3 - (q1 & 3)));
-                }
-                nz = x != 0u;
-            }
-            live = __any_sync(0xffffffffu, nz);
-        }
-        if (lane == 0) flags[q] = live ? 1 : 0;
-        if (!live) continue;
-        int prev = -1, first = G_NONE;
-        uint32_t heads = 0;
-        int64_t last_head = -1;
-        Stage32 stg{};
-        if constexpr (sizeof(W) == 4) stg = stage_chunk(a, sg, tb, tend, s_f[threadIdx.x >> 5], s_d[threadIdx.x >> 5]);
-        for (int64_t gb = tb; gb < tend; gb += 32 * kU) {
-            W x[kU];
-            chunk_groups<W>(a, sg, stg, gb, tend, x);
-#pragma unroll
-            for (int k = 0; k < kU; ++k) {
-                const int64_t g0 = gb + 32 * k;
-                if (g0 >= tend) break;
-                const bool valid = g0 + lane < tend;
-                const int ty = valid ? group_type<W>(x[k]) : G_NONE;
-                ones += (unsigned long long)T::popc(x[k]);
-                int pt = __shfl_up_sync(0xffffffffu, ty, 1);
-                if (lane == 0) pt = prev;
-                const uint32_t b = __ballot_sync(0xffffffffu, valid && (ty == G_LIT || ty != pt));
-                heads += __popc(b);
-                if (b) last_head = g0 + 31 - __clz(b);
-                if (g0 == tb) first = __shfl_sync(0xffffffffu, ty, 0);
-                const int lv = (tend - g0 < 32) ? (int)(tend - g0 - 1) : 31;
-                prev = __shfl_sync(0xffffffffu, ty, lv);
-            }
-        }
-        if (lane == 0) {
-            ChunkSum cs;
-            cs.heads = heads;
-            cs.types = (uint32_t)first | ((uint32_t)prev << 8);
-            cs.last_head = last_head;
-            sums[q] = cs;
-        }
-        __syncwarp();           // the staging buffers are reused by the next chunk
-    }
-    if (setbits) {
-        ones = warp_sum(ones);
-        if (lane == 0 && ones) atomicAdd(setbits, ones);
-    }
-}
 
 // One warp per slot (blockDim.x = 32).
 template <typename W>
@@ -581,84 +423,13 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
     }
 }
 
-template <typename W>
-__global__ void __launch_bounds__(kEW) enc_chunk_write(EncodeArgs a, const ChunkBase* bases, const uint8_t* flags,
-                                                       int64_t cps) {
-    using T = Wah<W>;
-    constexpr int GB = T::GB;
-    __shared__ __align__(16) uint32_t s_f[kEW / 32][sizeof(W) == 4 ? kStageWords : 4];
-    __shared__ __align__(16) uint32_t s_d[kEW / 32][sizeof(W) == 4 ? kStageWords : 4];
-    const int64_t n = (int64_t)a.nslots * cps;
-    const int lane = (int)lane_id();
-    const uint32_t le_mask = 0xffffffffu >> (31 - lane);        // lanes 0..lane
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t q = wid; q < n; q += nw) {
-        if (!flags[q]) continue;
-        const int s = (int)((uint32_t)q / (uint32_t)cps);          // slots x chunks fit in 32 bits
-        const int64_t c = (int64_t)((uint32_t)q - (uint32_t)s * (uint32_t)cps);
-        const SlotGeom sg = slot_geom(a, s);
-        const int64_t G = sg.nbits / GB;
-        const int64_t tb = c * kTile;
-        const int64_t tend = (tb + kTile < G) ? tb + kTile : G;
-        const ChunkBase cb = bases[q];
-        W* out = static_cast<W*>(a.out) + (int64_t)s * a.slot_cap;
-        int64_t* ub = a.unit_base ? a.unit_base + (int64_t)s * a.unit_stride : nullptr;
-        int64_t base = cb.words;          // next word to open
-        int64_t run_start = cb.run_start;
-        int prev = cb.prev_type;
-        Stage32 stg{};
-        if constexpr (sizeof(W) == 4) stg = stage_chunk(a, sg, tb, tend, s_f[threadIdx.x >> 5], s_d[threadIdx.x >> 5]);
-        for (int64_t gb = tb; gb < tend; gb += 32 * kU) {
-            W x[kU];
-            int tys[kU];
-            chunk_groups<W>(a, sg, stg, gb, tend, x);
-#pragma unroll
-            for (int k = 0; k < kU; ++k) tys[k] = (gb + 32 * k + lane < tend) ? group_type<W>(x[k]) : G_NONE;
-#pragma unroll
-            for (int k = 0; k < kU; ++k) {
-                const int64_t g0 = gb + 32 * k;
-                if (g0 >= tend) break;
-                const int64_t g = g0 + lane;
-                const bool valid = g < tend;
-                const int ty = tys[k];
-                int pt = __shfl_up_sync(0xffffffffu, ty, 1);
-                if (lane == 0) pt = prev;
-                const bool h = valid && (ty == G_LIT || ty != pt);
-                const uint32_t b = __ballot_sync(0xffffffffu, h);
-                int nt = __shfl_down_sync(0xffffffffu, ty, 1);
-                const int nt31 = (k + 1 < kU) ? __shfl_sync(0xffffffffu, tys[k + 1 < kU ? k + 1 : k], 0) : G_NONE;
-                if (valid) {
-                    const uint32_t bl = b & le_mask;
-                    const int64_t widx = base + __popc(bl) - 1;
-                    const int64_t start = bl ? g0 + 31 - __clz(bl) : run_start;
-                    if (g + 1 == tend) nt = cb.next_type;
-                    else if (lane == 31) {
-                        if (k + 1 < kU) nt = nt31;
-                        else if constexpr (sizeof(W) == 4) nt = group_type<W>((W)staged_group(stg, g + 1));
-                        else nt = group_type<W>(load_group<W>(a, sg, g + 1));
-                    }
-                    if (ty == G_LIT) out[widx] = T::to_payload(x[k]);
-                    else if (nt != ty) out[widx] = fill_word<W>(ty, (uint64_t)(g - start + 1));
-                    if (h && ub && (widx & 31) == 0) ub[widx >> 5] = g;
-                }
-                base += __popc(b);
-                if (b) run_start = g0 + 31 - __clz(b);
-                const int lv = (tend - g0 < 32) ? (int)(tend - g0 - 1) : 31;
-                prev = __shfl_sync(0xffffffffu, ty, lv);
-            }
-        }
-        __syncwarp();           // the staging buffers are reused by the next chunk
-    }
-}
 
 // 31-bit groups, lane-sequential: the chunk is staged in shared memory; lane
 // l takes groups 32l .. 32l+31, combining their words into c = f & V (in
 // registers, aligned to its first group), a group being two words of c
 // funnel-shifted; its groups are classified into zero / one masks, from which
 // head, run-end and word-index masks follow by bit operations, and the lanes'
-// partial results are combined by warp scans.  Same sums and the same words
-// as the batched kernels.
+// partial results are combined by warp scans.
 // The lane's 32 combined words c[k] = bits 32k.. of the sieved groups
 // 32*lane .. 32*lane+31 of the chunk (c = f & V aligned to the chunk's first
 // group; c[31] is past the lane's 992 bits).  Lanes read 31 words apart: no
@@ -891,6 +662,244 @@ __global__ void __launch_bounds__(kEW) enc_chunk_write32(EncodeArgs a, const Chu
     }
 }
 
+// 63-bit groups (64-bit words), lane-sequential like the 31-bit passes: a
+// chunk of 1024 groups is 64,512 bits, lane l owns groups 32l .. 32l+31, which
+// start at word 63l of the chunk (a stride of 63 words: no bank conflicts), and
+// takes them in two halves of 16 groups (1,008 bits; the second half starts
+// 16 bits into word 31), each from 33 combined words c = f & V in registers;
+// a group spans at most three of them.
+constexpr int kEW64 = 64;                 // threads per CTA (2 warps: shared memory per warp is ~17 KB)
+constexpr int kStage64 = 2176;            // words: a chunk (2,016) + alignment and funnel slack, and the
+                                          // padded 64-bit output words (2 x 1,059) of the write pass
+
+__device__ __forceinline__ Stage32 stage_chunk63(const EncodeArgs& a, const SlotGeom& sg, int64_t tb, int64_t tend,
+                                                 uint32_t* fbuf, uint32_t* dbuf) {
+    const int lane = (int)lane_id();
+    const int64_t fbit0 = sg.src0 + 63 * tb;
+    const int64_t fw0 = (fbit0 >> 5) & ~(int64_t)3;
+    const int64_t flast = ((sg.src0 + 63 * tend - 1) >> 5) + 1;
+    int64_t fend = (flast + 1 + 3) & ~(int64_t)3;
+    if (fend > a.frontier_words) fend = a.frontier_words;
+    for (int64_t i = lane; 4 * i < fend - fw0; i += 32) cp_async16(fbuf + 4 * i, a.frontier + fw0 + 4 * i);
+    Stage32 st;
+    st.f = fbuf;
+    st.off = (uint32_t)(fbit0 - 32 * fw0);
+    st.tb = tb;
+    st.d = nullptr;
+    if (sg.dirb) {
+        const int64_t dw0 = (63 * tb) >> 5;                          // 2,016 words per chunk: 16-byte aligned
+        const int64_t dlast = ((63 * tend - 1) >> 5) + 1;
+        int64_t dend = (dlast + 1 + 3) & ~(int64_t)3;
+        if (dend > a.dir_stride) dend = a.dir_stride;
+        for (int64_t i = lane; 4 * i < dend - dw0; i += 32) cp_async16(dbuf + 4 * i, sg.dirb + dw0 + 4 * i);
+        st.d = dbuf;
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+    return st;
+}
+
+// The 33 combined words of half h of the lane's groups.
+__device__ __forceinline__ void half_cwords63(const Stage32& st, int h, uint32_t (&c)[33]) {
+    const int lane = (int)lane_id();
+    const uint32_t sh = st.off & 31u;
+    const int w0 = 63 * lane + 31 * h;
+    const uint32_t* f = st.f + w0 + (st.off >> 5);
+    if (st.d) {
+        const uint32_t* d = st.d + w0;
+#pragma unroll
+        for (int k = 0; k < 33; ++k) c[k] = __funnelshift_r(f[k], f[k + 1], sh) & d[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 33; ++k) c[k] = __funnelshift_r(f[k], f[k + 1], sh);
+    }
+}
+
+// Group i (0..15) of half h from its combined words.
+__device__ __forceinline__ unsigned long long half_group63(const uint32_t (&c)[33], int h, int i) {
+    const int b = 16 * h + 63 * i;
+    const int k = b >> 5;
+    const uint32_t s = (uint32_t)(b & 31);
+    const uint32_t lo = __funnelshift_r(c[k], c[k + 1], s), hi = __funnelshift_r(c[k + 1], c[k + 2], s);
+    return (((unsigned long long)hi << 32) | lo) & 0x7fffffffffffffffull;
+}
+
+// Zero / one / valid masks of the lane's groups (bit i = group 32*lane + i) from
+// the combined words of its two halves and, when asked for, their set bits.
+__device__ __forceinline__ void lane_masks63(const uint32_t (&c0)[33], const uint32_t (&c1)[33], int ng, uint32_t& zm,
+                                             uint32_t& om, uint32_t& vm, unsigned long long* ones) {
+    const int nv = ng - 32 * (int)lane_id();
+    vm = nv >= 32 ? 0xffffffffu : (nv > 0 ? (1u << nv) - 1u : 0u);
+    zm = 0u;
+    om = 0u;
+#pragma unroll
+    for (int bi = 0; bi < 32; ++bi) {
+        const unsigned long long x = bi < 16 ? half_group63(c0, 0, bi) : half_group63(c1, 1, bi - 16);
+        zm |= (x == 0ull ? 1u : 0u) << bi;
+        om |= (x == 0x7fffffffffffffffull ? 1u : 0u) << bi;
+        if (ones && bi < nv) *ones += (unsigned long long)__popcll(x);
+    }
+    zm &= vm;
+    om &= vm;
+}
+
+__global__ void __launch_bounds__(kEW64) enc_chunk_sums64(EncodeArgs a, ChunkSum* sums, uint8_t* flags, int64_t cps,
+                                                          unsigned long long* setbits) {
+    __shared__ __align__(16) uint32_t s_f[kEW64 / 32][kStage64];
+    __shared__ __align__(16) uint32_t s_d[kEW64 / 32][kStage64];
+    const int64_t n = (int64_t)a.nslots * cps;
+    const int lane = (int)lane_id();
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long ones = 0;
+    for (int64_t q = wid; q < n; q += nw) {
+        const int s = (int)((uint32_t)q / (uint32_t)cps);
+        const int64_t c = (int64_t)((uint32_t)q - (uint32_t)s * (uint32_t)cps);
+        const SlotGeom sg = slot_geom(a, s);
+        const int64_t G = sg.nbits / 63;
+        const int64_t tb = c * kTile;
+        bool live = false;
+        int64_t tend = tb;
+        if (tb < G) {
+            tend = (tb + kTile < G) ? tb + kTile : G;
+            bool nz = true;
+            if (a.fsum) {
+                const int64_t q0 = (sg.src0 + tb * 63) >> 10, q1 = (sg.src0 + tend * 63 - 1) >> 10;
+                const int64_t w = (q0 >> 2) + lane;
+                uint32_t x = 0;
+                if (w <= (q1 >> 2)) {
+                    x = __ldcg(reinterpret_cast<const uint32_t*>(a.fsum) + w);
+                    if (w == (q0 >> 2)) x &= 0xffffffffu << (8 * (q0 & 3));
+                    if (w == (q1 >> 2)) x &= 0xffffffffu >> (8 * (3 - (q1 & 3)));
+                }
+                nz = x != 0u;
+            }
+            live = __any_sync(0xffffffffu, nz);
+        }
+        if (lane == 0) flags[q] = live ? 1 : 0;
+        if (!live) continue;
+        const Stage32 st = stage_chunk63(a, sg, tb, tend, s_f[threadIdx.x >> 5], s_d[threadIdx.x >> 5]);
+        const int ng = (int)(tend - tb);
+        uint32_t c0[33], c1[33];
+        half_cwords63(st, 0, c0);
+        half_cwords63(st, 1, c1);
+        uint32_t zm, om, vm;
+        lane_masks63(c0, c1, ng, zm, om, vm, setbits ? &ones : nullptr);
+        uint32_t pz = __shfl_up_sync(0xffffffffu, zm, 1) >> 31, po = __shfl_up_sync(0xffffffffu, om, 1) >> 31;
+        if (lane == 0) { pz = 0u; po = 0u; }              // the chunk's first group counts as a head
+        const uint32_t hm = (vm & ~(zm | om)) | (zm & ~((zm << 1) | pz)) | (om & ~((om << 1) | po));
+        const int heads = warp_sum(__popc(hm));
+        int lh = hm ? 32 * lane + 31 - __clz(hm) : -1;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) { const int y = __shfl_xor_sync(0xffffffffu, lh, d); lh = y > lh ? y : lh; }
+        const int lastl = (ng - 1) >> 5;
+        const int lastty = mask_type(__shfl_sync(0xffffffffu, zm, lastl), __shfl_sync(0xffffffffu, om, lastl),
+                                     (ng - 1) & 31);
+        if (lane == 0) {
+            ChunkSum cs;
+            cs.heads = (uint32_t)heads;
+            cs.types = (uint32_t)mask_type(zm, om, 0) | ((uint32_t)lastty << 8);
+            cs.last_head = lh >= 0 ? tb + lh : -1;
+            sums[q] = cs;
+        }
+        __syncwarp();
+    }
+    if (setbits) {
+        ones = warp_sum(ones);
+        if (lane == 0 && ones) atomicAdd(setbits, ones);
+    }
+}
+
+__global__ void __launch_bounds__(kEW64) enc_chunk_write64(EncodeArgs a, const ChunkBase* bases, const uint8_t* flags,
+                                                           int64_t cps) {
+    using T = Wah<unsigned long long>;
+    __shared__ __align__(16) uint32_t s_f[kEW64 / 32][kStage64];
+    __shared__ __align__(16) uint32_t s_d[kEW64 / 32][kStage64];
+    static_assert(2 * (kOutWords + kOutWords / 32 + 1) <= kStage64, "output words overflow the frontier buffer");
+    const int64_t n = (int64_t)a.nslots * cps;
+    const int lane = (int)lane_id();
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long* ob = reinterpret_cast<unsigned long long*>(s_f[threadIdx.x >> 5]);
+    for (int64_t q = wid; q < n; q += nw) {
+        if (!flags[q]) continue;
+        const int s = (int)((uint32_t)q / (uint32_t)cps);
+        const int64_t c = (int64_t)((uint32_t)q - (uint32_t)s * (uint32_t)cps);
+        const SlotGeom sg = slot_geom(a, s);
+        const int64_t G = sg.nbits / 63;
+        const int64_t tb = c * kTile;
+        const int64_t tend = (tb + kTile < G) ? tb + kTile : G;
+        const ChunkBase cb = bases[q];
+        unsigned long long* out = static_cast<unsigned long long*>(a.out) + (int64_t)s * a.slot_cap;
+        int64_t* ub = a.unit_base ? a.unit_base + (int64_t)s * a.unit_stride : nullptr;
+        const Stage32 st = stage_chunk63(a, sg, tb, tend, s_f[threadIdx.x >> 5], s_d[threadIdx.x >> 5]);
+        const int ng = (int)(tend - tb);
+        uint32_t c0[33], c1[33];
+        half_cwords63(st, 0, c0);
+        half_cwords63(st, 1, c1);
+        uint32_t zm, om, vm;
+        lane_masks63(c0, c1, ng, zm, om, vm, nullptr);
+        const int r0 = 32 * lane;
+        const int nv = ng - r0;
+        uint32_t pz = __shfl_up_sync(0xffffffffu, zm, 1) >> 31, po = __shfl_up_sync(0xffffffffu, om, 1) >> 31;
+        if (lane == 0) { pz = cb.prev_type == G_ZERO; po = cb.prev_type == G_ONE; }
+        uint32_t nz = __shfl_down_sync(0xffffffffu, zm, 1) & 1u, no = __shfl_down_sync(0xffffffffu, om, 1) & 1u;
+        if (nv <= 32) { nz = cb.next_type == G_ZERO; no = cb.next_type == G_ONE; }
+        const uint32_t lit = vm & ~(zm | om);
+        const uint32_t hm = lit | (zm & ~((zm << 1) | pz)) | (om & ~((om << 1) | po));
+        const int last = nv >= 32 ? 31 : nv - 1;
+        const uint32_t zend = nv > 0 ? zm & ~((zm >> 1) | (nz << last)) : 0u;
+        const uint32_t oend = nv > 0 ? om & ~((om >> 1) | (no << last)) : 0u;
+        const int hc = __popc(hm);
+        int incl = hc, hmax = hm ? r0 + 31 - __clz(hm) : -1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            const int z = __shfl_up_sync(0xffffffffu, hmax, d);
+            if (lane >= d) { incl += y; hmax = z > hmax ? z : hmax; }
+        }
+        const int H = __shfl_sync(0xffffffffu, incl, 31);
+        int hprev = __shfl_up_sync(0xffffffffu, hmax, 1);
+        if (lane == 0) hprev = -1;
+        const int li0 = incl - hc;
+        const int64_t st0 = hprev >= 0 ? tb + hprev : cb.run_start;
+        // every lane has read its frontier words: the buffer now takes the output words
+        __syncwarp();
+        if (nv > 0) {
+#pragma unroll
+            for (int bi = 0; bi < 32; ++bi) {
+                const uint32_t bit = 1u << bi;
+                const uint32_t hb = hm & (bi == 31 ? 0xffffffffu : (bit << 1) - 1u);
+                const int li = li0 + __popc(hb);
+                if (lit & bit) {
+                    ob[opad(li)] = T::to_payload(bi < 16 ? half_group63(c0, 0, bi) : half_group63(c1, 1, bi - 16));
+                } else if ((zend | oend) & bit) {
+                    const int64_t start = hb ? tb + r0 + 31 - __clz(hb) : st0;
+                    ob[opad(li)] = fill_word<unsigned long long>((oend & bit) ? G_ONE : G_ZERO,
+                                                                 (uint64_t)(tb + r0 + bi - start + 1));
+                }
+            }
+            if (ub && hc > 0) {
+                int j = (int)((1 - cb.words - li0) & 31);
+                if (j == 0) j = 32;
+                if (j <= hc) ub[(cb.words - 1 + li0 + j) >> 5] = tb + r0 + select32(hm, j - 1);
+            }
+        }
+        const uint32_t hm0 = __shfl_sync(0xffffffffu, hm, 0);
+        const int lastl = (ng - 1) >> 5, lastb = (ng - 1) & 31;
+        const uint32_t lit_l = __shfl_sync(0xffffffffu, lit, lastl);
+        const uint32_t end_l = __shfl_sync(0xffffffffu, zend | oend, lastl);
+        const bool last_lit = (lit_l >> lastb) & 1u, last_end = (end_l >> lastb) & 1u;
+        const bool w0 = !(hm0 & 1u) && (H > 0 || last_end);
+        const bool wH = H > 0 ? (last_lit || last_end) : w0;
+        __syncwarp();
+        const int lo = w0 ? 0 : 1, hi = wH ? H : H - 1;
+        for (int k = lo + lane; k <= hi; k += 32) out[cb.words - 1 + k] = ob[opad(k)];
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------- standalone decode --
 // One CTA decodes the stream into the zeroed output (cta_wah_decode_or);
 // malformed streams set *err.
@@ -928,9 +937,9 @@ bfs_status launch_wah_encode_parallel(const EncodeArgs& a, int wah_bits, void* s
         enc_chunk_scan<uint32_t><<<a.nslots, 32, 0, st>>>(a, cs, fl, cb, cps, setbits);
         enc_chunk_write32<<<grid, kEW, 0, st>>>(a, cb, fl, cps);
     } else {
-        enc_chunk_sums<unsigned long long><<<grid, kEW, 0, st>>>(a, cs, fl, cps, setbits);
+        enc_chunk_sums64<<<grid * 2, kEW64, 0, st>>>(a, cs, fl, cps, setbits);
         enc_chunk_scan<unsigned long long><<<a.nslots, 32, 0, st>>>(a, cs, fl, cb, cps, setbits);
-        enc_chunk_write<unsigned long long><<<grid, kEW, 0, st>>>(a, cb, fl, cps);
+        enc_chunk_write64<<<grid * 2, kEW64, 0, st>>>(a, cb, fl, cps);
     }
     BFS_CUDA_TRY(cudaGetLastError());
     return BFS_OK;
