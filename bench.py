@@ -42,6 +42,7 @@ WORKLOADS = {
 }
 METRIC = "harmonic-mean GTEPS on 1 GB300 (compressed+sieved vs plain GPU BFS) at bit-exact levels"
 MODE_NAMES = {0: "plain", 1: "compress", 2: "compress_sieve"}
+DIRECTIONS = {"top_down": 0, "hybrid": 1, "bottom_up": 2}
 KERNEL_SOURCES = ["paper_1208_5542_gb300/csrc/bfs_level.cu", "paper_1208_5542_gb300/csrc/wah.cuh",
                   "paper_1208_5542_gb300/csrc/common.cuh"]
 
@@ -59,6 +60,10 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrivals per second of the serving stream")
     ap.add_argument("--mode", type=int, default=2, help="0 plain, 1 compress, 2 compress+sieve")
     ap.add_argument("--wah-bits", type=int, default=32)
+    ap.add_argument("--direction", default="top_down", choices=sorted(DIRECTIONS),
+                    help="top_down: the paper's algorithms; hybrid: top-down / bottom-up levels chosen per level")
+    ap.add_argument("--alpha", type=int, default=4, help="hybrid: bottom-up once m_f > m_u / alpha")
+    ap.add_argument("--beta", type=int, default=24, help="hybrid: top-down again once the frontier < n / beta")
     ap.add_argument("--roots", type=int, default=0, help="override the number of roots")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -391,6 +396,8 @@ def main():
     n, src, dst = graphgen.edges(scale, ef, kind=kind)
     roots = graphgen.pick_roots(n, src, dst, nroots, seed=7 + 1000 * rank)
     g = bfs.Graph.from_edges(n, src, dst, p=p, mode=args.mode, wah_bits=args.wah_bits)
+    if args.direction != "top_down":
+        g.set_direction(DIRECTIONS[args.direction], args.alpha, args.beta)
     src_d = torch.from_numpy(src).to(dev)
     dst_d = torch.from_numpy(dst).to(dev)
     deg = (torch.bincount(src_d.long(), minlength=n) + torch.bincount(dst_d.long(), minlength=n))
@@ -496,6 +503,8 @@ def main():
     # hub pieces, reduction, level step); per search the init, root and first-level
     # kernels.  The levels of every root are those of the recording pass.
     launches_per_level = {0: 4, 1: 7, 2: 7}[args.mode]
+    if args.direction != "top_down":     # bottom-up expansion (+ clear and decode of the streams)
+        launches_per_level += 1 if args.mode == 0 else 3
     gpu_launches = args.steps * sum(3 + launches_per_level * st.n_levels for st in stats_cs[0])
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -508,7 +517,9 @@ def main():
     scatter_achieved = ex_entries / (ex_ms / 1e3) / 1e9 if ex_ms > 0 else 0.0
     nb_range = -(-n // p)
     window = 8 * -(-nb_range // 32) + 4096 <= 227 * 1024      # the library's row-window rule
-    traffic = ncu_traffic(args.workload, MODE_NAMES[args.mode], ex_bytes / launches if launches else 0)
+    traffic = None
+    if args.direction == "top_down":     # the counters were taken on top-down levels
+        traffic = ncu_traffic(args.workload, MODE_NAMES[args.mode], ex_bytes / launches if launches else 0)
     exch = []
     for k in sorted(per_level):
         a = per_level[k]
@@ -606,13 +617,17 @@ def main():
         "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": desc + f"-{MODE_NAMES[args.mode]}-{len(roots)}roots", "scale": scale,
+        "config": {"workload": desc + f"-{MODE_NAMES[args.mode]}-{len(roots)}roots" +
+                   ("" if args.direction == "top_down" else f"-{args.direction}"), "scale": scale,
                    "edgefactor": ef, "vertices": n, "tuples": int(len(src)), "grid": f"{p}x{p}",
                    "mode": MODE_NAMES[args.mode], "wah_word_bits": args.wah_bits, "roots": len(roots),
+                   "direction": args.direction if args.direction != "hybrid"
+                   else f"hybrid (alpha {args.alpha}, beta {args.beta})",
                    "step": "one search per root", "l2": "flushed (256 MiB write) before every search",
                    "parallelism": f"replicas x{world}"},
         "plain_gpu": plain,
-        "roofline": {"kernel": ("expand_wah" if args.mode else "expand_plain") + " + expand_pieces", "bound": "hbm",
+        "roofline": {"kernel": ("expand_wah" if args.mode else "expand_plain") + " + expand_pieces" +
+                     ("" if args.direction == "top_down" else " + expand_bottom_up"), "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4) if peak else None,
                      "peak_source": peak_src, "traffic": traffic,

@@ -154,6 +154,45 @@ BFS_API bfs_status bfs_graph_set_mode(bfs_graph_t g, int32_t mode, int32_t wah_w
  */
 BFS_API bfs_status bfs_graph_set_row_exchange(bfs_graph_t g, int32_t enabled);
 
+/* Direction of each level (bfs_graph_set_direction). */
+enum {
+    BFS_DIRECTION_TOP_DOWN = 0,   /* every level top-down: Alg. 1-3 as printed */
+    BFS_DIRECTION_HYBRID = 1,     /* top-down or bottom-up, chosen per level */
+    BFS_DIRECTION_BOTTOM_UP = 2   /* every level bottom-up (a test setting) */
+};
+
+/*
+ * The hybrid top-down / bottom-up traversal of Beamer et al., which the paper
+ * names in Sec. VIII and IX as the next method to combine with compression and
+ * sieve.  The algorithms of Table 5 expand top-down: every frontier vertex u
+ * scans its columns.  A bottom-up level instead lets every unvisited vertex v
+ * of block-row i scan its own neighbours range by range (j = 0, 1, ..., p-1:
+ * the column of v in block (j, i)), testing each neighbour u against the
+ * frontier that the exchange delivered for block (i, j): the stream of slot
+ * (i, j) (f_j sieved by V_{i,j} in COMPRESS_SIEVE mode, f_j in COMPRESS mode)
+ * decoded, or the raw slice f_j in PLAIN mode.  All streams of a level are
+ * decoded into one n-bit bitmap, ORed over the block-rows; it holds at u the
+ * bit of slot (i, j) itself, since u has a neighbour in range i
+ * (V_{i,j}(u) = 1).  The first range
+ * holding a frontier neighbour gives v its parent, the smallest such
+ * neighbour, which is the smallest neighbour on the previous level: levels and
+ * parents are identical to the top-down search, and so is every exchanged
+ * stream (the exchange of a level does not depend on its direction).
+ *   policy: BFS_DIRECTION_*.  HYBRID switches top-down -> bottom-up when the
+ *     frontier grew and its degree sum m_f exceeds m_u / alpha (m_u: degree
+ *     sum of the unvisited vertices), and bottom-up -> top-down when the
+ *     frontier shrank below n / beta vertices (Beamer et al.'s rule; they
+ *     use alpha = 14, beta = 24).
+ *   alpha, beta: 1 .. 1,000,000; used by HYBRID only.
+ * Bottom-up needs the in-neighbours of v, which are its out-neighbours only
+ * when the graph is undirected: a graph created with symmetrize = 0 (every
+ * CSR graph included) returns BFS_ERR_INVALID_ARG for any policy other than
+ * TOP_DOWN.  The first such call computes every vertex's degree (4 bytes per
+ * vertex, kept with the graph; ordered on the legacy default stream and
+ * synchronised).  Not safe while a search on `g` is running.
+ */
+BFS_API bfs_status bfs_graph_set_direction(bfs_graph_t g, int32_t policy, int32_t alpha, int32_t beta);
+
 /*
  * Copy the directory vector V_{i,j} (Eq. 4: bit k set iff source column
  * begin(j)+k of block A_{i,j} has an entry) into `out_words` (device,
@@ -169,7 +208,8 @@ typedef struct {
     int64_t exchanged_vertices;  /* set bits carried by the exchange (after the sieve);
                                     PLAIN/COMPRESS: p * |f_k| */
     int64_t column_hits;         /* (vertex, block) pairs with a nonempty column, the
-                                    work items of the expansion */
+                                    work items of the expansion (bottom-up: the columns
+                                    of unvisited vertices read) */
     int64_t raw_bytes;           /* bytes of the raw bitmap exchange: p slices of each range */
     int64_t wah_bytes;           /* bytes of the compressed streams (0 in PLAIN mode) */
     int64_t edges_scanned;       /* adjacency entries read by the expansion */
@@ -178,6 +218,8 @@ typedef struct {
     float ms_communication;      /* exchange: size scan (and packing when traced) */
     float ms_traversing;         /* expansion (the local SpMV) */
     float ms_reducing;           /* mask, visited update, level writeback, frontier count */
+    int32_t bottom_up;           /* 1: the level ran bottom-up (bfs_graph_set_direction) */
+    int32_t reserved;
 } bfs_level_stats;
 
 typedef struct {

@@ -12,7 +12,8 @@ import numpy as np
 import torch
 
 from . import native
-from .native import MODE_COMPRESS, MODE_COMPRESS_SIEVE, MODE_PLAIN, check  # noqa: F401
+from .native import (DIRECTION_BOTTOM_UP, DIRECTION_HYBRID, DIRECTION_TOP_DOWN,  # noqa: F401
+                     MODE_COMPRESS, MODE_COMPRESS_SIEVE, MODE_PLAIN, check)
 
 
 def _stream_ptr(stream) -> int:
@@ -121,6 +122,10 @@ class Graph:
 
     def set_row_exchange(self, enabled: bool):
         check(native.lib().bfs_graph_set_row_exchange(self._h, int(bool(enabled))))
+
+    def set_direction(self, policy: int, alpha: int = 14, beta: int = 24):
+        """Top-down (the default), hybrid top-down / bottom-up, or bottom-up levels."""
+        check(native.lib().bfs_graph_set_direction(self._h, int(policy), int(alpha), int(beta)))
 
     def mode(self):
         info = native.GraphInfo()

@@ -27,6 +27,14 @@
 // Visited tests and next-bit updates are then on-chip; the partial t_i of
 // every CTA is OR-folded into t when the CTA leaves the row (the fold of the
 // 2D partition, done through L2).
+//
+// Bottom-up levels (the hybrid traversal the paper names in Sec. VIII and IX,
+// when enabled): the exchange is the same, its streams are decoded into a
+// bitmap, and every unvisited vertex v of range i scans its columns in blocks
+// (j, i), j = 0 .. p-1, for a neighbour in the frontier delivered to block
+// (i, j); the first range with one gives v the smallest of them as its
+// parent.  The device picks each level's direction (level_next), and the
+// kernels of the other direction return at once.
 #include <algorithm>
 #include <cstring>
 
@@ -65,6 +73,11 @@ struct LevelCtl {
     int32_t plain_batch;   // PLAIN units per hand-out
     int32_t dedup;         // read the parent before updating it
     int32_t go;            // 1 while another level follows
+    int64_t m_f;           // degree sum of the frontier
+    int64_t m_u;           // degree sum of the unvisited vertices
+    int32_t bu;            // 1: this level runs bottom-up
+    int32_t policy;        // BFS_DIRECTION_*
+    int32_t alpha, beta;   // thresholds of the hybrid
 };
 
 struct LevelArgs {
@@ -111,6 +124,11 @@ struct LevelArgs {
     unsigned long long* rowbuf_count;   // slots used in this level
     int32_t* rowbuf_row;                // block-row of each slot
     int64_t* rowbuf_words;              // words in each slot
+    // bottom-up levels
+    uint32_t* gbits;                    // decoded streams (n bits, OR over the block-rows)
+    int64_t g_words;                    // its uint32 words (a multiple of 4)
+    const int64_t* bu_ptr;              // bottom-up rows: offsets (n + 1)
+    const int32_t* bu_adj;              // bottom-up rows: neighbour ids
 };
 
 __device__ __forceinline__ int64_t range_begin(const LevelArgs& a, int64_t b) {
@@ -498,7 +516,7 @@ __device__ __forceinline__ void row_affine(const LevelArgs& a, unsigned long lon
 // decoded vertices, and the warp expands them 32 at a time.
 template <typename W, bool WIN, bool DEDUP>
 __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
-    if (a.ctl->dedup != (DEDUP ? 1 : 0)) return;   // the other variant expands this level
+    if (a.ctl->dedup != (DEDUP ? 1 : 0) || a.ctl->bu) return;   // another variant expands this level
     using T = Wah<W>;
     constexpr int GB = T::GB;
     extern __shared__ uint32_t s_win[];                   // s_pi | s_t (WIN only)
@@ -611,7 +629,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
 // them 32 at a time.
 template <bool WIN, bool DEDUP>
 __global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
-    if (a.ctl->dedup != (DEDUP ? 1 : 0)) return;   // the other variant expands this level
+    if (a.ctl->dedup != (DEDUP ? 1 : 0) || a.ctl->bu) return;   // another variant expands this level
     extern __shared__ uint32_t s_win[];
     __shared__ int s_row[2];
     uint32_t* s_pi = s_win;
@@ -678,7 +696,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
 // Pieces of long columns, row by row: one warp per piece.
 template <bool WIN, bool DEDUP>
 __global__ void __launch_bounds__(kXT, 1) expand_pieces(LevelArgs a) {
-    if (a.ctl->dedup != (DEDUP ? 1 : 0)) return;   // the other variant expands this level
+    if (a.ctl->dedup != (DEDUP ? 1 : 0) || a.ctl->bu) return;   // another variant expands this level
     extern __shared__ uint32_t s_win[];
     __shared__ int s_row[2];
     uint32_t* s_pi = s_win;
@@ -716,13 +734,257 @@ __global__ void __launch_bounds__(kXT) fold_rows(LevelArgs a) {
     if (threadIdx.x == 0 && s_err) atomicOr(a.ctr + C_ERROR, 16ull);
 }
 
+// ------------------------------------------------------------- bottom-up --
+// OR the group bits `bits` (bit q = bitmap bit bit0 + q) into a bitmap.
+template <typename W>
+__device__ __forceinline__ void or_bits(uint32_t* dst, int64_t bit0, W bits) {
+    if (!bits) return;
+    const int64_t w = bit0 >> 5;
+    const uint32_t sh = (uint32_t)(bit0 & 31);
+    if constexpr (sizeof(W) == 4) {
+        atomicOr(dst + w, bits << sh);
+        if (sh) {
+            const uint32_t hi = bits >> (32 - sh);
+            if (hi) atomicOr(dst + w + 1, hi);
+        }
+    } else {
+        const unsigned long long x = bits;
+        const uint32_t w0 = (uint32_t)(x << sh);
+        const uint32_t w1 = sh ? (uint32_t)(x >> (32 - sh)) : (uint32_t)(x >> 32);
+        const uint32_t w2 = sh ? (uint32_t)(x >> (64 - sh)) : 0u;
+        if (w0) atomicOr(dst + w, w0);
+        if (w1) atomicOr(dst + w + 1, w1);
+        if (w2) atomicOr(dst + w + 2, w2);
+    }
+}
+
+// Zero the decoded bitmap (bottom-up levels only).
+__global__ void __launch_bounds__(kNT) clear_gbits(LevelArgs a) {
+    if (!a.ctl->bu) return;
+    const int64_t quads = a.g_words / 4;
+    uint4* q = reinterpret_cast<uint4*>(a.gbits);
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < quads; x += (int64_t)gridDim.x * blockDim.x)
+        q[x] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// The exchanged streams decoded into one n-bit bitmap (bottom-up levels only):
+// bit q of the stream of slot (i, j) lands on vertex begin(j) + q, ORed over
+// the block-rows i.  A block (i, j) only ever tests vertices u of range j with
+// a neighbour in range i, whose bit its own stream carries (V_{i,j}(u) = 1):
+// the OR holds exactly that bit, and one bitmap serves every block-row.  One
+// warp per 32-word unit of the decoder's plan (COMPRESS: the plan of row 0,
+// whose blocks hold the p streams once), each word placed by a scan of run
+// lengths from its chunk's group base; literal groups and the active word are
+// ORed in, 1-fill runs set by the whole warp, 0-fills left as cleared.
+template <typename W>
+__global__ void __launch_bounds__(kNT) decode_streams(LevelArgs a) {
+    if (!a.ctl->bu) return;
+    using T = Wah<W>;
+    constexpr int GB = T::GB;
+    const int p = a.p;
+    const bool sieve = a.mode == BFS_MODE_COMPRESS_SIEVE;
+    const int nblk = sieve ? p * p : p;
+    const int64_t total = a.slot_unit_base[nblk];
+    // every warp takes a contiguous share of the units: the slot of the next
+    // unit is the current one or a few on (one search per warp)
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t u0 = total * gw / nw, u1 = total * (gw + 1) / nw;
+    int sl = -1;
+    for (int64_t g = u0; g < u1; ++g) {
+        if (sl < 0) {
+            int lo = 0, hi = nblk - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.slot_unit_base[mid] <= g) lo = mid; else hi = mid - 1;
+            }
+            sl = lo;
+        } else {
+            while (sl + 1 < nblk && a.slot_unit_base[sl + 1] <= g) ++sl;
+        }
+        const int64_t s = sl, k = g - a.slot_unit_base[sl];
+        const int64_t j = sieve ? s % p : s;
+        const int64_t jb = range_begin(a, j), jl = range_begin(a, j + 1) - jb;
+        const int64_t G = (uint32_t)jl / (uint32_t)GB;
+        const int r = (int)((uint32_t)jl - (uint32_t)G * (uint32_t)GB);
+        const W* in = static_cast<const W*>(a.xbuf) + s * a.slot_cap;
+        const int64_t count = a.xcount[s];
+        const int64_t xw = k * 32 + lane_id();
+        const W y = (xw < count) ? in[xw] : W(0);
+        const uint32_t glen = (xw < count) ? (uint32_t)word_groups<W>(y) : 0u;
+        const uint32_t gincl = warp_incl_sum(glen);
+        const int64_t gs = a.chunk_base[s * a.chunks_per_slot + k] + (int64_t)(gincl - glen);
+        uint32_t* dst = a.gbits;
+        bool one = false;
+        if (xw < count) {
+            if (gs < G) {
+                if (!is_fill<W>(y)) or_bits<W>(dst, jb + gs * GB, T::from_payload(y));
+                else one = (y & T::VAL) != W(0);
+            } else if (r > 0) {
+                or_bits<W>(dst, jb + G * GB, T::from_active(y, r));
+            }
+        }
+        uint32_t m = __ballot_sync(0xffffffffu, one);
+        while (m) {
+            const int o = __ffs(m) - 1;
+            m &= m - 1;
+            const int64_t g0 = __shfl_sync(0xffffffffu, gs, o);
+            int64_t g1 = g0 + __shfl_sync(0xffffffffu, (int64_t)glen, o);
+            if (g1 > G) g1 = G;
+            const int64_t b0 = jb + g0 * GB, b1 = jb + g1 * GB;   // bits [b0, b1)
+            if (b1 <= b0) continue;
+            const int64_t w0 = b0 >> 5, w1 = (b1 - 1) >> 5;
+            for (int64_t w = w0 + lane_id(); w <= w1; w += 32) {
+                uint32_t mask = 0xffffffffu;
+                if (w == w0) mask &= 0xffffffffu << (b0 & 31);
+                if (w == w1) mask &= 0xffffffffu >> (31 - ((b1 - 1) & 31));
+                atomicOr(dst + w, mask);
+            }
+        }
+    }
+}
+
+// One bottom-up level: every unvisited vertex v of range i scans its columns
+// in blocks (j, i) -- its neighbours in range j, the graph being undirected --
+// for j = 0, 1, ..., testing each neighbour u against the frontier delivered
+// to block (i, j) (the decoded slot, or the raw slice f_j in PLAIN mode).  The
+// smallest frontier neighbour of the first range that has one is v's parent:
+// the ranges are ordered intervals of ids, so it is the smallest neighbour of
+// v on the previous level, and it is the smallest frontier neighbour seen
+// once the scan has passed the end of its range.  v's columns are read from
+// the bottom-up rows (stored back to back, range by range).  One warp per
+// visited word (32 vertices): a row of at most kBuLane entries is scanned by
+// its own lane (kIlp entries and their frontier words in flight), a longer
+// one by the whole warp (kIlp x 32 entries per step); the warp's next bits
+// are one store (t is clear and no other kernel writes it this level).
+constexpr int64_t kBuLane = 32;
+
+__device__ __forceinline__ uint32_t warp_min(uint32_t x) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, d);
+        x = y < x ? y : x;
+    }
+    return x;
+}
+
+struct BuFrontier {
+    const uint32_t* g;        // the decoded streams, or the raw frontier (PLAIN)
+    uint32_t nb;
+    // the range of u and whether the frontier delivered to block (i, range) holds u
+    __device__ __forceinline__ uint32_t test(uint32_t u, uint32_t& j) const {
+        j = u / nb;
+        return (__ldg(g + (u >> 5)) >> (u & 31u)) & 1u;
+    }
+};
+
+__global__ void __launch_bounds__(kNT) expand_bottom_up(LevelArgs a) {
+    if (!a.ctl->bu) return;
+    const int64_t words = (a.n + 31) >> 5;
+    const int64_t gw0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t gstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t nb = (uint32_t)a.nb;                                // n < 2^31
+    const uint32_t NONE = 0xffffffffu;
+    unsigned long long edges = 0, cols = 0;
+    for (int64_t w = gw0; w < words; w += gstride) {
+        const uint32_t piw = __ldg(a.pi + w);
+        if (piw == 0xffffffffu) continue;
+        const int64_t v = w * 32 + lane_id();
+        const bool mine = v < a.n && !((piw >> lane_id()) & 1u);
+        int64_t e0 = 0, e1 = 0;
+        if (mine) {
+            e0 = __ldg(a.bu_ptr + v);
+            e1 = __ldg(a.bu_ptr + v + 1);
+        }
+        const BuFrontier fr{a.mode != BFS_MODE_PLAIN ? a.gbits : a.f, nb};
+        uint32_t best = NONE;
+        if (mine && e1 - e0 <= kBuLane) {
+            uint32_t cur = NONE;                                        // range of the entries so far
+            for (int64_t e = e0; e < e1; e += kIlp) {
+                const int cnt = (e1 - e < kIlp) ? (int)(e1 - e) : kIlp;
+                uint32_t u[kIlp], j[kIlp], hit[kIlp];
+#pragma unroll
+                for (int k = 0; k < kIlp; ++k) u[k] = (k < cnt) ? (uint32_t)__ldg(a.bu_adj + e + k) : 0u;
+#pragma unroll
+                for (int k = 0; k < kIlp; ++k) hit[k] = (k < cnt) ? fr.test(u[k], j[k]) : 0u;
+                bool stop = false;
+#pragma unroll
+                for (int k = 0; k < kIlp; ++k) {
+                    if (k >= cnt || stop) continue;
+                    if (j[k] != cur) {                                  // a new range
+                        if (best != NONE) { stop = true; continue; }
+                        cur = j[k];
+                        ++cols;
+                    }
+                    ++edges;
+                    if (hit[k] && u[k] < best) best = u[k];
+                }
+                if (stop) break;
+            }
+        }
+        // long rows, one after the other, by the whole warp
+        uint32_t lm = __ballot_sync(0xffffffffu, mine && e1 - e0 > kBuLane);
+        while (lm) {
+            const int o = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const int64_t b0 = __shfl_sync(0xffffffffu, e0, o), b1 = __shfl_sync(0xffffffffu, e1, o);
+            uint32_t wb = NONE, wend = NONE;                            // best so far and the end of its range
+            uint32_t jlast = NONE;                                      // range of the last entry scanned
+            for (int64_t e = b0; e < b1; e += kIlp * 32) {
+                uint32_t u[kIlp], j[kIlp], hit[kIlp];
+#pragma unroll
+                for (int k = 0; k < kIlp; ++k) {
+                    const int64_t x = e + k * 32 + lane_id();
+                    u[k] = (x < b1) ? (uint32_t)__ldg(a.bu_adj + x) : NONE;
+                }
+#pragma unroll
+                for (int k = 0; k < kIlp; ++k) {
+                    hit[k] = 0u;
+                    j[k] = NONE;
+                    if (u[k] != NONE) hit[k] = fr.test(u[k], j[k]);
+                }
+                uint32_t cand = NONE;
+                bool past = false;
+#pragma unroll
+                for (int k = 0; k < kIlp; ++k) {
+                    if (hit[k] && u[k] < cand) cand = u[k];
+                    // entries (in row order) that open a range
+                    uint32_t jp = __shfl_up_sync(0xffffffffu, j[k], 1);
+                    if (lane_id() == 0) jp = jlast;
+                    const uint32_t opens = __ballot_sync(0xffffffffu, u[k] != NONE && j[k] != jp);
+                    const uint32_t valid = __ballot_sync(0xffffffffu, u[k] != NONE);
+                    if (lane_id() == (uint32_t)o) { cols += __popc(opens); edges += __popc(valid); }
+                    const uint32_t jl = __shfl_sync(0xffffffffu, j[k], 31);
+                    if (jl != NONE) jlast = jl;
+                }
+                cand = warp_min(cand);
+                if (cand < wb) {
+                    wb = cand;
+                    wend = (uint32_t)range_begin(a, cand / nb + 1);
+                }
+#pragma unroll
+                for (int k = 0; k < kIlp; ++k) past |= u[k] != NONE && u[k] >= wend;
+                if (wb != NONE && __any_sync(0xffffffffu, past)) break;   // the best's range is complete
+            }
+            if (lane_id() == (uint32_t)o) best = wb;
+        }
+        const bool found = best != NONE;
+        if (found) a.parent[v] = (int32_t)best;
+        const uint32_t m = __ballot_sync(0xffffffffu, found);
+        if (lane_id() == 0 && m) a.t[w] = m;
+    }
+    flush_counts(a, edges, cols, 0ull);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctr[C_BOTTOM_UP] = 1ull;
+}
+
 // ---------------------------------------------------------------- reduce --
 // x = t & ~pi; pi |= x; level of the new vertices; |x|; the next frontier f = x
 // and t cleared for the next level; frontier summary of x.
 __global__ void __launch_bounds__(kNT) reduce_level(uint32_t* __restrict__ t, uint32_t* __restrict__ pi,
                                                     uint32_t* __restrict__ f, uint8_t* __restrict__ fsum,
                                                     int64_t words, int64_t n, int32_t* __restrict__ level,
-                                                    const LevelCtl* __restrict__ ctl, unsigned long long* ctr) {
+                                                    const LevelCtl* __restrict__ ctl, unsigned long long* ctr,
+                                                    const uint32_t* __restrict__ deg) {
     const int32_t next_level = ctl->level + 1;
     const int64_t nwarps = (words + 31) / 32;
     const int64_t gw0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -730,6 +992,7 @@ __global__ void __launch_bounds__(kNT) reduce_level(uint32_t* __restrict__ t, ui
     for (int64_t gw = gw0; gw < nwarps; gw += gstride) {
         const int64_t w = gw * 32 + lane_id();
         uint32_t x = 0;
+        unsigned long long dsum = 0;
         if (w < words) {
             x = t[w] & ~pi[w];
             if (x) {
@@ -739,7 +1002,10 @@ __global__ void __launch_bounds__(kNT) reduce_level(uint32_t* __restrict__ t, ui
                     const int bpos = __ffs(y) - 1;
                     y &= y - 1;
                     const int64_t v = w * 32 + bpos;
-                    if (v < n) level[v] = next_level;
+                    if (v < n) {
+                        level[v] = next_level;
+                        if (deg) dsum += __ldg(deg + v);
+                    }
                 }
             }
             f[w] = x;
@@ -747,9 +1013,11 @@ __global__ void __launch_bounds__(kNT) reduce_level(uint32_t* __restrict__ t, ui
         }
         const uint32_t any = __ballot_sync(0xffffffffu, x != 0u);
         const int cnt = warp_sum(__popc(x));
+        if (deg) dsum = warp_sum(dsum);
         if (lane_id() == 0) {
             fsum[gw] = any ? 1 : 0;
             if (cnt) atomicAdd(ctr + C_NEXT_COUNT, (unsigned long long)cnt);
+            if (dsum) atomicAdd(ctr + C_NEXT_DEGREE, dsum);
         }
     }
 }
@@ -760,6 +1028,21 @@ __global__ void __launch_bounds__(kNT) reduce_level(uint32_t* __restrict__ t, ui
 __global__ void level_next(LevelCtl* c, const unsigned long long* ctr, int64_t n, int win, int32_t max_levels,
                            cudaGraphConditionalHandle handle, int use_handle) {
     const int64_t f = (int64_t)ctr[C_NEXT_COUNT];
+    const int64_t prev = c->frontier;
+    const int64_t mf = (int64_t)ctr[C_NEXT_DEGREE];
+    c->m_u -= mf;
+    c->m_f = mf;
+    // direction of the next level (Beamer et al.): bottom-up once the growing
+    // frontier's edges outweigh 1/alpha of the unvisited vertices' edges; back
+    // to top-down once the shrinking frontier is below n / beta vertices
+    if (c->policy == BFS_DIRECTION_BOTTOM_UP) {
+        c->bu = 1;
+    } else if (c->policy == BFS_DIRECTION_HYBRID) {
+        if (!c->bu) c->bu = (f > prev && mf * (int64_t)c->alpha > c->m_u) ? 1 : 0;
+        else c->bu = (f < prev && f * (int64_t)c->beta < n) ? 0 : 1;
+    } else {
+        c->bu = 0;
+    }
     c->frontier = f;
     c->visited += f;
     c->level += 1;
@@ -776,13 +1059,20 @@ __global__ void level_next(LevelCtl* c, const unsigned long long* ctr, int64_t n
     if (use_handle) cudaGraphSetConditional(handle, go ? 1u : 0u);
 }
 
-__global__ void level_first(LevelCtl* c, int64_t n, int win) {
+__global__ void level_first(LevelCtl* c, int64_t n, int win, int policy, int alpha, int beta,
+                            const uint32_t* deg, int32_t root, int64_t entries) {
     c->frontier = 1;
     c->visited = 1;
     c->level = 0;
     c->plain_batch = (64 < n) ? 32 : 2;
     c->dedup = (!win && 16 < n) ? 1 : 0;
     c->go = 1;
+    c->policy = policy;
+    c->alpha = alpha;
+    c->beta = beta;
+    c->bu = (policy == BFS_DIRECTION_BOTTOM_UP) ? 1 : 0;
+    c->m_f = deg ? (int64_t)deg[root] : 0;
+    c->m_u = entries - c->m_f;
 }
 
 __global__ void init_search(int32_t* __restrict__ level, int32_t* __restrict__ parent, int64_t n,
@@ -960,6 +1250,7 @@ void free_workspace(bfs_graph* g) {
     W.level_scratch.release(); W.row_meta.release();
     W.rowbuf.release(); W.rowbuf_row.release(); W.rowbuf_words.release();
     W.enc_sums.release(); W.enc_bases.release(); W.enc_flags.release(); W.enc_done.release(); W.ctl.release();
+    W.gbits.release();
     for (auto& c : W.sgraph) {
         if (c.exec) cudaGraphExecDestroy(c.exec);
         if (c.graph) cudaGraphDestroy(c.graph);
@@ -1018,6 +1309,14 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         BFS_TRY(W.rowbuf_words.alloc(sizeof(int64_t) * W.rowbuf_slots));
     }
     const size_t dyn = win ? window_bytes(W.win_words) : 0;
+    // bottom-up levels: degrees (direction choice) and the decoded streams
+    const bool bu_kernels = g->direction != BFS_DIRECTION_TOP_DOWN;
+    if (bu_kernels) BFS_TRY(ensure_degrees(g, st));
+    const int64_t g_words = (W.bm_words + 3) / 4 * 4;
+    if (bu_kernels && !W.gbits.ptr) {
+        // allocated once: captured level loops keep its address
+        BFS_TRY(W.gbits.alloc(sizeof(uint32_t) * (size_t)g_words));
+    }
     DevBuf slot_off;
     if (tracing) BFS_TRY(slot_off.alloc(sizeof(int64_t) * nslots));
     if (stats) { stats->n_levels = 0; stats->trace_used = 0; }
@@ -1072,6 +1371,10 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     a.rowbuf_count = lvl + 3 * p;
     a.rowbuf_row = W.rowbuf_row.as<int32_t>();
     a.rowbuf_words = W.rowbuf_words.as<int64_t>();
+    a.gbits = W.gbits.as<uint32_t>();
+    a.g_words = g_words;
+    a.bu_ptr = L.bu_ptr.as<int64_t>();
+    a.bu_adj = L.bu_adj.as<int32_t>();
 
     EncodeArgs ea;
     memset(&ea, 0, sizeof(ea));
@@ -1102,7 +1405,8 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     a.ctl = ctl;
     ea.frontier = f;
     const int32_t max_levels = (int32_t)std::min<int64_t>(L.n + 1, INT32_MAX);
-    level_first<<<1, 1, 0, st>>>(ctl, L.n, win ? 1 : 0);
+    const uint32_t* deg = bu_kernels ? L.deg.as<uint32_t>() : nullptr;
+    level_first<<<1, 1, 0, st>>>(ctl, L.n, win ? 1 : 0, g->direction, g->alpha, g->beta, deg, root, L.nnz);
     BFS_CUDA_TRY(cudaGetLastError());
 
     // One level: the same launch sequence every time.  `host` adds the
@@ -1126,6 +1430,12 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             // the exchanged-vertex count is a statistic: only the stepwise loop asks for it
             BFS_TRY(launch_wah_encode_parallel(ea, wbits, W.enc_sums.ptr, W.enc_bases.ptr, W.enc_cps,
                                                W.enc_flags.ptr, host ? ctr + C_EXCHANGED : nullptr, sm_count() * 6, s));
+            if (bu_kernels) {           // a bottom-up level reads the streams as bitmaps
+                clear_gbits<<<sm_count() * 4, kNT, 0, s>>>(a);
+                if (wbits == 32) decode_streams<uint32_t><<<sm_count() * 8, kNT, 0, s>>>(a);
+                else decode_streams<unsigned long long><<<sm_count() * 8, kNT, 0, s>>>(a);
+                BFS_CUDA_TRY(cudaGetLastError());
+            }
             if (host && timing) cudaEventRecord(W.ev[1], s);
             if (host && tracing && k < stats->capacity_levels) {
                 const int u32pw = wbits / 32;
@@ -1162,13 +1472,17 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             expand_pieces<false, false><<<xgrid, kXT, 0, s>>>(a);
         }
         BFS_CUDA_TRY(cudaGetLastError());
+        if (bu_kernels) {
+            expand_bottom_up<<<sm_count() * 8, kNT, 0, s>>>(a);
+            BFS_CUDA_TRY(cudaGetLastError());
+        }
         if (rowx) {
             fold_rows<<<xgrid, kXT, 0, s>>>(a);
             BFS_CUDA_TRY(cudaGetLastError());
         }
         if (host && timing) cudaEventRecord(W.ev[3], s);
         reduce_level<<<std::min<int64_t>((W.bm_words + 255) / 256 + 1, sm_count() * 16), kNT, 0, s>>>(
-            t, W.pi.as<uint32_t>(), f, W.fsum.as<uint8_t>(), W.bm_words, L.n, level, ctl, ctr);
+            t, W.pi.as<uint32_t>(), f, W.fsum.as<uint8_t>(), W.bm_words, L.n, level, ctl, ctr, deg);
         BFS_CUDA_TRY(cudaGetLastError());
         if (host && timing) cudaEventRecord(W.ev[4], s);
         level_next<<<1, 1, 0, s>>>(ctl, ctr, L.n, win ? 1 : 0, max_levels, handle, host ? 0 : 1);
@@ -1183,8 +1497,8 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         // buffers and reused.
         SearchGraph* sg = nullptr;
         for (auto& c : W.sgraph)
-            if (c.exec && c.mode == mode && c.wbits == wbits && c.rowx == (int)rowx && c.parent == parent &&
-                c.level == level)
+            if (c.exec && c.mode == mode && c.wbits == wbits && c.rowx == (int)rowx &&
+                c.bottom_up == (int)bu_kernels && c.parent == parent && c.level == level)
                 sg = &c;
         if (!sg) {
             SearchGraph& c = W.sgraph[W.sgraph_next];
@@ -1224,6 +1538,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             c.mode = mode;
             c.wbits = wbits;
             c.rowx = rowx ? 1 : 0;
+            c.bottom_up = bu_kernels ? 1 : 0;
             c.parent = parent;
             c.level = level;
             sg = &c;
@@ -1262,6 +1577,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             ls.wah_bytes = (mode == BFS_MODE_PLAIN) ? 0 : (int64_t)h[C_WAH_WORDS] * (wbits / 8);
             ls.edges_scanned = (int64_t)h[C_EDGES];
             ls.row_wah_bytes = (int64_t)h[C_ROW_WORDS] * 4;
+            ls.bottom_up = h[C_BOTTOM_UP] ? 1 : 0;
             if (timing) {
                 ls.ms_compress_sieve = elapsed(W.ev[0], W.ev[1]);
                 ls.ms_communication = elapsed(W.ev[1], W.ev[2]);

@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <new>
+#include <utility>
 
 #include "common.cuh"
 #include "internal.h"
@@ -219,6 +220,86 @@ __global__ void scatter_entries(const int32_t* __restrict__ src, const int32_t* 
     }
 }
 
+// Degree of every vertex u (range j): the lengths of its columns in blocks
+// (i, j), i = 0 .. p-1, saturated at 2^32 - 1.
+__global__ void vertex_degrees(const uint32_t* __restrict__ dir, const uint32_t* __restrict__ rank,
+                               int64_t dir_stride, const uint32_t* __restrict__ cp,
+                               const int64_t* __restrict__ cp_base, int p, int64_t nb, int64_t n,
+                               uint32_t* __restrict__ deg) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = u / nb, ul = u - j * nb;
+        const uint32_t bit = 1u << (ul & 31);
+        uint64_t d = 0;
+        for (int i = 0; i < p; ++i) {
+            const int64_t b = (int64_t)i * p + j;
+            const uint32_t dw = dir[b * dir_stride + (ul >> 5)];
+            if (!(dw & bit)) continue;
+            const int64_t c = cp_base[b] + rank[b * dir_stride + (ul >> 5)] + __popc(dw & (bit - 1u));
+            d += cp[c + 1] - cp[c];
+        }
+        deg[u] = d > 0xffffffffull ? 0xffffffffu : (uint32_t)d;
+    }
+}
+
+// Bottom-up layout, step 1: exclusive scan of the degrees in tiles of 1024,
+// in 64 bits, with every tile's total.
+__global__ void __launch_bounds__(1024) degree_tile_scan(const uint32_t* __restrict__ deg, int64_t n,
+                                                         int64_t* __restrict__ ptr, int64_t* __restrict__ tile_sum) {
+    __shared__ int64_t warp_tot[32];
+    const int64_t x = blockIdx.x * 1024LL + threadIdx.x;
+    const int64_t d = x < n ? (int64_t)deg[x] : 0;
+    int64_t incl = d;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane_id() >= o) incl += y;
+    }
+    if (lane_id() == 31) warp_tot[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int64_t t = warp_tot[threadIdx.x], ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, ti, o);
+            if ((int)threadIdx.x >= o) ti += y;
+        }
+        warp_tot[threadIdx.x] = ti - t;
+        if (threadIdx.x == 31) tile_sum[blockIdx.x] = ti;
+    }
+    __syncthreads();
+    if (x <= n) ptr[x] = incl - d + warp_tot[threadIdx.x >> 5];      // ptr[n]: the entries before n in its tile
+}
+
+// Step 2: add the tiles' scanned totals; ptr[n] = the total.
+__global__ void degree_tile_add(int64_t* __restrict__ ptr, int64_t n, const int64_t* __restrict__ tile_base) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x <= n; x += (int64_t)gridDim.x * blockDim.x)
+        ptr[x] += tile_base[x >> 10];
+}
+
+// Step 3: the columns of every vertex v (range i) in blocks (0,i), (1,i), ...
+// copied back to back from bu_ptr[v]: its neighbours grouped by range j in
+// ascending order (in any order inside a range).
+__global__ void bottom_up_rows(const uint32_t* __restrict__ dir, const uint32_t* __restrict__ rank,
+                               int64_t dir_stride, const uint32_t* __restrict__ cp,
+                               const int64_t* __restrict__ cp_base, const int64_t* __restrict__ ir_base,
+                               const int32_t* __restrict__ ir, int p, int64_t nb, int64_t n,
+                               const int64_t* __restrict__ ptr, int32_t* __restrict__ adj) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = v / nb, vl = v - i * nb;
+        const uint32_t bit = 1u << (vl & 31);
+        int64_t pos = ptr[v];
+        for (int j = 0; j < p; ++j) {
+            const int64_t b = (int64_t)j * p + i;
+            const uint32_t dw = dir[b * dir_stride + (vl >> 5)];
+            if (!(dw & bit)) continue;
+            const int64_t c = cp_base[b] + rank[b * dir_stride + (vl >> 5)] + __popc(dw & (bit - 1u));
+            const int32_t* col = ir + ir_base[b];
+            const uint32_t c0 = cp[c], c1 = cp[c + 1];
+            for (uint32_t e = c0; e < c1; ++e) adj[pos++] = col[e];
+        }
+    }
+}
+
 // CSR -> per-entry source ids.
 __global__ void expand_rows(const int64_t* __restrict__ row_ptr, int64_t n, int32_t* __restrict__ src) {
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
@@ -356,6 +437,53 @@ bfs_status build_layout(bfs_graph* g, int64_t n, int64_t m, const int32_t* d_src
     return BFS_OK;
 }
 
+bfs_status ensure_degrees(bfs_graph* g, cudaStream_t st) {
+    Layout& L = g->L;
+    if (L.deg.ptr) return BFS_OK;
+    DevBuf deg;
+    BFS_TRY(deg.alloc(sizeof(uint32_t) * L.n));
+    vertex_degrees<<<grid_for(L.n, 256), 256, 0, st>>>(L.dir.as<uint32_t>(), L.rank.as<uint32_t>(), L.dir_stride,
+                                                       L.cp.as<uint32_t>(), L.cp_base_d.as<int64_t>(), L.p, L.nb,
+                                                       L.n, deg.as<uint32_t>());
+    BFS_CUDA_TRY(cudaGetLastError());
+    // the bottom-up rows: offsets = scan of the degrees, then the columns
+    const int64_t tiles = (L.n + 1 + 1023) / 1024;
+    DevBuf ptr, adj, tsum;
+    BFS_TRY(ptr.alloc(sizeof(int64_t) * (L.n + 1)));
+    BFS_TRY(adj.alloc(sizeof(int32_t) * (L.nnz > 0 ? L.nnz : 1)));
+    BFS_TRY(tsum.alloc(sizeof(int64_t) * tiles));
+    degree_tile_scan<<<tiles, 1024, 0, st>>>(deg.as<uint32_t>(), L.n, ptr.as<int64_t>(), tsum.as<int64_t>());
+    BFS_CUDA_TRY(cudaGetLastError());
+    std::vector<int64_t> h(tiles);
+    BFS_CUDA_TRY(cudaMemcpyAsync(h.data(), tsum.ptr, sizeof(int64_t) * tiles, cudaMemcpyDeviceToHost, st));
+    BFS_CUDA_TRY(cudaStreamSynchronize(st));
+    int64_t run = 0;
+    for (int64_t t = 0; t < tiles; ++t) {
+        const int64_t x = h[t];
+        h[t] = run;
+        run += x;
+    }
+    if (run != L.nnz)
+        return set_error(BFS_ERR_CUDA, "bottom-up rows: degrees sum to %lld, not %lld entries", (long long)run,
+                         (long long)L.nnz);
+    BFS_CUDA_TRY(cudaMemcpyAsync(tsum.ptr, h.data(), sizeof(int64_t) * tiles, cudaMemcpyHostToDevice, st));
+    degree_tile_add<<<grid_for(L.n + 1, 256), 256, 0, st>>>(ptr.as<int64_t>(), L.n, tsum.as<int64_t>());
+    BFS_CUDA_TRY(cudaGetLastError());
+    bottom_up_rows<<<grid_for(L.n, 256), 256, 0, st>>>(L.dir.as<uint32_t>(), L.rank.as<uint32_t>(), L.dir_stride,
+                                                       L.cp.as<uint32_t>(), L.cp_base_d.as<int64_t>(),
+                                                       L.ir_base_d.as<int64_t>(), L.ir.as<int32_t>(), L.p, L.nb,
+                                                       L.n, ptr.as<int64_t>(), adj.as<int32_t>());
+    BFS_CUDA_TRY(cudaGetLastError());
+    BFS_CUDA_TRY(cudaStreamSynchronize(st));
+    std::swap(L.deg.ptr, deg.ptr);
+    std::swap(L.deg.bytes, deg.bytes);
+    std::swap(L.bu_ptr.ptr, ptr.ptr);
+    std::swap(L.bu_ptr.bytes, ptr.bytes);
+    std::swap(L.bu_adj.ptr, adj.ptr);
+    std::swap(L.bu_adj.bytes, adj.bytes);
+    return BFS_OK;
+}
+
 // --------------------------------------------------------- entry helpers --
 namespace {
 
@@ -386,6 +514,7 @@ bfs_status create_common(int64_t n, int64_t m, const int32_t* src, const int32_t
     g->wah_bits = o.wah_word_bits;
     g->debug_checks = o.debug_checks;
     g->row_exchange = o.row_exchange ? 1 : 0;
+    g->symmetric = symmetrize ? 1 : 0;
     cudaGetDevice(&g->device);
 
     DevBuf dsrc, ddst;
@@ -528,12 +657,13 @@ bfs_status bfs_graph_footprint(bfs_graph_t g, int64_t* bytes) {
     if (!g || !bytes) return set_error(BFS_ERR_INVALID_ARG, "NULL argument");
     const Layout& L = g->L;
     const Workspace& W = g->W;
-    int64_t b = (int64_t)(L.dir.bytes + L.rank.bytes + L.cp.bytes + L.ir.bytes + L.cp_base_d.bytes + L.ir_base_d.bytes);
+    int64_t b = (int64_t)(L.dir.bytes + L.rank.bytes + L.cp.bytes + L.ir.bytes + L.cp_base_d.bytes + L.ir_base_d.bytes +
+                          L.deg.bytes + L.bu_ptr.bytes + L.bu_adj.bytes);
     b += (int64_t)(W.pi.bytes + W.fa.bytes + W.fb.bytes + W.fsum.bytes + W.xbuf.bytes + W.xcount.bytes +
                    W.chunk_base.bytes + W.units.bytes + W.counters.bytes + W.tmp_parent.bytes + W.tmp_level.bytes +
                    W.pieces.bytes + W.level_scratch.bytes + W.row_meta.bytes + W.rowbuf.bytes + W.rowbuf_row.bytes +
                    W.rowbuf_words.bytes + W.enc_sums.bytes + W.enc_bases.bytes + W.enc_flags.bytes +
-                   W.enc_done.bytes);
+                   W.enc_done.bytes + W.gbits.bytes);
     *bytes = b;
     return BFS_OK;
 }
@@ -568,6 +698,30 @@ bfs_status bfs_graph_set_row_exchange(bfs_graph_t g, int32_t enabled) {
     if (g->busy.load()) return set_error(BFS_ERR_BUSY, "graph is in use");
     std::lock_guard<std::mutex> lk(g->mu);
     g->row_exchange = enabled ? 1 : 0;
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_set_direction(bfs_graph_t g, int32_t policy, int32_t alpha, int32_t beta) {
+    if (!g) return set_error(BFS_ERR_INVALID_ARG, "graph is NULL");
+    if (policy < BFS_DIRECTION_TOP_DOWN || policy > BFS_DIRECTION_BOTTOM_UP)
+        return set_error(BFS_ERR_INVALID_ARG, "unknown direction policy %d", policy);
+    if (alpha < 1 || alpha > 1000000 || beta < 1 || beta > 1000000)
+        return set_error(BFS_ERR_INVALID_ARG, "alpha and beta must lie in [1, 1000000]");
+    if (policy != BFS_DIRECTION_TOP_DOWN && !g->symmetric)
+        return set_error(BFS_ERR_INVALID_ARG, "bottom-up levels need an undirected graph (created with symmetrize = 1)");
+    if (g->busy.load()) return set_error(BFS_ERR_BUSY, "graph is in use");
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (policy != BFS_DIRECTION_TOP_DOWN) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(g->device);
+        const bfs_status rc = ensure_degrees(g, nullptr);
+        cudaSetDevice(cur);
+        BFS_TRY(rc);
+    }
+    g->direction = policy;
+    g->alpha = alpha;
+    g->beta = beta;
     return BFS_OK;
 }
 

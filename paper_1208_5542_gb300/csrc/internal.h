@@ -64,6 +64,9 @@ struct Layout {
     int64_t dir_stride = 0; // uint32 words per block directory (padded)
     int64_t nnzc_total = 0; // nonempty columns over all blocks
     DevBuf dir, rank, cp, ir, cp_base_d, ir_base_d;
+    DevBuf deg;             // entries per source vertex (uint32, saturated), computed for bottom-up levels
+    DevBuf bu_ptr, bu_adj;  // bottom-up levels: the columns of v in blocks (0,i) .. (p-1,i) back to back
+                            // (int64 offsets n+1, int32 ids), grouped by range in ascending order
     std::vector<int64_t> cp_base, ir_base, nnzc, nnz_b;   // host copies, p*p
     int64_t range_begin(int b) const { int64_t x = (int64_t)b * nb; return x < n ? x : n; }
     int64_t range_len(int b) const { return range_begin(b + 1) - range_begin(b); }
@@ -89,6 +92,8 @@ enum Counter : int {
     C_EXCHANGED,         // set bits carried by the exchange
     C_PIECES,            // pieces of long columns queued for the piece kernel
     C_ROW_WORDS,         // WAH words of the compressed row exchange
+    C_NEXT_DEGREE,       // degree sum of the next frontier (direction choice)
+    C_BOTTOM_UP,         // 1: this level ran bottom-up
     C_NUM
 };
 
@@ -97,7 +102,7 @@ enum Counter : int {
 struct SearchGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int mode = -1, wbits = 0, rowx = 0;
+    int mode = -1, wbits = 0, rowx = 0, bottom_up = 0;
     int32_t* parent = nullptr;
     int32_t* level = nullptr;
 };
@@ -122,6 +127,7 @@ struct Workspace {
     DevBuf enc_flags;            // chunks with frontier bits
     DevBuf enc_done;             // slots finished by the encoder's scan
     DevBuf ctl;                  // the level values kept on the device
+    DevBuf gbits;                // exchanged streams decoded into one bitmap (bottom-up levels)
     SearchGraph sgraph[2];       // level loops as CUDA graphs, most recent configurations
     int sgraph_next = 0;
     int64_t enc_cps = 0;         // encoder chunks per slot
@@ -144,6 +150,9 @@ struct bfs_graph {
     int wah_bits = 32;
     int debug_checks = 0;
     int row_exchange = 0;
+    int symmetric = 0;           // built with symmetrize = 1: in-neighbours = out-neighbours
+    int direction = BFS_DIRECTION_TOP_DOWN;
+    int alpha = 14, beta = 24;   // switch thresholds of the hybrid
     int device = 0;
     std::atomic<int> busy{0};
     std::mutex mu;
@@ -156,6 +165,7 @@ namespace bfsgb {
 bfs_status build_layout(bfs_graph* g, int64_t n, int64_t m, const int32_t* d_src,
                         const int32_t* d_dst, int symmetrize, cudaStream_t st);
 bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st);
+bfs_status ensure_degrees(bfs_graph* g, cudaStream_t st);
 void free_workspace(bfs_graph* g);
 
 // wah.cu

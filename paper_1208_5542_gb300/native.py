@@ -25,6 +25,7 @@ P = ctypes.POINTER
 STATUS = ["BFS_OK", "BFS_ERR_INVALID_ARG", "BFS_ERR_OUT_OF_MEMORY", "BFS_ERR_CUDA", "BFS_ERR_TIMEOUT",
           "BFS_ERR_CORRUPT", "BFS_ERR_BUSY", "BFS_ERR_NOT_FOUND"]
 MODE_PLAIN, MODE_COMPRESS, MODE_COMPRESS_SIEVE = 0, 1, 2
+DIRECTION_TOP_DOWN, DIRECTION_HYBRID, DIRECTION_BOTTOM_UP = 0, 1, 2
 
 
 class Options(ctypes.Structure):
@@ -41,7 +42,8 @@ class LevelStats(ctypes.Structure):
     _fields_ = [("frontier_vertices", i64), ("exchanged_vertices", i64), ("column_hits", i64),
                 ("raw_bytes", i64), ("wah_bytes", i64), ("edges_scanned", i64), ("row_wah_bytes", i64),
                 ("ms_compress_sieve", ctypes.c_float), ("ms_communication", ctypes.c_float),
-                ("ms_traversing", ctypes.c_float), ("ms_reducing", ctypes.c_float)]
+                ("ms_traversing", ctypes.c_float), ("ms_reducing", ctypes.c_float),
+                ("bottom_up", i32), ("reserved", i32)]
 
 
 class BatchStats(ctypes.Structure):
@@ -71,6 +73,7 @@ _SIGS = {
     "bfs_graph_info": (ctypes.c_int, [vp, P(GraphInfo)]),
     "bfs_graph_set_mode": (ctypes.c_int, [vp, i32, i32]),
     "bfs_graph_set_row_exchange": (ctypes.c_int, [vp, i32]),
+    "bfs_graph_set_direction": (ctypes.c_int, [vp, i32, i32, i32]),
     "bfs_graph_directory": (ctypes.c_int, [vp, i32, i32, vp, vp]),
     "bfs_run": (ctypes.c_int, [vp, i32, vp, vp, P(RunStats), vp]),
     "bfs_run_batch": (ctypes.c_int, [vp, vp, i32, vp, vp, P(BatchStats), vp]),
