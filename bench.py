@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -118,8 +119,10 @@ class ClockSampler:
         self.path = None
 
     def start(self):
-        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples (summarised in the JSON line) go to BFS_BENCH_LOG_DIR, else the temp dir
+        log_dir = os.environ.get("BFS_BENCH_LOG_DIR") or tempfile.gettempdir()
+        os.makedirs(log_dir, exist_ok=True)
+        self.path = os.path.join(log_dir, f"clocks_{os.getpid()}.csv")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
