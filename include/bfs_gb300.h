@@ -187,9 +187,13 @@ enum {
  * Bottom-up needs the in-neighbours of v, which are its out-neighbours only
  * when the graph is undirected: a graph created with symmetrize = 0 (every
  * CSR graph included) returns BFS_ERR_INVALID_ARG for any policy other than
- * TOP_DOWN.  The first such call computes every vertex's degree (4 bytes per
- * vertex, kept with the graph; ordered on the legacy default stream and
- * synchronised).  Not safe while a search on `g` is running.
+ * TOP_DOWN.  The first such call computes every vertex's degree and a copy of
+ * the adjacency laid out for bottom-up scans: v's columns in blocks (0, i),
+ * (1, i), ... back to back (4 + 8 bytes per vertex and 4 bytes per entry, kept
+ * with the graph and counted by bfs_graph_footprint; ordered on the legacy
+ * default stream and synchronised).  Applies to bfs_run; the batched and
+ * served searches (bfs_run_batch, bfs_server_*) stay top-down.  Not safe
+ * while a search on `g` is running.
  */
 BFS_API bfs_status bfs_graph_set_direction(bfs_graph_t g, int32_t policy, int32_t alpha, int32_t beta);
 
