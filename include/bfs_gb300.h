@@ -392,6 +392,43 @@ BFS_API bfs_status bfs_wah_decode(const void *words, int64_t nwords, int64_t nbi
 BFS_API bfs_status bfs_wah_decode_static(const void *words, int64_t nwords, int64_t nbits, int32_t word_bits,
                                          uint32_t *bits, void *cuda_stream);
 
+/*
+ * PLWAH, the position-list word-aligned hybrid code that Sec. IV names beside
+ * WAH as an alternative bitmap code (Deliege and Pedersen), for one bitmap on
+ * the device.  32-bit words over 31-bit groups, bit order and active word as
+ * in 32-bit WAH (bfs_wah_encode):
+ *   literal: bit 31 = 0, bits 30..0 = one group;
+ *   fill:    bit 31 = 1, bit 30 = the fill value v, bits 29..25 = a position q
+ *            (0: none), bits 24..0 = the run length in groups (>= 1); q > 0
+ *            stands for one more group right after the run, equal to v in
+ *            every bit but its q-th (q = 1: the group's first bit).
+ * An all-0 or all-1 group is a fill group and equal fill groups form one run;
+ * a literal group right after a run that differs from the run's value in one
+ * bit is carried by the run's position and not written.  The exchange of the
+ * search keeps WAH; this code is offered beside it, for callers that ship
+ * bitmaps themselves and for comparing the two codes on the same frontiers.
+ *   bits: device, as for bfs_wah_encode (ceil(nbits/32) + 2 words readable).
+ *   nbits: 0 .. 1,040,187,361 (31 x (2^25 - 1): every run fits the 25-bit
+ *         length); larger requests return BFS_ERR_INVALID_ARG.
+ *   words: device output, capacity_words >= floor(nbits/31) + 1.
+ *   nwords: device int64, receives the word count.
+ * Allocates scratch (cudaMalloc) and synchronises `cuda_stream`.
+ */
+BFS_API bfs_status bfs_plwah_encode(const uint32_t *bits, int64_t nbits, uint32_t *words, int64_t capacity_words,
+                                   int64_t *nwords, void *cuda_stream);
+
+/*
+ * Decode a PLWAH stream (the inverse of bfs_plwah_encode; accepts well-formed
+ * non-canonical streams) into `bits` (device, ceil(nbits/32) words, bits past
+ * nbits in the last word cleared).  Allocates scratch and synchronises
+ * `cuda_stream`.  Errors: BFS_ERR_CORRUPT for a malformed stream (a fill of
+ * length 0, groups -- a position's group included -- past nbits, a missing
+ * or oversized active word, trailing words); BFS_ERR_INVALID_ARG for nbits
+ * above the limit of bfs_plwah_encode or bad pointers.
+ */
+BFS_API bfs_status bfs_plwah_decode(const uint32_t *words, int64_t nwords, int64_t nbits, uint32_t *bits,
+                                   void *cuda_stream);
+
 /* ------------------------------------------------------------ diagnostics -- */
 
 /* bfs_measure_scatter_reads -- the rate of scattered 4-byte reads of this GPU,

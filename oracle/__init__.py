@@ -70,6 +70,8 @@ def _load():
                 "oracle_cross_directory": (None, [_i64, _int, _ptr, _ptr, _ptr]),
                 "oracle_wah_encode": (_i64, [_ptr, _i64, _int, _int, _ptr]),
                 "oracle_wah_decode": (_int, [_ptr, _i64, _i64, _int, _int, _ptr]),
+                "oracle_plwah_encode": (_i64, [_ptr, _i64, _ptr]),
+                "oracle_plwah_decode": (_int, [_ptr, _i64, _i64, _ptr]),
                 "oracle_dist_bfs": (_i64, [_i64, _int, _ptr, _ptr, ctypes.c_int32, _int, _int, _int,
                                            _ptr, _ptr, _ptr, _i64, _ptr, _i64]),
             }
@@ -166,6 +168,23 @@ def wah_decode(words: np.ndarray, nbits: int, w: int = 32, fill_bit: bool = True
     bits = np.zeros(max(1, nbits), dtype=np.uint8)
     rc = _load().oracle_wah_decode(_p(words) if len(words) else 0, len(words), nbits, w,
                                    int(fill_bit), _p(bits))
+    return None if rc != 0 else bits[:nbits]
+
+
+def plwah_encode(bits: np.ndarray) -> np.ndarray:
+    """PLWAH words (uint32) of a 0/1 byte array."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    nbits = len(bits)
+    out = np.empty(nbits // 31 + 2, dtype=np.uint32)
+    nw = _load().oracle_plwah_encode(_p(bits) if nbits else 0, nbits, _p(out))
+    return out[:nw].copy()
+
+
+def plwah_decode(words: np.ndarray, nbits: int):
+    """0/1 byte array, or ``None`` if the stream is malformed."""
+    words = np.ascontiguousarray(words, dtype=np.uint32)
+    bits = np.zeros(max(1, nbits), dtype=np.uint8)
+    rc = _load().oracle_plwah_decode(_p(words) if len(words) else 0, len(words), nbits, _p(bits))
     return None if rc != 0 else bits[:nbits]
 
 

@@ -19,6 +19,10 @@
  *                            column k of block A_{i,j} holds a nonzero.
  *   oracle_wah_encode/_decode -- word-aligned hybrid code of Sec. IV, Table 3:
  *                            literal / fill / active words over (w-1)-bit groups.
+ *   oracle_plwah_encode/_decode -- position-list WAH, the alternative bitmap
+ *                            code Sec. IV names beside WAH (Deliege and
+ *                            Pedersen): a fill word also carries the one odd
+ *                            bit of the group that follows its run.
  *   oracle_dist_bfs       -- Algorithms 1, 2 and 3 (BIT, WAH, DIR-WAH) run on a
  *                            simulated p x p grid, step by step in the paper's
  *                            order, recording every exchanged buffer.
@@ -248,6 +252,104 @@ int oracle_wah_decode(const uint64_t *words, int64_t nwords, int64_t nbits, int 
         uint64_t word = words[k++];
         if ((word >> r) != 0) return -1;
         for (int64_t b = 0; b < r; ++b) bits[full * g + b] = (uint8_t)((word >> (r - 1 - b)) & 1ULL);
+    }
+    return k == nwords ? 0 : -1;
+}
+
+/* ---------------------------------------------------------------- PLWAH -- */
+
+/*
+ * Position-list word-aligned hybrid code, 32-bit words over 31-bit groups
+ * (bit order and active word as in WAH: first bit of a group most
+ * significant; the nbits mod 31 trailing bits right-aligned in a last word,
+ * first bit highest).  Word kinds:
+ *   literal: bit 31 = 0, bits 30..0 = the 31 bits of one group;
+ *   fill:    bit 31 = 1, bit 30 = the fill value v, bits 29..25 = a position
+ *            q (0: none), bits 24..0 = the run length in groups (>= 1).  A
+ *            position q > 0 stands for one more group right after the run:
+ *            all bits equal to v except bit q of the group (q = 1 is the
+ *            group's first bit).
+ * Encoding rule: an all-0 or all-1 group is a fill group; a run of equal fill
+ * groups is one fill word (a run longer than 2^25 - 1 groups continues in a
+ * new word); a literal group that directly follows a run and differs from
+ * the run's value in exactly one bit is not written -- its bit goes into the
+ * position of the run's last word; every other literal group is a literal
+ * word.  Returns the number of words written (at most nbits/31 + 1).
+ */
+int64_t oracle_plwah_encode(const uint8_t *bits, int64_t nbits, uint32_t *out)
+{
+    const uint32_t ones = 0x7fffffffu;
+    const uint32_t max_count = (1u << 25) - 1u;
+    const int64_t full = nbits / 31;
+    const int64_t r = nbits % 31;
+    int64_t nw = 0;
+    int run_value = -1;     /* value of the run the previous group belongs to, else -1 */
+    for (int64_t k = 0; k < full; ++k) {
+        uint32_t x = 0;
+        for (int b = 0; b < 31; ++b) x = (x << 1) | (uint32_t)(bits[k * 31 + b] & 1);
+        const int value = (x == 0) ? 0 : (x == ones ? 1 : -1);
+        if (value < 0) {
+            /* a literal: folded into the run before it if one bit differs */
+            const uint32_t diff = x ^ (run_value == 1 ? ones : 0u);
+            if (run_value >= 0 && (diff & (diff - 1u)) == 0u) {
+                int q = 1;          /* the odd bit's place in the group, first bit = 1 */
+                while (!((diff >> (31 - q)) & 1u)) ++q;
+                out[nw - 1] |= (uint32_t)q << 25;
+            } else {
+                out[nw++] = x;
+            }
+            run_value = -1;
+            continue;
+        }
+        if (run_value == value && (out[nw - 1] & max_count) < max_count) {
+            out[nw - 1] += 1u;
+        } else {
+            out[nw++] = 0x80000000u | ((uint32_t)value << 30) | 1u;
+        }
+        run_value = value;
+    }
+    if (r > 0) {
+        uint32_t x = 0;
+        for (int64_t b = 0; b < r; ++b) x = (x << 1) | (uint32_t)(bits[full * 31 + b] & 1);
+        out[nw++] = x;
+    }
+    return nw;
+}
+
+/* Inverse of oracle_plwah_encode (any well-formed stream, canonical or not).
+ * Returns 0, or -1 if the stream is malformed: a fill of length 0, groups
+ * beyond nbits (a position group included), a missing or oversized active
+ * word, or trailing words. */
+int oracle_plwah_decode(const uint32_t *words, int64_t nwords, int64_t nbits, uint8_t *bits)
+{
+    const int64_t full = nbits / 31;
+    const int64_t r = nbits % 31;
+    int64_t pos = 0;     /* groups written */
+    int64_t k = 0;       /* words read */
+    while (pos < full) {
+        if (k >= nwords) return -1;
+        const uint32_t word = words[k++];
+        if (word & 0x80000000u) {
+            const int64_t len = (int64_t)(word & ((1u << 25) - 1u));
+            const int value = (int)((word >> 30) & 1u);
+            const int q = (int)((word >> 25) & 31u);
+            if (len == 0 || len + (q ? 1 : 0) > full - pos) return -1;
+            for (int64_t g = 0; g < len; ++g, ++pos)
+                for (int b = 0; b < 31; ++b) bits[pos * 31 + b] = (uint8_t)value;
+            if (q) {
+                for (int b = 0; b < 31; ++b) bits[pos * 31 + b] = (uint8_t)(b == q - 1 ? !value : value);
+                ++pos;
+            }
+        } else {
+            for (int b = 0; b < 31; ++b) bits[pos * 31 + b] = (uint8_t)((word >> (30 - b)) & 1u);
+            ++pos;
+        }
+    }
+    if (r > 0) {
+        if (k >= nwords) return -1;
+        const uint32_t word = words[k++];
+        if ((word >> r) != 0) return -1;
+        for (int64_t b = 0; b < r; ++b) bits[full * 31 + b] = (uint8_t)((word >> (r - 1 - b)) & 1u);
     }
     return k == nwords ? 0 : -1;
 }

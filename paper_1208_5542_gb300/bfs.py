@@ -238,6 +238,27 @@ def wah_decode(words: torch.Tensor, nbits: int, word_bits: int = 32, stream=None
     return out[: (nbits + 31) // 32]
 
 
+def plwah_encode(bits: torch.Tensor, nbits: int, stream=None) -> torch.Tensor:
+    """PLWAH words (int32 CUDA tensor) of the first ``nbits`` bits of ``bits`` (int32 CUDA words)."""
+    words_in = (nbits + 31) // 32
+    src = torch.zeros(words_in + 2, dtype=torch.int32, device="cuda")
+    if words_in:
+        src[:words_in] = bits[:words_in]
+    cap = nbits // 31 + 1
+    out = torch.zeros(max(1, cap), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    check(native.lib().bfs_plwah_encode(_ptr(src), int(nbits), _ptr(out), int(cap), _ptr(cnt), _stream_ptr(stream)))
+    return out[: int(cnt.item())]
+
+
+def plwah_decode(words: torch.Tensor, nbits: int, stream=None) -> torch.Tensor:
+    """Decode a PLWAH stream (int32 CUDA tensor) into int32 bitmap words; raises on a malformed stream."""
+    out = torch.zeros(max(1, (nbits + 31) // 32), dtype=torch.int32, device="cuda")
+    check(native.lib().bfs_plwah_decode(_ptr(words) if words.numel() else None, int(words.numel()), int(nbits),
+                                        _ptr(out), _stream_ptr(stream)))
+    return out[: (nbits + 31) // 32]
+
+
 class Server:
     """Continuous-batching query server over resident graphs (``bfs_server_*``)."""
 
