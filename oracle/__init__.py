@@ -72,6 +72,8 @@ def _load():
                 "oracle_wah_decode": (_int, [_ptr, _i64, _i64, _int, _int, _ptr]),
                 "oracle_plwah_encode": (_i64, [_ptr, _i64, _ptr]),
                 "oracle_plwah_decode": (_int, [_ptr, _i64, _i64, _ptr]),
+                "oracle_adaptive_encode": (_i64, [_ptr, _i64, _int, _ptr, _ptr]),
+                "oracle_adaptive_decode": (_int, [_int, _ptr, _i64, _i64, _int, _ptr]),
                 "oracle_dist_bfs": (_i64, [_i64, _int, _ptr, _ptr, ctypes.c_int32, _int, _int, _int,
                                            _ptr, _ptr, _ptr, _i64, _ptr, _i64]),
             }
@@ -185,6 +187,28 @@ def plwah_decode(words: np.ndarray, nbits: int):
     words = np.ascontiguousarray(words, dtype=np.uint32)
     bits = np.zeros(max(1, nbits), dtype=np.uint8)
     rc = _load().oracle_plwah_decode(_p(words) if len(words) else 0, len(words), nbits, _p(bits))
+    return None if rc != 0 else bits[:nbits]
+
+
+ADAPTIVE_WAH, ADAPTIVE_LIST, ADAPTIVE_RAW = 0, 1, 2
+
+
+def adaptive_encode(bits: np.ndarray, w: int = 32):
+    """``(format, elements)`` of a 0/1 byte array: the smallest of its WAH stream
+    (0), sparse vector of set-bit offsets (1) and raw 32-bit bitmap words (2)."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    nbits = len(bits)
+    out = np.empty(max(nbits // (w - 1) + 2, nbits, (nbits + 31) // 32, 1), dtype=np.uint64)
+    fmt = ctypes.c_int(-1)
+    k = _load().oracle_adaptive_encode(_p(bits) if nbits else 0, nbits, w, ctypes.addressof(fmt), _p(out))
+    return int(fmt.value), out[:k].copy()
+
+
+def adaptive_decode(fmt: int, elems: np.ndarray, nbits: int, w: int = 32):
+    """0/1 byte array, or ``None`` if the elements are malformed."""
+    elems = np.ascontiguousarray(elems, dtype=np.uint64)
+    bits = np.zeros(max(1, nbits), dtype=np.uint8)
+    rc = _load().oracle_adaptive_decode(int(fmt), _p(elems) if len(elems) else 0, len(elems), nbits, w, _p(bits))
     return None if rc != 0 else bits[:nbits]
 
 

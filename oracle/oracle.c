@@ -23,6 +23,9 @@
  *                            code Sec. IV names beside WAH (Deliege and
  *                            Pedersen): a fill word also carries the one odd
  *                            bit of the group that follows its run.
+ *   oracle_adaptive_encode/_decode -- a sieved slice sent as the smallest of
+ *                            its WAH stream, its sparse vector (Sec. II,
+ *                            Table 2; Sec. V-A) and its raw bitmap (Alg. 1).
  *   oracle_dist_bfs       -- Algorithms 1, 2 and 3 (BIT, WAH, DIR-WAH) run on a
  *                            simulated p x p grid, step by step in the paper's
  *                            order, recording every exchanged buffer.
@@ -352,6 +355,82 @@ int oracle_plwah_decode(const uint32_t *words, int64_t nwords, int64_t nbits, ui
         for (int64_t b = 0; b < r; ++b) bits[full * 31 + b] = (uint8_t)((word >> (r - 1 - b)) & 1u);
     }
     return k == nwords ? 0 : -1;
+}
+
+/* ------------------------------------------------------ adaptive format -- */
+
+/*
+ * Level-adaptive format of one exchanged slice of nbits bits: the smallest,
+ * in bytes, of three encodings, the lower number on a tie:
+ *   0  its WAH stream (w-bit words, Sec. IV), w/8 bytes a word;
+ *   1  its sparse vector (Sec. II represents a sparse frontier as the list of
+ *      its vertices, Table 2; Sec. V-A notes that a sieved slice is very
+ *      sparse): the offsets of its set bits inside the slice in increasing
+ *      order, 4 bytes each (a slice is a range of fewer than 2^31 vertices);
+ *   2  its raw bitmap (the BIT exchange of Alg. 1): ceil(nbits/32) 32-bit
+ *      words, bit b = bit b%32 of word b/32.
+ * Every element goes to out as one uint64 value; returns their count and
+ * sets *format.  out must hold max(nbits/(w-1) + 1, nbits, ceil(nbits/32)).
+ */
+int64_t oracle_adaptive_encode(const uint8_t *bits, int64_t nbits, int w, int *format, uint64_t *out)
+{
+    int64_t ones = 0;
+    for (int64_t b = 0; b < nbits; ++b) ones += bits[b] & 1;
+    const int64_t raw_words = (nbits + 31) / 32;
+    const int64_t wah_words = oracle_wah_encode(bits, nbits, w, 1, out);
+    const int64_t wah_bytes = wah_words * (w / 8), list_bytes = 4 * ones, raw_bytes = 4 * raw_words;
+    if (wah_bytes <= list_bytes && wah_bytes <= raw_bytes) {
+        *format = 0;
+        return wah_words;
+    }
+    if (list_bytes <= raw_bytes) {
+        *format = 1;
+        int64_t k = 0;
+        for (int64_t b = 0; b < nbits; ++b)
+            if (bits[b] & 1) out[k++] = (uint64_t)b;
+        return k;
+    }
+    *format = 2;
+    for (int64_t x = 0; x < raw_words; ++x) {
+        uint64_t word = 0;
+        for (int q = 0; q < 32 && x * 32 + q < nbits; ++q) word |= (uint64_t)(bits[x * 32 + q] & 1) << q;
+        out[x] = word;
+    }
+    return raw_words;
+}
+
+/* Inverse of oracle_adaptive_encode for any of the three formats.  Returns 0,
+ * or -1 if the elements are malformed: a bad WAH stream; a sparse vector that
+ * is not strictly increasing or names an offset >= nbits; a raw bitmap of the
+ * wrong length or with bits set past nbits; an unknown format. */
+int oracle_adaptive_decode(int format, const uint64_t *in, int64_t count, int64_t nbits, int w, uint8_t *bits)
+{
+    for (int64_t b = 0; b < nbits; ++b) bits[b] = 0;
+    if (format == 0) return oracle_wah_decode(in, count, nbits, w, 1, bits);
+    if (format == 1) {
+        for (int64_t k = 0; k < count; ++k) {
+            if (in[k] >= (uint64_t)nbits || (k > 0 && in[k] <= in[k - 1])) return -1;
+            bits[in[k]] = 1;
+        }
+        return 0;
+    }
+    if (format == 2) {
+        if (count != (nbits + 31) / 32) return -1;
+        for (int64_t x = 0; x < count; ++x) {
+            if (in[x] >> 32) return -1;
+            for (int q = 0; q < 32; ++q) {
+                const int64_t b = x * 32 + q;
+                const int v = (int)((in[x] >> q) & 1u);
+                if (b >= nbits) {
+                    if (v) return -1;
+                } else {
+                    bits[b] = (uint8_t)v;
+                }
+            }
+        }
+        return 0;
+    }
+    return -1;
 }
 
 /* ------------------------------------------- Algorithms 1-3 on a p x p grid -- */
