@@ -180,6 +180,17 @@ def hm_gteps(m, t):
 
 
 # ---------------------------------------------------------- reference arm --
+def workload_config(args, n, tuples, nroots):
+    """The workload keys both arms report (so that their lines pair up)."""
+    scale, ef, p, _, _, desc = WORKLOADS[args.workload]
+    return {"workload": desc + f"-{MODE_NAMES[args.mode]}-{nroots}roots" +
+            ("" if args.direction == "top_down" else f"-{args.direction}"), "scale": scale,
+            "edgefactor": ef, "vertices": n, "tuples": int(tuples), "grid": f"{p}x{p}",
+            "mode": MODE_NAMES[args.mode], "wah_word_bits": args.wah_bits, "roots": nroots,
+            "direction": args.direction if args.direction != "hybrid"
+            else f"hybrid (alpha {args.alpha}, beta {args.beta})"}
+
+
 def run_reference(args):
     """The CPU oracle, as it stands, on the host cores (one core)."""
     import numpy as np  # noqa: F401
@@ -187,7 +198,9 @@ def run_reference(args):
     import graphgen
     import oracle
     rank = int(os.environ.get("RANK", "0"))
-    scale, ef, p, kind, nroots, desc = WORKLOADS[args.workload]
+    scale, ef, _, kind, nroots, _ = WORKLOADS[args.workload]
+    if args.roots:
+        nroots = args.roots
     if rank != 0:
         return
     n, src, dst = graphgen.edges(scale, ef, kind=kind)
@@ -213,8 +226,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(step_times) / len(step_times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": desc, "scale": scale, "edgefactor": ef, "grid": f"{p}x{p}", "roots": nroots,
-                   "step": "one search (plain single-threaded CPU oracle: queue BFS + smallest-parent pass)"},
+        "config": {**workload_config(args, n, len(src), nroots),
+                   "step": "one search (plain single-threaded CPU oracle: queue BFS + smallest-parent pass)",
+                   "parallelism": "one host core"},
         "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} roots of the {nroots}, one per step"},
         "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -620,12 +634,7 @@ def main():
         "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": desc + f"-{MODE_NAMES[args.mode]}-{len(roots)}roots" +
-                   ("" if args.direction == "top_down" else f"-{args.direction}"), "scale": scale,
-                   "edgefactor": ef, "vertices": n, "tuples": int(len(src)), "grid": f"{p}x{p}",
-                   "mode": MODE_NAMES[args.mode], "wah_word_bits": args.wah_bits, "roots": len(roots),
-                   "direction": args.direction if args.direction != "hybrid"
-                   else f"hybrid (alpha {args.alpha}, beta {args.beta})",
+        "config": {**workload_config(args, n, len(src), len(roots)),
                    "step": "one search per root", "l2": "flushed (256 MiB write) before every search",
                    "parallelism": f"replicas x{world}"},
         "plain_gpu": plain,

@@ -1,0 +1,43 @@
+"""bench.py's reference arm (the CPU oracle) keeps the JSON-line contract and
+reports the same workload keys as the GPU arm, so that the two lines pair up."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _reference_line(*extra):
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "s12", "--steps", "2",
+                          "--warmup", "3", *extra], cwd=ROOT, capture_output=True, text=True, timeout=300, check=True)
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    return json.loads(lines[0])
+
+
+def test_reference_line_contract():
+    d = _reference_line()
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["unit"] == "GTEPS" and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 3 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_config_matches_the_gpu_arm():
+    sys.path.insert(0, ROOT)
+    import bench
+    for extra, argv in [((), []), (("--roots", "4", "--direction", "hybrid"), ["--roots", "4", "--direction", "hybrid"])]:
+        d = _reference_line(*extra)
+        old = sys.argv
+        sys.argv = ["bench.py", "--workload", "s12", *argv]
+        try:
+            args = bench.parse()
+        finally:
+            sys.argv = old
+        want = bench.workload_config(args, d["config"]["vertices"], d["config"]["tuples"], d["config"]["roots"])
+        assert {k: d["config"][k] for k in want} == want
+        assert d["config"]["roots"] == (int(argv[1]) if argv else 16)
