@@ -212,6 +212,23 @@ def adaptive_decode(fmt: int, elems: np.ndarray, nbits: int, w: int = 32):
     return None if rc != 0 else bits[:nbits]
 
 
+def adaptive_trace(tr, n: int, p: int, mode: int = COMPRESS_SIEVE, w: int = 32):
+    """The level-adaptive exchange of a traced search (``dist_bfs(..., trace=True)``):
+    per exchange, per slot, ``(format, elements)`` of its slice re-sent as the
+    smallest of WAH stream, sparse vector and raw bitmap."""
+    out = []
+    for level in tr:
+        row = []
+        for s, words in enumerate(level):
+            j = s % p if mode == COMPRESS_SIEVE else s
+            bits = wah_decode(np.asarray(words, np.uint64), range_len(n, p, j), w)
+            if bits is None:
+                raise ValueError(f"traced stream of slot {s} does not decode")
+            row.append(adaptive_encode(bits, w))
+        out.append(row)
+    return out
+
+
 def dist_bfs(g: CSR, p: int, root: int, mode: int = COMPRESS_SIEVE, w: int = 32,
              use_max: bool = False, trace: bool = False, max_levels: int = 256,
              trace_cap: int | None = None):

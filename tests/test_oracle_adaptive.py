@@ -103,3 +103,26 @@ def test_search_levels_choose_by_density():
     assert tot["adaptive"] < min(tot["wah"], tot["raw"])
     assert any(c[RAW] == sum(c) for c in per_level)          # a dense level: every slice raw
     assert per_level[1][LIST] == sum(per_level[1])           # the root's neighbours: every slice a vector
+
+
+@pytest.mark.parametrize("mode,w", [(oracle.COMPRESS_SIEVE, 32), (oracle.COMPRESS, 32), (oracle.COMPRESS_SIEVE, 64)])
+def test_adaptive_trace_carries_the_same_slices(mode, w):
+    """Every slot of the adaptive exchange decodes to the slice the WAH exchange
+    carries: the format changes the bytes, never the frontier."""
+    n, src, dst = graphgen.edges(12, 16)
+    go = oracle.csr(n, src, dst)
+    p = 4
+    root = int(graphgen.pick_roots(n, src, dst, 1)[0])
+    _, _, tr = oracle.dist_bfs(go, p, root, mode=mode, w=w, trace=True)
+    ad = oracle.adaptive_trace(tr, n, p, mode=mode, w=w)
+    assert len(ad) == len(tr)
+    for level, arow in zip(tr, ad):
+        assert len(level) == len(arow) == (p * p if mode == oracle.COMPRESS_SIEVE else p)
+        for s, (words, (fmt, elems)) in enumerate(zip(level, arow)):
+            j = s % p if mode == oracle.COMPRESS_SIEVE else s
+            nbits = oracle.range_len(n, p, j)
+            want = oracle.wah_decode(np.asarray(words, np.uint64), nbits, w)
+            got = oracle.adaptive_decode(fmt, elems, nbits, w)
+            assert got is not None and (got == want).all()
+            if fmt == WAH:
+                assert (np.asarray(elems, np.uint64) == np.asarray(words, np.uint64)).all()
