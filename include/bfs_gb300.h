@@ -10,7 +10,11 @@
  * with the word-aligned hybrid code (Sec. IV, Table 3, Alg. 2) after being
  * sieved by the cross directory V_{i,j} (Eq. 4-5, Sec. V-B, Alg. 3).  On one
  * GPU the p x p processor grid is a virtual grid of blocks in HBM and every
- * exchanged message is a per-block buffer in HBM.
+ * exchanged message is a per-block buffer in HBM.  Beside the paper's three
+ * algorithms: the hybrid top-down / bottom-up levels it names as future work
+ * (Sec. VIII, IX; bfs_graph_set_direction), bit-parallel batches of up to 64
+ * roots and a continuous-batching server (bfs_run_batch, bfs_server_*), and
+ * the PLWAH code it names beside WAH (Sec. IV; bfs_plwah_*).
  *
  * Conventions for every entry point:
  *   - Errors are returned as a bfs_status; nothing throws across the ABI and
