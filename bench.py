@@ -172,6 +172,16 @@ def job_value(inv, ms_step, n_roots, dist=None, device=None):
     return ((n_roots * world / inv) / 1e9 if inv > 0 else 0.0), ms_step
 
 
+def compression_factor(exch, mode):
+    """C (Alg. 2) or C' (Alg. 3) of Sec. VI-A: the mean over the levels of the
+    compressed-to-raw size of the exchange, 1 / C_i at level i.  None for
+    PLAIN (nothing is compressed) or when no level was recorded."""
+    r = [e["wah_over_raw"] for e in exch if e.get("wah_over_raw") is not None]
+    if mode == 0 or not r:
+        return None
+    return {"symbol": "C'" if mode == 2 else "C", "value": round(sum(r) / len(r), 6), "levels": len(r)}
+
+
 def hm_gteps(m, t):
     """Harmonic mean of m_r / t_r in GTEPS (t in seconds)."""
     s = sum(tr / mr for mr, tr in zip(m, t) if mr > 0)
@@ -656,6 +666,7 @@ def main():
                                    else "through L1/L2, one scattered read per entry"}},
         "phases_ms_per_search": phases,
         "exchange_per_level": exch,
+        "compression_factor": compression_factor(exch, args.mode),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,

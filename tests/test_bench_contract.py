@@ -41,3 +41,16 @@ def test_reference_config_matches_the_gpu_arm():
         want = bench.workload_config(args, d["config"]["vertices"], d["config"]["tuples"], d["config"]["roots"])
         assert {k: d["config"][k] for k in want} == want
         assert d["config"]["roots"] == (int(argv[1]) if argv else 16)
+
+
+def test_compression_factor_is_the_mean_of_the_level_ratios():
+    """Sec. VI-A: C = (1/d) sum_i 1/C_i with C_i = raw / compressed at level i."""
+    sys.path.insert(0, ROOT)
+    import bench
+    exch = [{"level": 0, "wah_over_raw": 0.001}, {"level": 1, "wah_over_raw": 0.5},
+            {"level": 2, "wah_over_raw": 1.03}, {"level": 3, "wah_over_raw": None}]
+    got = bench.compression_factor(exch, 2)
+    assert got == {"symbol": "C'", "value": round((0.001 + 0.5 + 1.03) / 3, 6), "levels": 3}
+    assert bench.compression_factor(exch, 1)["symbol"] == "C"
+    assert bench.compression_factor(exch, 0) is None
+    assert bench.compression_factor([], 2) is None
