@@ -16,7 +16,9 @@ Each function follows a passage of the paper:
   (Eq. 4) and the cross directory (Eq. 5).
 * :func:`wah_encode` / :func:`wah_decode` -- the WAH code of Sec. IV, Table 3.
 * :func:`dist_bfs` -- Algorithms 1, 2, 3 (BIT, WAH, DIR-WAH) on a simulated
-  p x p grid, with every exchanged buffer recorded.
+  p x p grid, with every exchanged buffer recorded: the column streams of the
+  frontier exchange and, for DIR-WAH, the row buffers of the fold (the WAH
+  stream of what each block reached, sieved by the visited set).
 * :func:`level_exchange` -- the exchanged buffers for one given frontier.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against worked examples
@@ -75,7 +77,7 @@ def _load():
                 "oracle_adaptive_encode": (_i64, [_ptr, _i64, _int, _ptr, _ptr]),
                 "oracle_adaptive_decode": (_int, [_int, _ptr, _i64, _i64, _int, _ptr]),
                 "oracle_dist_bfs": (_i64, [_i64, _int, _ptr, _ptr, ctypes.c_int32, _int, _int, _int,
-                                           _ptr, _ptr, _ptr, _i64, _ptr, _i64]),
+                                           _ptr, _ptr, _ptr, _i64, _ptr, _i64, _ptr, _i64, _ptr]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -231,42 +233,62 @@ def adaptive_trace(tr, n: int, p: int, mode: int = COMPRESS_SIEVE, w: int = 32):
 
 def dist_bfs(g: CSR, p: int, root: int, mode: int = COMPRESS_SIEVE, w: int = 32,
              use_max: bool = False, trace: bool = False, max_levels: int = 256,
-             trace_cap: int | None = None):
+             trace_cap: int | None = None, rows: bool = False):
     """Algorithm 1/2/3 on a simulated p x p grid.
 
     Returns ``(level, parent, trace)``; ``trace`` is a list (one entry per
     exchange, i.e. per BFS level that had a nonempty frontier) of lists of
     word arrays, indexed by slot: ``i*p + j`` for DIR-WAH (stream from source
     range j to block-row i), ``j`` for WAH.  ``None`` unless ``trace``.
+
+    With ``rows=True`` (DIR-WAH only) a fourth element is returned: the row
+    buffers of every level's fold, in the same layout (slot ``i*p + j`` = the
+    WAH stream of the vertices of range i that block (i, j) reached, sieved by
+    the visited set of range i before the level).
     """
     lib = _load()
     level = np.empty(g.n, dtype=np.int32)
     parent = np.empty(g.n, dtype=np.int32)
     slots = p * p if mode == COMPRESS_SIEVE else (p if mode == COMPRESS else 0)
+    if rows and mode != COMPRESS_SIEVE:
+        raise ValueError("row buffers exist for DIR-WAH (COMPRESS_SIEVE) only")
+    if (trace or rows) and trace_cap is None:
+        trace_cap = max_levels * (slots * 2 + (g.n * (p if mode == COMPRESS_SIEVE else 1)) // (w - 1) + 8)
     if trace and slots:
-        if trace_cap is None:
-            trace_cap = max_levels * (slots * 2 + (g.n * (p if mode == COMPRESS_SIEVE else 1)) // (w - 1) + 8)
         words = np.empty(trace_cap, dtype=np.uint64)
         counts = np.zeros(max_levels * slots, dtype=np.int64)
         wp, cp = _p(words), _p(counts)
+        tcap = trace_cap
     else:
         words = counts = None
         wp = cp = 0
-        trace_cap = 0
+        tcap = 0
+    if rows:
+        rwords = np.empty(trace_cap, dtype=np.uint64)
+        rcounts = np.zeros(max_levels * slots, dtype=np.int64)
+        rwp, rcp, rcap = _p(rwords), _p(rcounts), trace_cap
+    else:
+        rwords = rcounts = None
+        rwp = rcp = rcap = 0
     rc = lib.oracle_dist_bfs(g.n, p, _p(g.row_ptr), _p(g.col), root, mode, w, int(use_max),
-                             _p(level), _p(parent), wp, trace_cap, cp, max_levels)
+                             _p(level), _p(parent), wp, tcap, cp, max_levels, rwp, rcap, rcp)
     if rc < 0:
         raise ValueError(f"oracle_dist_bfs failed ({rc})")
-    tr = None
-    if trace and slots:
-        tr, off = [], 0
+
+    def unpack(ws, cs):
+        out, off = [], 0
         for k in range(min(rc, max_levels)):
             lv = []
             for s in range(slots):
-                c = int(counts[k * slots + s])
-                lv.append(words[off: off + c].copy())
+                c = int(cs[k * slots + s])
+                lv.append(ws[off: off + c].copy())
                 off += c
-            tr.append(lv)
+            out.append(lv)
+        return out
+
+    tr = unpack(words, counts) if (trace and slots) else None
+    if rows:
+        return level, parent, tr, unpack(rwords, rcounts)
     return level, parent, tr
 
 

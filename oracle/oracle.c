@@ -26,9 +26,14 @@
  *   oracle_adaptive_encode/_decode -- a sieved slice sent as the smallest of
  *                            its WAH stream, its sparse vector (Sec. II,
  *                            Table 2; Sec. V-A) and its raw bitmap (Alg. 1).
- *   oracle_dist_bfs       -- Algorithms 1, 2 and 3 (BIT, WAH, DIR-WAH) run on a
- *                            simulated p x p grid, step by step in the paper's
- *                            order, recording every exchanged buffer.
+ *   oracle_dist_bfs       -- Algorithms 1, 2 and 3 (BIT, WAH, DIR-WAH) on a
+ *                            simulated p x p grid: the frontier exchange
+ *                            (raw, compressed, or sieved by f_j (.) V_{i,j}
+ *                            and compressed), the per-block products of the
+ *                            (select, min) semiring, their fold over a
+ *                            block-row and the visited mask, recording every
+ *                            exchanged buffer -- the column streams and, for
+ *                            DIR-WAH, the compressed row buffers of the fold.
  *
  * Bitmaps are held one byte per bit (0 or 1) so every step reads as its
  * definition.  Vertex ranges: range b of a p-way split of n vertices is
@@ -436,57 +441,79 @@ int oracle_adaptive_decode(int format, const uint64_t *in, int64_t count, int64_
 /* ------------------------------------------- Algorithms 1-3 on a p x p grid -- */
 
 /*
- * Distributed BFS on a simulated p x p grid, one processor P_i per vertex
- * range i (paper indices shifted to start at 0).  mode 0 = BIT (Alg. 1),
- * 1 = WAH (Alg. 2), 2 = DIR-WAH (Alg. 3).  Each level:
- *   t_i = sum_j A_{i,j} (x) f_{i,j}   over the (select, min|max) semiring, so
- *         t_i[v] carries the chosen parent of v;
- *   t_i = t_i (.) not(pi_i);  pi_i = pi_i + t_i;  f_i = t_i;
- * then the exchange of the new f:
- *   BIT:     f = Allgatherv(f_i)                       (raw bitmaps)
- *   WAH:     f' = Allgatherv(Compress(f_i)); f = Uncompress(f')
- *   DIR-WAH: f_{i,j} = f_i (.) V_{j,i}; f'_{i,j} = Compress(f_{i,j});
- *            g'_i = Alltoallv(f'_i); f_{i,j} = Uncompress(g'_{i,j})
+ * Distributed BFS on a simulated p x p grid (Eq. 1-3), one processor P_i per
+ * vertex range i (the paper's indices shifted to start at 0).  mode 0 = BIT
+ * (Alg. 1), 1 = WAH (Alg. 2), 2 = DIR-WAH (Alg. 3).  Every level computes:
+ *   the exchange of the frontier f (the frontier of level k):
+ *     BIT:     every P_i receives the raw bitmap of every range j;
+ *     WAH:     every range j is WAH-compressed once (Sec. IV, Table 3), every
+ *              P_i receives the p streams and decompresses them;
+ *     DIR-WAH: the slice of range j bound for P_i is sieved by the cross
+ *              directory first, f_j (.) V_{i,j} (Eq. 4-5, Sec. V), then
+ *              compressed; P_i decompresses the stream it receives from
+ *              every range j;
+ *   the product of every block, t_{i,j} = A_{i,j} (x) f_{i,j} over the
+ *     (select, min) semiring (or (select, max), use_max): t_{i,j}[v] is the
+ *     smallest (largest) source u of range j that P_i received with an entry
+ *     u -> v, for v in range i;
+ *   the fold of block-row i, t_i = (+)_j t_{i,j} (the same semiring);
+ *   the visited mask and update, t_i = t_i (.) not(pi_i), pi_i = pi_i + t_i,
+ *     and the next frontier f_i = t_i, whose vertices get level k + 1 and
+ *     parent t_i[v].
  * The exchange before level 0 carries f = {root}.
  *
- * Trace (optional, trace_counts != NULL): the exchanged buffers of the
- * exchange that feeds level k are recorded as
+ * Column trace (optional, trace_counts != NULL; modes 1 and 2): the
+ * compressed frontier slices of the exchange that feeds level k,
  *   WAH:     one stream per source range j, slot s = j        (p slots)
- *   DIR-WAH: stream "from range j to block-row i", slot s = i*p + j  (p*p slots)
+ *   DIR-WAH: the stream of f_j (.) V_{i,j}, slot s = i*p + j   (p*p slots)
  * trace_counts[k * slots + s] = word count; the words are appended to
  * trace_words in (k, s) order (trace_cap words available).
  *
+ * Row trace (optional, row_counts != NULL; mode 2): the row buffer of every
+ * block in the level-k fold when the fold is itself a compressed exchange
+ * (the 2D partitioning the paper names in Sec. VIII): the WAH stream of the
+ * vertices block (i,j) reached, sieved by the visited set of range i before
+ * the level, support(t_{i,j}) (.) not(pi_i), slot s = i*p + j, counted and
+ * appended like the column trace (row_cap words available).  The oracle
+ * decompresses every row buffer and checks that their OR over j is the next
+ * frontier of range i.
+ *
  * Outputs level[] and parent[] (length n).  Returns the number of levels
- * traced (the number of exchanges), -1 on a bad argument, -2 if the trace
- * does not fit, -3 on a decode failure (cannot happen for encoder output).
+ * traced (the number of exchanges), -1 on a bad argument, -2 if a trace does
+ * not fit, -3 on a decode failure (cannot happen for encoder output), -4 if
+ * the OR of the row buffers differs from the next frontier (cannot happen).
  */
 int64_t oracle_dist_bfs(int64_t n, int p, const int64_t *row_ptr, const int32_t *col, int32_t root,
                         int mode, int w, int use_max, int32_t *level, int32_t *parent,
                         uint64_t *trace_words, int64_t trace_cap, int64_t *trace_counts,
-                        int64_t max_levels)
+                        int64_t max_levels, uint64_t *row_words, int64_t row_cap, int64_t *row_counts)
 {
     if (n <= 0 || p <= 0 || p > n || root < 0 || root >= n || mode < 0 || mode > 2) return -1;
     const int64_t nb = range_size(n, p);
+    const int rows = (mode == 2 && row_counts != NULL);
     uint8_t *f = (uint8_t *)calloc((size_t)n, 1);        /* current frontier, all ranges */
     uint8_t *pi = (uint8_t *)calloc((size_t)n, 1);       /* visited */
     int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);   /* semiring value, -1 = zero */
+    int32_t *tij = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nb + 1));  /* one block's product */
     uint8_t *recv = (uint8_t *)calloc((size_t)n * (size_t)p, 1);   /* f_{i,j} as received by P_i */
     uint8_t *slice = (uint8_t *)malloc((size_t)nb + 1);
     uint8_t *dec = (uint8_t *)malloc((size_t)nb + 1);
+    uint8_t *fold = (uint8_t *)calloc((size_t)n, 1);     /* OR of the decoded row buffers */
     uint64_t *words = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nb + 2));
     uint8_t *D = (mode == 2) ? (uint8_t *)malloc((size_t)n * (size_t)p) : NULL;
-    if (!f || !pi || !t || !recv || !slice || !dec || !words || (mode == 2 && !D)) {
-        free(f); free(pi); free(t); free(recv); free(slice); free(dec); free(words); free(D);
+    if (!f || !pi || !t || !tij || !recv || !slice || !dec || !fold || !words || (mode == 2 && !D)) {
+        free(f); free(pi); free(t); free(tij); free(recv); free(slice); free(dec); free(fold); free(words);
+        free(D);
         return -1;
     }
-    /* Alg. 3 line 2: initialise the cross directories (static for the graph) */
+    /* the cross directories of every processor (Eq. 5), static for the graph */
     if (mode == 2) oracle_cross_directory(n, p, row_ptr, col, D);
     /* recv[i*n + u] = bit u of the frontier as P_i holds it after the exchange */
     for (int64_t v = 0; v < n; ++v) { level[v] = -1; parent[v] = -1; }
     level[root] = 0; parent[root] = root;
     f[root] = 1; pi[root] = 1;
     const int64_t slots = (mode == 2) ? (int64_t)p * p : (mode == 1 ? p : 0);
-    int64_t k = 0, used = 0, rc = 0;
+    int64_t k = 0, used = 0, row_used = 0, rc = 0;
     for (;;) {
         /* ---- exchange of f (the frontier of level k) ---- */
         int64_t fsize = 0;
@@ -522,17 +549,39 @@ int64_t oracle_dist_bfs(int64_t n, int p, const int64_t *row_ptr, const int32_t 
                 memcpy(dst, dec, (size_t)jl);
             }
         }
-        /* ---- t_i = sum_j A_{i,j} (x) f_{i,j} over (select, min|max) ---- */
-        for (int64_t v = 0; v < n; ++v) t[v] = -1;
+        /* ---- t_i = (+)_j t_{i,j}, t_{i,j} = A_{i,j} (x) f_{i,j} over (select, min|max) ---- */
+        for (int64_t v = 0; v < n; ++v) { t[v] = -1; fold[v] = 0; }
         for (int i = 0; i < p; ++i) {
             const int64_t ib = range_begin(n, p, i), ie = range_end(n, p, i);
             const uint8_t *fi = recv + (size_t)i * (size_t)n;
-            for (int64_t u = 0; u < n; ++u) {
-                if (!fi[u]) continue;
-                for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
-                    int32_t v = col[e];
-                    if (v < ib || v >= ie) continue;
-                    if (t[v] < 0 || (!use_max && u < t[v]) || (use_max && u > t[v])) t[v] = (int32_t)u;
+            for (int j = 0; j < p; ++j) {
+                const int64_t jb = range_begin(n, p, j), je = range_end(n, p, j);
+                for (int64_t v = ib; v < ie; ++v) tij[v - ib] = -1;
+                for (int64_t u = jb; u < je; ++u) {
+                    if (!fi[u]) continue;
+                    for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                        const int32_t v = col[e];
+                        if (v < ib || v >= ie) continue;
+                        int32_t *x = &tij[v - ib];
+                        if (*x < 0 || (!use_max && u < *x) || (use_max && u > *x)) *x = (int32_t)u;
+                    }
+                }
+                if (rows && k < max_levels) {
+                    /* row buffer of block (i,j): what it reached, sieved by not(pi_i) */
+                    for (int64_t v = ib; v < ie; ++v) slice[v - ib] = (uint8_t)(tij[v - ib] >= 0 && !pi[v]);
+                    const int64_t nw = oracle_wah_encode(slice, ie - ib, w, 1, words);
+                    row_counts[k * slots + (int64_t)i * p + j] = nw;
+                    if (row_used + nw > row_cap) { rc = -2; goto done; }
+                    memcpy(row_words + row_used, words, sizeof(uint64_t) * (size_t)nw);
+                    row_used += nw;
+                    if (oracle_wah_decode(words, nw, ie - ib, w, 1, dec) != 0) { rc = -3; goto done; }
+                    for (int64_t v = ib; v < ie; ++v) fold[v] |= dec[v - ib];
+                }
+                /* the fold: t_i = t_i (+) t_{i,j} */
+                for (int64_t v = ib; v < ie; ++v) {
+                    const int32_t x = tij[v - ib];
+                    if (x < 0) continue;
+                    if (t[v] < 0 || (!use_max && x < t[v]) || (use_max && x > t[v])) t[v] = x;
                 }
             }
         }
@@ -542,10 +591,13 @@ int64_t oracle_dist_bfs(int64_t n, int p, const int64_t *row_ptr, const int32_t 
             f[v] = (uint8_t)(t[v] >= 0);
             if (f[v]) { pi[v] = 1; level[v] = (int32_t)(k + 1); parent[v] = t[v]; }
         }
+        if (rows && k < max_levels)
+            for (int64_t v = 0; v < n; ++v)
+                if (fold[v] != f[v]) { rc = -4; goto done; }
         ++k;
     }
     rc = k;
 done:
-    free(f); free(pi); free(t); free(recv); free(slice); free(dec); free(words); free(D);
+    free(f); free(pi); free(t); free(tij); free(recv); free(slice); free(dec); free(fold); free(words); free(D);
     return rc;
 }

@@ -60,3 +60,16 @@ def wah_examples():
         else:
             cur[key] = int(vals[0])
     return out
+
+
+def row_buffer_example():
+    """{p: [[word per slot] per level]} of paper_row_buffers.txt."""
+    out = {}
+    for tok in _lines("paper_row_buffers.txt"):
+        if tok[0] != "words":
+            continue
+        p, k = int(tok[1]), int(tok[2])
+        lv = out.setdefault(p, [])
+        assert len(lv) == k
+        lv.append([int(x, 16) for x in tok[3:]])
+    return out
