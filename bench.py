@@ -65,6 +65,8 @@ def parse():
                     help="top_down: the paper's algorithms; hybrid: top-down / bottom-up levels chosen per level")
     ap.add_argument("--alpha", type=int, default=4, help="hybrid: bottom-up once m_f > m_u / alpha")
     ap.add_argument("--beta", type=int, default=24, help="hybrid: top-down again once the frontier < n / beta")
+    ap.add_argument("--row-exchange", default="on", choices=["on", "off"],
+                    help="compress_sieve: the fold of each block-row as a compressed exchange of row buffers")
     ap.add_argument("--roots", type=int, default=0, help="override the number of roots")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -423,6 +425,7 @@ def main():
     n, src, dst = graphgen.edges(scale, ef, kind=kind)
     roots = graphgen.pick_roots(n, src, dst, nroots, seed=7 + 1000 * rank)
     g = bfs.Graph.from_edges(n, src, dst, p=p, mode=args.mode, wah_bits=args.wah_bits)
+    g.set_row_exchange(args.row_exchange == "on")
     if args.direction != "top_down":
         g.set_direction(DIRECTIONS[args.direction], args.alpha, args.beta)
     src_d = torch.from_numpy(src).to(dev)
@@ -556,13 +559,16 @@ def main():
                      "sieve_drop": round(1 - a["exchanged"] / (p * a["frontier"]), 4) if a["frontier"] else None})
 
     # phase breakdown (Table 6 labels), summed over the timed searches
-    phases = {"compression_sieve": 0.0, "communication": 0.0, "traversing": 0.0, "reducing": 0.0}
+    phases = {"compression_sieve": 0.0, "communication": 0.0, "traversing": 0.0, "row_compression_sieve": 0.0,
+              "row_fold": 0.0, "reducing": 0.0}
     for sts in stats_cs:
         for st in sts:
             for ls in st.levels:
                 phases["compression_sieve"] += ls["ms_compress_sieve"]
                 phases["communication"] += ls["ms_communication"]
                 phases["traversing"] += ls["ms_traversing"]
+                phases["row_compression_sieve"] += ls["ms_row_compress"]
+                phases["row_fold"] += ls["ms_row_fold"]
                 phases["reducing"] += ls["ms_reducing"]
     nsearch = sum(len(s) for s in stats_cs)
     phases = {k: round(v / nsearch, 4) for k, v in phases.items()}

@@ -77,11 +77,12 @@ typedef struct {
     int32_t autotune;        /* reserved, 0 */
     int32_t debug_checks;    /* 1: kernels verify internal invariants and report
                                 BFS_ERR_CORRUPT instead of continuing */
-    int32_t row_exchange;    /* 1: compressed row exchange (see bfs_graph_set_row_exchange) */
+    int32_t row_exchange;    /* 1: compressed row exchange of the fold in COMPRESS_SIEVE mode
+                                (see bfs_graph_set_row_exchange) */
 } bfs_options;
 
 /* Fill `opt` with the defaults: 1 x 1 grid, BFS_MODE_COMPRESS_SIEVE, 32-bit words,
- * row exchange off. */
+ * row exchange on. */
 BFS_API void bfs_options_default(bfs_options *opt);
 
 /* Human-readable name of a status ("BFS_OK", ...). Never NULL. */
@@ -144,17 +145,25 @@ BFS_API bfs_status bfs_graph_info(bfs_graph_t g, bfs_graph_info_t *info);
 BFS_API bfs_status bfs_graph_set_mode(bfs_graph_t g, int32_t mode, int32_t wah_word_bits);
 
 /*
- * The row exchange of the 2D partition (the fold of the partial next
- * frontiers of one block-row; the paper names the combination with 2D
- * partitioning in Sec. VIII).  The expansion keeps, per CTA and block-row i, a
- * partial next bitmap t_i of the destinations it reached, already sieved by
- * not(pi_i) (vertices visited before the level are never set: the row
- * exchange drops already-visited vertices).  With `enabled` = 0 the partials
- * are OR-folded into t through L2; with 1 each partial is WAH-encoded
- * (32-bit words) into a row buffer when its CTA leaves the row, and the row is
- * folded by OR-decoding its buffers.  The result never changes t_i.  Applies
- * when a range's bitmaps fit in shared memory (range size up to about 830K
- * vertices); larger ranges fold through L2 either way.
+ * The row exchange of the 2D partition: the fold of block-row i, which the
+ * paper names as the combination of its method with 2D partitioning (Sec.
+ * VIII), made a compressed and sieved exchange like the column exchange of
+ * Alg. 3.  On a level with the row exchange every block (i,j) records the
+ * vertices of range i it reached, t_{i,j} = support(A_{i,j} (x) f_{i,j}), in a
+ * bitmap of its own; the partial is sieved by not(pi_i) -- vertices visited
+ * before the level are dropped -- and WAH-encoded (Sec. IV, Table 3, the
+ * graph's word width) into the row buffer of slot i*p + j; the fold
+ * OR-decodes the p buffers of block-row i into t_i.  Row buffers are unique
+ * (they depend on the graph, the frontier and pi only) and can be traced
+ * (bfs_run_stats.row_trace_*).  The result never changes t_i.
+ *   enabled: 1 (the default) or 0 (the partials are ORed into t directly,
+ *   as one undivided next bitmap).
+ * Applies to top-down levels of COMPRESS_SIEVE searches (bfs_run); PLAIN and
+ * COMPRESS searches (Alg. 1, 2), bottom-up levels and the batched and served
+ * searches fold without buffers.  The first search with it allocates the
+ * partials (p*p directory-sized bitmaps) and the row buffers (p*p worst-case
+ * WAH streams), kept with the graph and counted by bfs_graph_footprint.  Not
+ * safe while a search on `g` is running.
  */
 BFS_API bfs_status bfs_graph_set_row_exchange(bfs_graph_t g, int32_t enabled);
 
@@ -221,12 +230,15 @@ typedef struct {
     int64_t raw_bytes;           /* bytes of the raw bitmap exchange: p slices of each range */
     int64_t wah_bytes;           /* bytes of the compressed streams (0 in PLAIN mode) */
     int64_t edges_scanned;       /* adjacency entries read by the expansion */
-    int64_t row_wah_bytes;       /* bytes of the compressed row exchange (0 when off) */
+    int64_t row_wah_bytes;       /* bytes of the row buffers of the fold (0 when the row exchange is
+                                    off and on bottom-up levels) */
     float ms_compress_sieve;     /* sieve + compress + decompress kernels */
     float ms_communication;      /* exchange: size scan (and packing when traced) */
     float ms_traversing;         /* expansion (the local SpMV) */
     float ms_reducing;           /* mask, visited update, level writeback, frontier count */
     int32_t bottom_up;           /* 1: the level ran bottom-up (bfs_graph_set_direction) */
+    float ms_row_compress;       /* row exchange: sieve by not(pi) + compress of the partials */
+    float ms_row_fold;           /* row exchange: decompress + OR of the row buffers (the fold) */
     int32_t reserved;
 } bfs_level_stats;
 
@@ -245,6 +257,15 @@ typedef struct {
     int64_t trace_capacity;      /* uint32 elements available in trace_words */
     int64_t *trace_counts;       /* device, capacity_levels * slots entries */
     int64_t trace_used;          /* out: uint32 elements written */
+    /* Optional row-buffer trace (device pointers, or NULL; COMPRESS_SIEVE with the
+     * row exchange on): for each level k, the row buffers of the fold packed in
+     * slot order (slot = i*p + j: the WAH stream of the vertices of range i that
+     * block (i,j) reached, sieved by not(pi_i)), words as in trace_words;
+     * row_trace_counts[k*p*p + s] = words in slot s (0 on bottom-up levels). */
+    uint32_t *row_trace_words;
+    int64_t row_trace_capacity;  /* uint32 elements available in row_trace_words */
+    int64_t *row_trace_counts;   /* device, capacity_levels * p * p entries */
+    int64_t row_trace_used;      /* out: uint32 elements written */
 } bfs_run_stats;
 
 /*

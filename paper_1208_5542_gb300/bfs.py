@@ -43,6 +43,9 @@ class SearchStats:
     trace_words: torch.Tensor | None = None         # int32 view of the packed streams
     trace_counts: torch.Tensor | None = None        # [levels, slots] int64
     trace_used: int = 0
+    row_trace_words: torch.Tensor | None = None     # int32 view of the packed row buffers of the fold
+    row_trace_counts: torch.Tensor | None = None    # [levels, p*p] int64
+    row_trace_used: int = 0
 
 
 class Graph:
@@ -146,12 +149,13 @@ class Graph:
 
     # -------------------------------------------------------------- search --
     def run(self, root: int, parent=None, level=None, stats: bool = False, timing: bool = False,
-            trace_capacity: int = 0, max_levels: int = 256, stream=None):
+            trace_capacity: int = 0, max_levels: int = 256, stream=None, row_trace_capacity: int = 0):
         """One search from ``root``; returns ``(parent, level, SearchStats | None)``.
 
         ``parent``/``level`` may be int32 CUDA tensors (filled in place), int32
         host tensors or numpy arrays (the library copies back), or None
-        (CUDA tensors are allocated).
+        (CUDA tensors are allocated).  ``trace_capacity`` / ``row_trace_capacity``
+        (uint32 elements) record the column streams / the row buffers of the fold.
         """
         if parent is None:
             parent = torch.empty(self.n, dtype=torch.int32, device="cuda")
@@ -160,7 +164,7 @@ class Graph:
         rs = None
         out_stats = None
         keep = []
-        if stats or timing or trace_capacity:
+        if stats or timing or trace_capacity or row_trace_capacity:
             out_stats = SearchStats()
             lv = (native.LevelStats * max_levels)()
             rs = native.RunStats()
@@ -177,6 +181,13 @@ class Graph:
                 rs.trace_capacity = int(trace_capacity)
                 rs.trace_counts = _ptr(tc)
                 out_stats.trace_words, out_stats.trace_counts = tw, tc
+            if row_trace_capacity:
+                rw = torch.zeros(int(row_trace_capacity), dtype=torch.int32, device="cuda")
+                rcn = torch.zeros((max_levels, self.p * self.p), dtype=torch.int64, device="cuda")
+                rs.row_trace_words = _ptr(rw)
+                rs.row_trace_capacity = int(row_trace_capacity)
+                rs.row_trace_counts = _ptr(rcn)
+                out_stats.row_trace_words, out_stats.row_trace_counts = rw, rcn
         check(native.lib().bfs_run(self._h, int(root), _ptr(parent), _ptr(level),
                                    ctypes.byref(rs) if rs is not None else None, _stream_ptr(stream)))
         if out_stats is not None:
@@ -185,8 +196,11 @@ class Graph:
             for k in range(min(out_stats.n_levels, max_levels)):
                 s = lv[k]
                 out_stats.levels.append({f: getattr(s, f) for f, _ in native.LevelStats._fields_})
+            out_stats.row_trace_used = int(rs.row_trace_used)
             if out_stats.trace_counts is not None:
                 out_stats.trace_counts = out_stats.trace_counts[: out_stats.n_levels]
+            if out_stats.row_trace_counts is not None:
+                out_stats.row_trace_counts = out_stats.row_trace_counts[: out_stats.n_levels]
         return parent, level, out_stats
 
     # -------------------------------------------------------------- batch --

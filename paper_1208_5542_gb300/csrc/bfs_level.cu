@@ -114,16 +114,19 @@ struct LevelArgs {
     int mode;
     int64_t plain_upb;                  // PLAIN units per block
     int64_t win_words;                  // words of the shared-memory row window (0: none)
-    // compressed row exchange (2D fold): row buffers of the partial next bits
+    // compressed row exchange (the fold of the 2D partition): per block (i,j)
+    // the destinations it reached, t_{i,j}, as a bitmap of range i; the
+    // encoder turns t_{i,j} & ~pi_i into the row buffer of slot i*p + j
     int row_exchange;
-    uint32_t* rowbuf;                   // rowbuf_slots x rowbuf_cap 32-bit WAH words
-    int64_t rowbuf_cap;
-    int64_t rowbuf_slots;
+    uint32_t* tblk;                     // p*p partial bitmaps, dir_stride words each
+    const void* rowbuf;                 // row buffers: p*p slots of row_cap words
+    int64_t row_cap;
+    const int64_t* row_count;           // words in each row buffer
+    const int64_t* row_first;           // per (slot, chunk): first word and its first group
+    int64_t row_cps;                    // encoder chunks per slot
+    int64_t row_bcps;                   // fold chunks per range
     int sweep;                          // all CTAs start at row 0 (rows in turn)
     const LevelCtl* ctl;                // this level's values
-    unsigned long long* rowbuf_count;   // slots used in this level
-    int32_t* rowbuf_row;                // block-row of each slot
-    int64_t* rowbuf_words;              // words in each slot
     // bottom-up levels
     uint32_t* gbits;                    // decoded streams (n bits, OR over the block-rows)
     int64_t g_words;                    // its uint32 words (a multiple of 4)
@@ -148,6 +151,8 @@ struct Visitor {
     const uint32_t* s_pi;
     uint32_t* s_t;
     int64_t rb;     // first vertex of the row
+    uint32_t* tb;   // row exchange: the partial bitmap of the visiting block (i,j), or nullptr
+    uint32_t jb;    // row exchange: first vertex of the block's source range j
     // The visited word of v (loads of several entries are issued before
     // their visits, so that their latencies overlap).
     __device__ __forceinline__ uint32_t probe(const LevelArgs& a, int32_t v) const {
@@ -163,12 +168,42 @@ struct Visitor {
     __device__ __forceinline__ uint32_t seen(const LevelArgs& a, int32_t v) const {
         return __ldcg(reinterpret_cast<const unsigned int*>(a.parent) + v);
     }
+    // The word of v's bit in the visiting block's partial t_{i,j} (row exchange).
+    __device__ __forceinline__ uint32_t seen_t(int32_t v) const {
+        const uint32_t vl = (uint32_t)(v - rb);
+        return __ldcg(tb + (vl >> 5));
+    }
+    // After the visited word piw of v was probed: v <- -1 if v was visited
+    // before the level (nothing to do), else pv <- the parent read first
+    // (DEDUP) or -1, and tw <- the partial's word read first (DEDUP with the
+    // row exchange) or 0.
+    __device__ __forceinline__ void stage(const LevelArgs& a, int32_t& v, uint32_t& piw, uint32_t& tw) const {
+        tw = 0u;
+        if (v < 0 || !fresh(v, piw)) {
+            v = -1;
+            return;
+        }
+        piw = DEDUP ? seen(a, v) : 0xffffffffu;
+        if (DEDUP && tb) tw = seen_t(v);
+    }
     // Visit of a fresh v from u, given an earlier read pv of its parent: when
     // pv <= u the visit changes nothing (pv != -1 means v already has a
     // visitor in this level, which set the next bit); otherwise lower the
     // parent, and the visitor that read -1 sets the next bit.  The visitor of
     // the first update read -1, so the bit is always set.
-    __device__ __forceinline__ void mark(const LevelArgs& a, int32_t v, int32_t u, uint32_t pv) const {
+    __device__ __forceinline__ void mark(const LevelArgs& a, int32_t v, int32_t u, uint32_t pv, uint32_t tw) const {
+        if (tb) {
+            // Row exchange: every block that reaches v records it in its own
+            // partial t_{i,j}.  The bit is already there when the word read
+            // first has it, or when the parent read first lies in [jb, u]: a
+            // visitor of the same source range lowered it and records v in
+            // the same partial.  The parent is lowered when pv > u.
+            const uint32_t vl = (uint32_t)(v - rb);
+            const bool have = ((tw >> (vl & 31u)) & 1u) || (pv <= (uint32_t)u && pv >= jb);
+            if (pv > (uint32_t)u) atomicMin(reinterpret_cast<unsigned int*>(a.parent) + v, (unsigned int)u);
+            if (!have) atomicOr(tb + (vl >> 5), 1u << (vl & 31u));
+            return;
+        }
         if (pv <= (uint32_t)u) return;
         atomicMin(reinterpret_cast<unsigned int*>(a.parent) + v, (unsigned int)u);
         if (pv != 0xffffffffu) return;
@@ -191,16 +226,16 @@ __device__ __forceinline__ void warp_column(const LevelArgs& a, const Visitor<WI
     const int32_t* col = a.ir + beg;
     for (uint32_t e = lane_id(); e < len; e += 32 * kIlp) {
         int32_t v[kIlp];
-        uint32_t w[kIlp];
+        uint32_t w[kIlp], t[kIlp];
 #pragma unroll
         for (int k = 0; k < kIlp; ++k) v[k] = (e + 32 * k < len) ? __ldg(col + e + 32 * k) : -1;
 #pragma unroll
         for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0) ? vis.probe(a, v[k]) : 0u;
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0 && vis.fresh(v[k], w[k])) ? (DEDUP ? vis.seen(a, v[k]) : 0xffffffffu) : 0u;
+        for (int k = 0; k < kIlp; ++k) vis.stage(a, v[k], w[k], t[k]);
 #pragma unroll
         for (int k = 0; k < kIlp; ++k)
-            if (v[k] >= 0) vis.mark(a, v[k], u, w[k]);
+            if (v[k] >= 0) vis.mark(a, v[k], u, w[k], t[k]);
     }
 }
 
@@ -248,7 +283,7 @@ __device__ __forceinline__ void warp_expand(const LevelArgs& a, const Visitor<WI
     const uint32_t excl = incl - len;
     for (uint32_t e0 = 0; e0 < total; e0 += 32 * kIlp) {
         int32_t v[kIlp], ou[kIlp];
-        uint32_t w[kIlp];
+        uint32_t w[kIlp], t[kIlp];
 #pragma unroll
         for (int k = 0; k < kIlp; ++k) {
             const uint32_t e = e0 + 32 * k + lane;
@@ -267,10 +302,10 @@ __device__ __forceinline__ void warp_expand(const LevelArgs& a, const Visitor<WI
 #pragma unroll
         for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0) ? vis.probe(a, v[k]) : 0u;
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0 && vis.fresh(v[k], w[k])) ? (DEDUP ? vis.seen(a, v[k]) : 0xffffffffu) : 0u;
+        for (int k = 0; k < kIlp; ++k) vis.stage(a, v[k], w[k], t[k]);
 #pragma unroll
         for (int k = 0; k < kIlp; ++k)
-            if (v[k] >= 0) vis.mark(a, v[k], ou[k], w[k]);
+            if (v[k] >= 0) vis.mark(a, v[k], ou[k], w[k], t[k]);
     }
 }
 
@@ -345,90 +380,12 @@ __device__ __forceinline__ int owner_lane(uint32_t excl, uint64_t q) {
 }
 
 // ------------------------------------------------------------ row window --
-// 32-bit WAH stream (Sec. IV, Table 3) of the CTA's window bits t & ~pi
-// (nbits of them), written to out by the whole CTA: tiles of kXT groups, one
-// group per thread, block scans of head flags and of head positions as in the
-// exchange encoder.  Returns the word count (to every thread).
-__device__ int64_t cta_encode_window(const uint32_t* s_t, const uint32_t* s_pi, int64_t win, int64_t nbits,
-                                     uint32_t* out) {
-    __shared__ uint8_t s_ty[kXT];
-    __shared__ int64_t s_red[kXW + 1];
-    __shared__ int s_next, s_carry_type;
-    __shared__ int64_t s_carry_start, s_total;
-    auto word_at = [&](int64_t w) -> uint32_t { return (w < win) ? (s_t[w] & ~s_pi[w]) : 0u; };
-    auto group = [&](int64_t g) -> uint32_t {
-        const int64_t pos = g * 31;
-        const int64_t w = pos >> 5;
-        return __funnelshift_r(word_at(w), word_at(w + 1), (uint32_t)(pos & 31)) & 0x7fffffffu;
-    };
-    auto type_of = [](uint32_t x) -> int { return x == 0u ? G_ZERO : (x == 0x7fffffffu ? G_ONE : G_LIT); };
-    const int64_t G = nbits / 31;
-    const int r = (int)(nbits % 31);
-    int64_t nw = 0, run_start = 0;
-    int prev = -1;
-    for (int64_t tb = 0; tb < G; tb += kXT) {
-        const int64_t tend = (tb + kXT < G) ? tb + kXT : G;
-        const int64_t g = tb + threadIdx.x;
-        const bool valid = g < tend;
-        const uint32_t x = valid ? group(g) : 0u;
-        const int ty = valid ? type_of(x) : G_NONE;
-        s_ty[threadIdx.x] = (uint8_t)ty;
-        if (threadIdx.x == 0) s_next = (tend < G) ? type_of(group(tend)) : G_NONE;
-        __syncthreads();
-        const int pt = (threadIdx.x == 0) ? prev : (int)s_ty[threadIdx.x - 1];
-        const bool h = valid && (ty == G_LIT || ty != pt);
-        int64_t tot_h, dummy;
-        const int64_t excl_h = block_excl_scan<kXT>((int64_t)h, (int64_t)0, OpSum(), s_red, &tot_h);
-        const int64_t excl_pos = block_excl_scan<kXT>(h ? g : (int64_t)-1, (int64_t)-1, OpMax(), s_red, &dummy);
-        const int64_t start = h ? g : (excl_pos > run_start ? excl_pos : run_start);
-        const int64_t widx = nw + excl_h - (h ? 0 : 1);
-        if (valid) {
-            const int nt = (g + 1 < tend) ? (int)s_ty[threadIdx.x + 1] : s_next;
-            if (ty == G_LIT) out[widx] = __brev(x) >> 1;
-            else if (nt != ty) out[widx] = 0x80000000u | (ty == G_ONE ? 0x40000000u : 0u) | (uint32_t)(g - start + 1);
-            if (g + 1 == tend) { s_carry_type = ty; s_carry_start = start; }
-        }
-        __syncthreads();
-        nw += tot_h;
-        prev = s_carry_type;
-        run_start = s_carry_start;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        int64_t total = nw;
-        if (r > 0) {
-            const int64_t pos = G * 31;
-            const uint32_t y = __funnelshift_r(word_at(pos >> 5), word_at((pos >> 5) + 1), (uint32_t)(pos & 31)) &
-                               ((1u << r) - 1u);
-            out[total++] = __brev(y) >> (32 - r);
-        }
-        s_total = total;
-    }
-    __syncthreads();
-    return s_total;
-}
-
-// Leave the current row: fold the CTA's partial next bits into t -- directly
-// (OR through L2), or, with the compressed row exchange, as a WAH row buffer
-// of t_i & ~pi_i that fold_rows OR-decodes into t.
-__device__ void window_leave(const LevelArgs& a, uint32_t* s_t, const uint32_t* s_pi, int row) {
+// Leave the current row: fold the CTA's partial next bits into t (OR through
+// L2).  With the row exchange the visits record their blocks' partials in HBM
+// instead and the window holds no next bits.
+__device__ void window_leave(const LevelArgs& a, uint32_t* s_t, int row) {
+    if (a.row_exchange) return;
     const int64_t rb = range_begin(a, row);
-    if (a.row_exchange) {
-        __shared__ unsigned long long s_slot;
-        if (threadIdx.x == 0) s_slot = atomicAdd(a.rowbuf_count, 1ull);
-        __syncthreads();
-        const unsigned long long slot = s_slot;
-        if (slot < (unsigned long long)a.rowbuf_slots) {
-            const int64_t nbits = range_begin(a, row + 1) - rb;
-            const int64_t nw = cta_encode_window(s_t, s_pi, a.win_words, nbits, a.rowbuf + (int64_t)slot * a.rowbuf_cap);
-            if (threadIdx.x == 0) {
-                a.rowbuf_row[slot] = row;
-                a.rowbuf_words[slot] = nw;
-            }
-            return;
-        }
-        if (threadIdx.x == 0) atomicOr(a.ctr + C_ERROR, 32ull);    // no slot left (cannot happen by the bound)
-    }
     for (int64_t w = threadIdx.x; w < a.win_words; w += kXT) {
         const uint32_t x = s_t[w];
         if (!x) continue;
@@ -500,7 +457,7 @@ __device__ __forceinline__ void row_affine(const LevelArgs& a, unsigned long lon
             for (; x < xe; ++x) do_unit(row, x);
         }
         __syncthreads();
-        if (WIN) window_leave(a, s_t, s_pi, row);
+        if (WIN) window_leave(a, s_t, row);
         if (threadIdx.x == 0) s_row[0] = pick(row + 1 == p ? 0 : row + 1);
         __syncthreads();
         row = s_row[0];
@@ -583,7 +540,8 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
         const uint32_t items = __shfl_sync(0xffffffffu, cincl, 31);
         nitems += c;
         const BlockView bv = block_view(a, s);
-        const Visitor<WIN, DEDUP> vis{s_pi, s_t, range_begin(a, row)};
+        const Visitor<WIN, DEDUP> vis{s_pi, s_t, range_begin(a, row),
+                                      a.row_exchange ? a.tblk + s * a.dir_stride : nullptr, (uint32_t)jb};
         // items q0 .. q0+31, one per lane: decode, look up the column and
         // prefetch its entries; the next batch's lookups and prefetches are
         // issued before this batch is expanded
@@ -658,7 +616,8 @@ __global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
         if (items == 0) return;
         nitems += cnt;
         const BlockView bv = block_view(a, b);
-        const Visitor<WIN, DEDUP> vis{s_pi, s_t, range_begin(a, row)};
+        const Visitor<WIN, DEDUP> vis{s_pi, s_t, range_begin(a, row),
+                                      a.row_exchange ? a.tblk + b * a.dir_stride : nullptr, (uint32_t)jb};
         auto item = [&](uint32_t q0, int32_t& u, int64_t& begin, uint32_t& len) {
             const uint32_t q = q0 + lane_id();
             const int o = owner_lane(cexcl, q < items ? q : items - 1);
@@ -706,32 +665,144 @@ __global__ void __launch_bounds__(kXT, 1) expand_pieces(LevelArgs a) {
     };
     auto do_unit = [&](int row, int64_t x) {
         const Item it = a.pieces[a.row_piece_base[row] + x];
-        const Visitor<WIN, DEDUP> vis{s_pi, s_t, range_begin(a, row)};
+        const uint32_t j = (uint32_t)it.u / (uint32_t)a.nb;               // the piece's source range
+        const Visitor<WIN, DEDUP> vis{s_pi, s_t, range_begin(a, row),
+                                      a.row_exchange ? a.tblk + ((int64_t)row * a.p + j) * a.dir_stride : nullptr,
+                                      (uint32_t)range_begin(a, j)};
         warp_column<WIN, DEDUP>(a, vis, it.u, it.begin, it.len);
     };
     row_affine<WIN>(a, a.row_piece_next, 1, units_in_row, do_unit, s_pi, s_t, s_row);
 }
 
-// The fold of the compressed row exchange: one CTA per row buffer OR-decodes it
-// into t at its row's first bit.
-__global__ void __launch_bounds__(kXT) fold_rows(LevelArgs a) {
-    __shared__ unsigned long long smu[kXW + 1];
-    __shared__ unsigned long long s_err;
-    const unsigned long long used = *a.rowbuf_count;
-    const unsigned long long nslots = used < (unsigned long long)a.rowbuf_slots ? used : (unsigned long long)a.rowbuf_slots;
-    if (threadIdx.x == 0) s_err = 0ull;
-    __syncthreads();
-    for (unsigned long long slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
-        const int row = a.rowbuf_row[slot];
-        const int64_t rb = range_begin(a, row);
-        const int64_t nbits = range_begin(a, row + 1) - rb;
-        const int64_t nw = a.rowbuf_words[slot];
-        cta_wah_decode_or<uint32_t, kXT>(a.rowbuf + (int64_t)slot * a.rowbuf_cap, nw, nbits, a.t, (uint64_t)rb,
-                                         &s_err, smu);
-        if (threadIdx.x == 0) atomicAdd(a.ctr + C_ROW_WORDS, (unsigned long long)nw);
+// ------------------------------------------------------------------ fold --
+// OR the bits of v (bit q at image bit pos + q; at most 63 bits) into a
+// shared-memory image of bitmap words.
+template <typename W>
+__device__ __forceinline__ void img_or(uint32_t* img, uint32_t pos, W v) {
+    if (!v) return;
+    const uint32_t w = pos >> 5, sh = pos & 31u;
+    if constexpr (sizeof(W) == 4) {
+        atomicOr(img + w, v << sh);
+        if (sh && (v >> (32 - sh))) atomicOr(img + w + 1, v >> (32 - sh));
+    } else {
+        const unsigned long long x = v;
+        const uint32_t w0 = (uint32_t)(x << sh);
+        const uint32_t w1 = sh ? (uint32_t)(x >> (32 - sh)) : (uint32_t)(x >> 32);
+        const uint32_t w2 = sh ? (uint32_t)(x >> (64 - sh)) : 0u;
+        if (w0) atomicOr(img + w, w0);
+        if (w1) atomicOr(img + w + 1, w1);
+        if (w2) atomicOr(img + w + 2, w2);
+    }
+}
+
+// Set the image bits [b0, b1), by the whole warp.
+__device__ __forceinline__ void img_fill(uint32_t* img, uint32_t b0, uint32_t b1) {
+    if (b1 <= b0) return;
+    const uint32_t w0 = b0 >> 5, w1 = (b1 - 1) >> 5;
+    for (uint32_t w = w0 + lane_id(); w <= w1; w += 32) {
+        uint32_t mask = 0xffffffffu;
+        if (w == w0) mask &= 0xffffffffu << (b0 & 31u);
+        if (w == w1) mask &= 0xffffffffu >> (31u - ((b1 - 1) & 31u));
+        atomicOr(img + w, mask);
+    }
+}
+
+constexpr int kFT = 512;            // threads of the fold CTAs
+
+// The fold of the compressed row exchange: t_i is the OR over j of the row
+// buffers (i, j), each the WAH stream of t_{i,j} & ~pi_i.  One CTA per (range
+// i, chunk c of kEncChunkGroups groups of the range): its warps take the p
+// buffers in turn, start at the word the encoder recorded for the chunk and
+// decode the words covering the chunk's groups (and the active word, in the
+// chunk that holds the range's last bits) into a shared-memory image of t's
+// words; the image is then stored, the words shared with a neighbouring chunk
+// or range ORed.  t is clear before the fold and nothing else writes it on a
+// level with the row exchange.  Malformed buffers set C_ERROR (16).
+template <typename W>
+__global__ void __launch_bounds__(kFT) fold_rows(LevelArgs a) {
+    if (a.ctl->bu) return;
+    using T = Wah<W>;
+    constexpr int GB = T::GB;
+    constexpr int64_t CG = kEncChunkGroups;
+    constexpr int64_t CBITS = CG * GB;
+    constexpr int IW = (int)(CBITS / 32) + 2;
+    constexpr int NW = kFT / 32;
+    __shared__ uint32_t img[IW];
+    __shared__ int s_err;
+    const int p = a.p;
+    const int lane = (int)lane_id(), warp = (int)(threadIdx.x >> 5);
+    const int64_t items = (int64_t)p * a.row_bcps;
+    for (int64_t q = blockIdx.x; q < items; q += gridDim.x) {
+        const int i = (int)(q / a.row_bcps);
+        const int64_t c = q - (int64_t)i * a.row_bcps;
+        const int64_t ib = range_begin(a, i), nbits = range_begin(a, i + 1) - ib;
+        const int64_t b0 = c * CBITS;
+        if (b0 >= nbits) continue;
+        const int64_t b1 = (b0 + CBITS < nbits) ? b0 + CBITS : nbits;
+        const int64_t G = nbits / GB;
+        const int r = (int)(nbits - G * GB);
+        const int64_t nch = (G + CG - 1) / CG;
+        const int64_t g_lo = c * CG, g_hi = (g_lo + CG < G) ? g_lo + CG : G;
+        const uint32_t al = (uint32_t)((ib + b0) & 31);
+        const int nimg = (int)((al + (b1 - b0) + 31) >> 5);
+        for (int k = threadIdx.x; k < nimg; k += kFT) img[k] = 0u;
+        if (threadIdx.x == 0) s_err = 0;
+        __syncthreads();
+        for (int j = warp; j < p; j += NW) {
+            const int64_t s = (int64_t)i * p + j;
+            const W* in = static_cast<const W*>(a.rowbuf) + s * a.row_cap;
+            const int64_t count = a.row_count[s];
+            if (c < nch) {
+                int64_t x0 = a.row_first[2 * (s * a.row_cps + c)];
+                int64_t gpos = a.row_first[2 * (s * a.row_cps + c) + 1];
+                while (gpos < g_hi) {
+                    if (x0 >= count) {                         // the words end before the groups do
+                        if (lane == 0) s_err = 1;
+                        break;
+                    }
+                    const int64_t x = x0 + lane;
+                    const W y = (x < count) ? in[x] : W(0);
+                    const unsigned long long len = (x < count) ? (unsigned long long)word_groups<W>(y) : 0ull;
+                    const unsigned long long incl = warp_incl_sum(len);
+                    const int64_t gs = gpos + (int64_t)(incl - len);
+                    bool one = false;
+                    if (x < count && gs < g_hi && gs + (int64_t)len > g_lo) {
+                        if (!is_fill<W>(y)) img_or<W>(img, al + (uint32_t)((gs - g_lo) * GB), T::from_payload(y));
+                        else one = (y & T::VAL) != W(0);
+                    }
+                    uint32_t m = __ballot_sync(0xffffffffu, one);
+                    while (m) {                                 // 1-fills, by the whole warp
+                        const int o = __ffs(m) - 1;
+                        m &= m - 1;
+                        int64_t f0 = __shfl_sync(0xffffffffu, gs, o);
+                        int64_t f1 = f0 + (int64_t)__shfl_sync(0xffffffffu, len, o);
+                        if (f0 < g_lo) f0 = g_lo;
+                        if (f1 > g_hi) f1 = g_hi;
+                        img_fill(img, al + (uint32_t)((f0 - g_lo) * GB), al + (uint32_t)((f1 - g_lo) * GB));
+                    }
+                    x0 += 32;
+                    gpos += (int64_t)__shfl_sync(0xffffffffu, incl, 31);
+                }
+            }
+            // the active word holds the range's last r bits
+            if (r > 0 && lane == 0 && G * GB >= b0 && G * GB < b1) {
+                const W y = (count > 0) ? in[count - 1] : W(0);
+                if (count <= 0 || (y >> r) != W(0)) s_err = 1;
+                else img_or<W>(img, al + (uint32_t)(G * GB - b0), T::from_active(y, r));
+            }
+        }
+        __syncthreads();
+        const int64_t gw0 = (ib + b0) >> 5;
+        for (int k = threadIdx.x; k < nimg; k += kFT) {
+            const uint32_t x = img[k];
+            if (!x) continue;
+            const int64_t wlo = (gw0 + k) * 32;
+            if (wlo >= ib + b0 && wlo + 32 <= ib + b1) a.t[gw0 + k] = x;
+            else atomicOr(a.t + gw0 + k, x);
+        }
+        if (threadIdx.x == 0 && s_err) atomicOr(a.ctr + C_ERROR, 16ull);
         __syncthreads();
     }
-    if (threadIdx.x == 0 && s_err) atomicOr(a.ctr + C_ERROR, 16ull);
 }
 
 // ------------------------------------------------------------- bottom-up --
@@ -1099,12 +1170,13 @@ __global__ void set_root(int32_t* level, int32_t* parent, uint32_t* pi, uint32_t
     fsum[root >> 10] = 1;
 }
 
-// Pack the streams of this exchange into the trace (receive buffer g').
+// Pack the streams of this exchange into a trace (the receive buffer g'):
+// ctr[cursor] is the trace's fill, kept from level to level.
 __global__ void __launch_bounds__(kNT) trace_offsets(const int64_t* __restrict__ counts, int nslots, int u32_per_word,
                                                      int64_t* __restrict__ slot_off, int64_t* __restrict__ trace_counts,
-                                                     unsigned long long* ctr, int64_t capacity) {
+                                                     unsigned long long* ctr, int cursor, int64_t capacity) {
     __shared__ unsigned long long red[kNT / 32 + 1];
-    const unsigned long long used = ctr[C_TRACE_USED];
+    const unsigned long long used = ctr[cursor];
     unsigned long long carry = 0;
     for (int s0 = 0; s0 < nslots; s0 += kNT) {
         const int s = s0 + threadIdx.x;
@@ -1120,22 +1192,23 @@ __global__ void __launch_bounds__(kNT) trace_offsets(const int64_t* __restrict__
     if (threadIdx.x == 0) {
         if (used + carry > (unsigned long long)capacity) {
             ctr[C_ERROR] |= 2ull;                 // trace overflow
-            ctr[C_TRACE_USED] = (unsigned long long)capacity + 1;
+            ctr[cursor] = (unsigned long long)capacity + 1;
         } else {
-            ctr[C_TRACE_USED] = used + carry;
+            ctr[cursor] = used + carry;
         }
     }
 }
 
 __global__ void trace_copy(const uint32_t* __restrict__ xbuf, int64_t slot_cap_u32, const int64_t* __restrict__ counts,
-                           int u32_per_word, const int64_t* __restrict__ slot_off, uint32_t* __restrict__ trace,
-                           int64_t capacity) {
-    const int s = blockIdx.y;
-    const int64_t c = counts[s] * u32_per_word;
-    const int64_t off = slot_off[s];
-    if (off + c > capacity) return;
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < c; x += (int64_t)gridDim.x * blockDim.x)
-        trace[off + x] = xbuf[(int64_t)s * slot_cap_u32 + x];
+                           int nslots, int u32_per_word, const int64_t* __restrict__ slot_off,
+                           uint32_t* __restrict__ trace, int64_t capacity) {
+    for (int s = blockIdx.y; s < nslots; s += gridDim.y) {
+        const int64_t c = counts[s] * u32_per_word;
+        const int64_t off = slot_off[s];
+        if (off + c > capacity) continue;
+        for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < c; x += (int64_t)gridDim.x * blockDim.x)
+            trace[off + x] = xbuf[(int64_t)s * slot_cap_u32 + x];
+    }
 }
 
 int sm_count() {
@@ -1248,7 +1321,8 @@ void free_workspace(bfs_graph* g) {
     W.pi.release(); W.fa.release(); W.fb.release(); W.fsum.release(); W.xbuf.release();
     W.xcount.release(); W.chunk_base.release(); W.units.release(); W.counters.release(); W.pieces.release();
     W.level_scratch.release(); W.row_meta.release();
-    W.rowbuf.release(); W.rowbuf_row.release(); W.rowbuf_words.release();
+    W.tblk.release(); W.rowbuf.release(); W.rowcount.release(); W.rowfirst.release(); W.rowlive.release();
+    W.tblk_dirty = false;
     W.enc_sums.release(); W.enc_bases.release(); W.enc_flags.release(); W.enc_done.release(); W.ctl.release();
     W.gbits.release();
     for (auto& c : W.sgraph) {
@@ -1299,15 +1373,26 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     unsigned long long* ctr = W.counters.as<unsigned long long>();
     const bool win = W.win_words > 0;
     const int xgrid = sm_count();                  // persistent: one 1024-thread CTA per SM
-    const bool rowx = win && g->row_exchange;      // the compressed row exchange needs the row window
-    if (rowx && !W.rowbuf.ptr) {
-        // every CTA leaves every row at most once per kernel: expansion + pieces
-        W.rowbuf_slots = 2LL * xgrid * p;
-        W.rowbuf_cap = L.nb / 31 + 2;
-        BFS_TRY(W.rowbuf.alloc(sizeof(uint32_t) * W.rowbuf_slots * W.rowbuf_cap));
-        BFS_TRY(W.rowbuf_row.alloc(sizeof(int32_t) * W.rowbuf_slots));
-        BFS_TRY(W.rowbuf_words.alloc(sizeof(int64_t) * W.rowbuf_slots));
+    // the compressed row exchange of the fold belongs to DIR-WAH (COMPRESS_SIEVE)
+    const bool rowx = g->row_exchange && mode == BFS_MODE_COMPRESS_SIEVE;
+    if (rowx && !W.tblk.ptr) {
+        // allocated once: captured level loops keep the addresses
+        const int64_t cap32 = L.nb / 31 + 2, cap64 = L.nb / 63 + 2;
+        W.row_cap = cap32;
+        BFS_TRY(W.tblk.alloc(sizeof(uint32_t) * (size_t)(p2 * L.dir_stride)));
+        BFS_TRY(W.rowbuf.alloc((size_t)p2 * std::max<int64_t>(4 * cap32, 8 * cap64)));
+        BFS_TRY(W.rowcount.alloc(sizeof(int64_t) * (size_t)p2));
+        BFS_TRY(W.rowfirst.alloc(sizeof(int64_t) * 2 * (size_t)(p2 * W.enc_cps)));
+        BFS_TRY(W.rowlive.alloc((size_t)p2));
+        BFS_CUDA_TRY(cudaMemsetAsync(W.tblk.ptr, 0, W.tblk.bytes, st));
+        W.tblk_dirty = false;
     }
+    if (rowx && W.tblk_dirty) {          // an earlier search stopped between marking and encoding
+        BFS_CUDA_TRY(cudaMemsetAsync(W.tblk.ptr, 0, W.tblk.bytes, st));
+        W.tblk_dirty = false;
+    }
+    const int64_t row_cap = (wbits == 32) ? L.nb / 31 + 2 : L.nb / 63 + 2;
+    const bool row_tracing = stats && rowx && stats->row_trace_words && stats->row_trace_counts;
     const size_t dyn = win ? window_bytes(W.win_words) : 0;
     // bottom-up levels: degrees (direction choice) and the decoded streams
     const bool bu_kernels = g->direction != BFS_DIRECTION_TOP_DOWN;
@@ -1318,8 +1403,8 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         BFS_TRY(W.gbits.alloc(sizeof(uint32_t) * (size_t)g_words));
     }
     DevBuf slot_off;
-    if (tracing) BFS_TRY(slot_off.alloc(sizeof(int64_t) * nslots));
-    if (stats) { stats->n_levels = 0; stats->trace_used = 0; }
+    if (tracing || row_tracing) BFS_TRY(slot_off.alloc(sizeof(int64_t) * (size_t)std::max<int64_t>(nslots, p2)));
+    if (stats) { stats->n_levels = 0; stats->trace_used = 0; stats->row_trace_used = 0; }
 
     init_search<<<sm_count() * 4, kNT, 0, st>>>(level, parent, L.n, W.pi.as<uint32_t>(), W.fa.as<uint32_t>(),
                                                 W.fb.as<uint32_t>(), W.bm_words, W.fsum.as<uint8_t>(), W.fsum_len);
@@ -1365,12 +1450,13 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     // CTAs take the block-rows in turn, so that only one row's slice of it
     // (and of pi and t) is being updated at a time.
     a.sweep = (!win && 4 * L.n > l2_bytes() / 2) ? 1 : 0;
-    a.rowbuf = W.rowbuf.as<uint32_t>();
-    a.rowbuf_cap = W.rowbuf_cap;
-    a.rowbuf_slots = W.rowbuf_slots;
-    a.rowbuf_count = lvl + 3 * p;
-    a.rowbuf_row = W.rowbuf_row.as<int32_t>();
-    a.rowbuf_words = W.rowbuf_words.as<int64_t>();
+    a.tblk = W.tblk.as<uint32_t>();
+    a.rowbuf = W.rowbuf.ptr;
+    a.row_cap = row_cap;
+    a.row_count = W.rowcount.as<int64_t>();
+    a.row_first = W.rowfirst.as<int64_t>();
+    a.row_cps = W.enc_cps;
+    a.row_bcps = (L.nb + (int64_t)kEncChunkGroups * (wbits - 1) - 1) / ((int64_t)kEncChunkGroups * (wbits - 1));
     a.gbits = W.gbits.as<uint32_t>();
     a.g_words = g_words;
     a.bu_ptr = L.bu_ptr.as<int64_t>();
@@ -1396,6 +1482,31 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     ea.plan_units = ctr + C_UNITS;
     ea.plan_done = W.enc_done.as<unsigned int>();
     ea.frontier_words = W.bm_words;
+    if (rowx) ea.slot_bits = W.rowlive.as<uint8_t>();    // the row encoder skips blocks that expanded nothing
+
+    // the row encoder: slot s = i*p + j is the partial t_{i,j} (the directory
+    // operand, consumed and cleared) sieved by not(pi_i) (the frontier operand
+    // at range i, complemented)
+    EncodeArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.frontier = W.pi.as<uint32_t>();
+    ra.frontier_words = W.bm_words;
+    ra.invert_frontier = 1;
+    ra.dir = W.tblk.as<uint32_t>();
+    ra.dir_clear = W.tblk.as<uint32_t>();
+    ra.dir_stride = L.dir_stride;
+    ra.p = p;
+    ra.nb = L.nb;
+    ra.n = L.n;
+    ra.sieve = 1;
+    ra.row_slots = 1;
+    ra.nslots = (int)p2;
+    ra.out = W.rowbuf.ptr;
+    ra.slot_cap = row_cap;
+    ra.counts = W.rowcount.as<int64_t>();
+    ra.wah_words = ctr + C_ROW_WORDS;
+    ra.chunk_first = W.rowfirst.as<int64_t>();
+    ra.slot_live = W.rowlive.as<uint8_t>();      // t_{i,j} = 0 when stream (i,j) carried no vertex
 
     uint32_t* f = W.fa.as<uint32_t>();       // frontier of the level (reduce_level writes the next one here)
     uint32_t* t = W.fb.as<uint32_t>();       // next bits (cleared by reduce_level)
@@ -1404,6 +1515,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     a.t = t;
     a.ctl = ctl;
     ea.frontier = f;
+    ra.skip = &ctl->bu;                      // bottom-up levels have no row exchange
     const int32_t max_levels = (int32_t)std::min<int64_t>(L.n + 1, INT32_MAX);
     const uint32_t* deg = bu_kernels ? L.deg.as<uint32_t>() : nullptr;
     level_first<<<1, 1, 0, st>>>(ctl, L.n, win ? 1 : 0, g->direction, g->alpha, g->beta, deg, root, L.nnz);
@@ -1440,11 +1552,11 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             if (host && tracing && k < stats->capacity_levels) {
                 const int u32pw = wbits / 32;
                 trace_offsets<<<1, kNT, 0, s>>>(W.xcount.as<int64_t>(), nslots, u32pw, slot_off.as<int64_t>(),
-                                                stats->trace_counts + (int64_t)k * nslots, ctr,
+                                                stats->trace_counts + (int64_t)k * nslots, ctr, C_TRACE_USED,
                                                 stats->trace_capacity);
-                dim3 tg(8, nslots);
-                trace_copy<<<tg, kNT, 0, s>>>(W.xbuf.as<uint32_t>(), slot_cap * u32pw, W.xcount.as<int64_t>(), u32pw,
-                                              slot_off.as<int64_t>(), stats->trace_words, stats->trace_capacity);
+                dim3 tg(8, std::min(nslots, 65535));
+                trace_copy<<<tg, kNT, 0, s>>>(W.xbuf.as<uint32_t>(), slot_cap * u32pw, W.xcount.as<int64_t>(), nslots,
+                                              u32pw, slot_off.as<int64_t>(), stats->trace_words, stats->trace_capacity);
                 BFS_CUDA_TRY(cudaGetLastError());
             }
             if (host && timing) cudaEventRecord(W.ev[2], s);
@@ -1476,11 +1588,34 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             expand_bottom_up<<<sm_count() * 8, kNT, 0, s>>>(a);
             BFS_CUDA_TRY(cudaGetLastError());
         }
-        if (rowx) {
-            fold_rows<<<xgrid, kXT, 0, s>>>(a);
-            BFS_CUDA_TRY(cudaGetLastError());
-        }
         if (host && timing) cudaEventRecord(W.ev[3], s);
+        if (rowx) {
+            // the row exchange: every block's partial, sieved by not(pi_i), WAH-encoded
+            // into its row buffer; the fold OR-decodes the buffers of each block-row into t
+            BFS_TRY(launch_wah_encode_parallel(ra, wbits, W.enc_sums.ptr, W.enc_bases.ptr, W.enc_cps, W.enc_flags.ptr,
+                                               nullptr, sm_count() * 6, s));
+            if (host && timing) cudaEventRecord(W.ev[5], s);
+            if (host && row_tracing && k < stats->capacity_levels) {
+                const int u32pw = wbits / 32;
+                trace_offsets<<<1, kNT, 0, s>>>(W.rowcount.as<int64_t>(), (int)p2, u32pw, slot_off.as<int64_t>(),
+                                                stats->row_trace_counts + (int64_t)k * p2, ctr, C_ROW_TRACE_USED,
+                                                stats->row_trace_capacity);
+                dim3 tg(8, (unsigned)std::min<int64_t>(p2, 65535));
+                trace_copy<<<tg, kNT, 0, s>>>(static_cast<const uint32_t*>(W.rowbuf.ptr), row_cap * u32pw,
+                                              W.rowcount.as<int64_t>(), (int)p2, u32pw, slot_off.as<int64_t>(),
+                                              stats->row_trace_words, stats->row_trace_capacity);
+                BFS_CUDA_TRY(cudaGetLastError());
+            }
+            const int64_t fitems = (int64_t)p * a.row_bcps;
+            const int fgrid = (int)std::min<int64_t>(std::max<int64_t>(fitems, 1), (int64_t)sm_count() * 4);
+            if (wbits == 32) fold_rows<uint32_t><<<fgrid, kFT, 0, s>>>(a);
+            else fold_rows<unsigned long long><<<fgrid, kFT, 0, s>>>(a);
+            BFS_CUDA_TRY(cudaGetLastError());
+            if (host && timing) cudaEventRecord(W.ev[6], s);
+        } else if (host && timing) {
+            cudaEventRecord(W.ev[5], s);
+            cudaEventRecord(W.ev[6], s);
+        }
         reduce_level<<<std::min<int64_t>((W.bm_words + 255) / 256 + 1, sm_count() * 16), kNT, 0, s>>>(
             t, W.pi.as<uint32_t>(), f, W.fsum.as<uint8_t>(), W.bm_words, L.n, level, ctl, ctr, deg);
         BFS_CUDA_TRY(cudaGetLastError());
@@ -1576,17 +1711,20 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             ls.raw_bytes = raw_bytes;
             ls.wah_bytes = (mode == BFS_MODE_PLAIN) ? 0 : (int64_t)h[C_WAH_WORDS] * (wbits / 8);
             ls.edges_scanned = (int64_t)h[C_EDGES];
-            ls.row_wah_bytes = (int64_t)h[C_ROW_WORDS] * 4;
+            ls.row_wah_bytes = (int64_t)h[C_ROW_WORDS] * (wbits / 8);
             ls.bottom_up = h[C_BOTTOM_UP] ? 1 : 0;
             if (timing) {
                 ls.ms_compress_sieve = elapsed(W.ev[0], W.ev[1]);
                 ls.ms_communication = elapsed(W.ev[1], W.ev[2]);
                 ls.ms_traversing = elapsed(W.ev[2], W.ev[3]);
-                ls.ms_reducing = elapsed(W.ev[3], W.ev[4]);
+                ls.ms_row_compress = elapsed(W.ev[3], W.ev[5]);
+                ls.ms_row_fold = elapsed(W.ev[5], W.ev[6]);
+                ls.ms_reducing = elapsed(W.ev[6], W.ev[4]);
             }
         }
         stats->n_levels = k + 1;
         if (tracing) stats->trace_used = (int64_t)h[C_TRACE_USED];
+        if (row_tracing) stats->row_trace_used = (int64_t)h[C_ROW_TRACE_USED];
         frontier = (int64_t)h[C_NEXT_COUNT];
         if (frontier == 0 || k + 1 >= max_levels) break;
     }
@@ -1609,13 +1747,20 @@ extern "C" bfs_status bfs_run(bfs_graph_t g, int32_t root, int32_t* parent, int3
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool dev_p = is_device_pointer(parent), dev_l = is_device_pointer(level);
     if (dev_p != dev_l) return set_error(BFS_ERR_INVALID_ARG, "parent and level must both be host or both be device pointers");
-    if (dev_p) return run_search(g, root, parent, level, stats, st);
+    if (dev_p) {
+        const bfs_status rs = run_search(g, root, parent, level, stats, st);
+        if (rs != BFS_OK) g->W.tblk_dirty = true;     // the row partials may hold a level's marks
+        return rs;
+    }
     Workspace& W = g->W;
     if (!W.tmp_parent.ptr) {
         BFS_TRY(W.tmp_parent.alloc(sizeof(int32_t) * g->L.n));
         BFS_TRY(W.tmp_level.alloc(sizeof(int32_t) * g->L.n));
     }
-    BFS_TRY(run_search(g, root, W.tmp_parent.as<int32_t>(), W.tmp_level.as<int32_t>(), stats, st));
+    {
+        const bfs_status rs = run_search(g, root, W.tmp_parent.as<int32_t>(), W.tmp_level.as<int32_t>(), stats, st);
+        if (rs != BFS_OK) { W.tblk_dirty = true; return rs; }
+    }
     BFS_CUDA_TRY(cudaMemcpyAsync(parent, W.tmp_parent.ptr, sizeof(int32_t) * g->L.n, cudaMemcpyDeviceToHost, st));
     BFS_CUDA_TRY(cudaMemcpyAsync(level, W.tmp_level.ptr, sizeof(int32_t) * g->L.n, cudaMemcpyDeviceToHost, st));
     BFS_CUDA_TRY(cudaStreamSynchronize(st));

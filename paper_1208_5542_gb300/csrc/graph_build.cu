@@ -562,7 +562,7 @@ void bfs_options_default(bfs_options* opt) {
     opt->wah_word_bits = 32;
     opt->autotune = 0;
     opt->debug_checks = 0;
-    opt->row_exchange = 0;
+    opt->row_exchange = 1;
 }
 
 const char* bfs_status_string(bfs_status s) {
@@ -661,8 +661,8 @@ bfs_status bfs_graph_footprint(bfs_graph_t g, int64_t* bytes) {
                           L.deg.bytes + L.bu_ptr.bytes + L.bu_adj.bytes);
     b += (int64_t)(W.pi.bytes + W.fa.bytes + W.fb.bytes + W.fsum.bytes + W.xbuf.bytes + W.xcount.bytes +
                    W.chunk_base.bytes + W.units.bytes + W.counters.bytes + W.tmp_parent.bytes + W.tmp_level.bytes +
-                   W.pieces.bytes + W.level_scratch.bytes + W.row_meta.bytes + W.rowbuf.bytes + W.rowbuf_row.bytes +
-                   W.rowbuf_words.bytes + W.enc_sums.bytes + W.enc_bases.bytes + W.enc_flags.bytes +
+                   W.pieces.bytes + W.level_scratch.bytes + W.row_meta.bytes + W.tblk.bytes + W.rowbuf.bytes +
+                   W.rowcount.bytes + W.rowfirst.bytes + W.rowlive.bytes + W.enc_sums.bytes + W.enc_bases.bytes + W.enc_flags.bytes +
                    W.enc_done.bytes + W.gbits.bytes);
     *bytes = b;
     return BFS_OK;

@@ -88,6 +88,7 @@ enum Counter : int {
     C_EDGES,             // adjacency entries scanned
     C_ERROR,             // nonzero: an invariant failed (code)
     C_TRACE_USED,        // uint32 elements of the trace written so far
+    C_ROW_TRACE_USED,    // uint32 elements of the row-buffer trace written so far
     C_WAH_WORDS,         // words of all streams of this level
     C_EXCHANGED,         // set bits carried by the exchange
     C_PIECES,            // pieces of long columns queued for the piece kernel
@@ -122,7 +123,10 @@ struct Workspace {
     DevBuf row_meta;            // per-row piece bases and capacities
     int64_t piece_cap = 0;      // capacity of `pieces` (Item entries)
     int64_t win_words = 0;      // shared-memory row window of the expansion (0: none)
-    DevBuf rowbuf, rowbuf_row, rowbuf_words;   // compressed row exchange
+    DevBuf tblk;                // row exchange: per-block partial next bitmaps t_{i,j} (dir layout)
+    DevBuf rowbuf, rowcount, rowfirst;   // row exchange: row buffers, their word counts, chunk index
+    DevBuf rowlive;             // row exchange: 1 for a block whose column stream carried a vertex
+    bool tblk_dirty = false;    // a search stopped mid-level: clear the partials before the next one
     DevBuf enc_sums, enc_bases;  // chunk summaries of the parallel encoder
     DevBuf enc_flags;            // chunks with frontier bits
     DevBuf enc_done;             // slots finished by the encoder's scan
@@ -131,7 +135,7 @@ struct Workspace {
     SearchGraph sgraph[2];       // level loops as CUDA graphs, most recent configurations
     int sgraph_next = 0;
     int64_t enc_cps = 0;         // encoder chunks per slot
-    int64_t rowbuf_cap = 0, rowbuf_slots = 0;
+    int64_t row_cap = 0;        // words (of the WAH width) per row buffer
     DevBuf tmp_parent, tmp_level;      // for searches with host outputs
     uint64_t* h_counters = nullptr;    // pinned mirror of the counters
     cudaEvent_t ev[8] = {};
@@ -188,6 +192,17 @@ struct EncodeArgs {
     int64_t* plan_base;         // or nullptr: the decoder's units per block, p*p + 1 entries
     unsigned long long* plan_units;  // their total
     unsigned int* plan_done;    // slots finished (zero between uses)
+    // the row exchange of the fold (slot s = i*p + j carries range i, not j):
+    int row_slots;              // 1: slot s covers range s / p; the bitmap read at its range is
+                                //    `frontier`, combined as ~frontier & dir (with invert_frontier)
+    int invert_frontier;        // 1: the frontier operand enters complemented (the sieve by not(pi))
+    uint32_t* dir_clear;        // or nullptr: the directory operand, zeroed as the passes consume it
+    int64_t* chunk_first;       // or nullptr: per (slot, chunk) the word holding the chunk's first
+                                //   group and that word's first group, 2 entries
+    const int32_t* skip;        // or nullptr: the passes do nothing while *skip != 0 (the counts
+                                //   are set to 0)
+    uint8_t* slot_bits;         // or nullptr: the scan writes 1 for a slot whose stream carries a set bit
+    const uint8_t* slot_live;   // or nullptr: a slot with slot_live[s] == 0 is all zero (not read)
 };
 bfs_status launch_wah_encode(const EncodeArgs& a, int wah_bits, cudaStream_t st);
 

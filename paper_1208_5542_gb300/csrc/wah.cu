@@ -25,6 +25,7 @@ namespace {
 constexpr int kNT = 256;          // threads per encoder CTA
 constexpr int kK = 4;             // groups per thread per tile
 constexpr int kTile = kNT * kK;   // groups per tile
+static_assert(kTile == kEncChunkGroups, "the encoder's chunk is the unit of its chunk index");
 
 struct SlotGeom {
     int64_t src0;      // first bitmap bit of the slot's source range
@@ -33,7 +34,8 @@ struct SlotGeom {
 };
 
 __device__ __forceinline__ SlotGeom slot_geom(const EncodeArgs& a, int s) {
-    const int j = a.sieve ? (int)((uint32_t)s % (uint32_t)a.p) : s;
+    const int j = a.sieve ? (a.row_slots ? (int)((uint32_t)s / (uint32_t)a.p) : (int)((uint32_t)s % (uint32_t)a.p))
+                          : s;
     int64_t b0 = (int64_t)j * a.nb, b1 = b0 + a.nb;
     if (b0 > a.n) b0 = a.n;
     if (b1 > a.n) b1 = a.n;
@@ -192,7 +194,12 @@ __global__ void __launch_bounds__(kNT) wah_encode_kernel(EncodeArgs a, unsigned 
         if (r > 0) {
             const uint64_t pos = (uint64_t)(sg.src0 + G * GB);
             W y = T::tail(a.frontier, pos, r);
+            if (a.invert_frontier) y = ~y & (W)((W(1) << r) - W(1));
             if (sg.dirb && y) y &= T::tail(sg.dirb, (uint64_t)(G * GB), r);
+            if (a.dir_clear) {              // the tail words no chunk of the write pass owns
+                uint32_t* d = a.dir_clear + (int64_t)s * a.dir_stride;
+                for (int64_t w = (G * GB + 31) >> 5; w < (sg.nbits + 31) >> 5; ++w) d[w] = 0u;
+            }
             if (setbits && y) atomicAdd(setbits, (unsigned long long)T::popc(y));
             out[total++] = T::to_active(y, r);
         }
@@ -238,6 +245,7 @@ struct Stage32 {
     const uint32_t* f;     // frontier words from a 16-byte boundary at or before group tb
     const uint32_t* d;     // directory words from group tb (or nullptr: no sieve)
     uint32_t off;          // bit of group tb in f
+    uint32_t fx;           // xor mask of the frontier operand (all ones: complemented)
     int64_t tb;
 };
 
@@ -253,6 +261,7 @@ __device__ __forceinline__ Stage32 stage_chunk(const EncodeArgs& a, const SlotGe
     Stage32 st;
     st.f = fbuf;
     st.off = (uint32_t)(fbit0 - 32 * fw0);
+    st.fx = a.invert_frontier ? 0xffffffffu : 0u;
     st.tb = tb;
     st.d = nullptr;
     if (sg.dirb) {
@@ -282,6 +291,15 @@ struct ChunkBase {
 };
 
 
+// The write pass is the last reader of a chunk's directory words: zero the
+// nonzero ones among the words [w0, w1) that hold its groups (the staged copy
+// d starts at word w0), so that the operand is clear for its next use.
+__device__ __forceinline__ void clear_consumed(const EncodeArgs& a, int s, int64_t w0, int64_t w1, const uint32_t* d) {
+    uint32_t* dst = a.dir_clear + (int64_t)s * a.dir_stride;
+    for (int64_t k = lane_id(); k < w1 - w0; k += 32)
+        if (d[k]) dst[w0 + k] = 0u;
+}
+
 // One warp per slot (blockDim.x = 32).
 template <typename W>
 __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t* flags, ChunkBase* bases,
@@ -289,6 +307,10 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
     using T = Wah<W>;
     constexpr int GB = T::GB;
     const int s = blockIdx.x;
+    if (a.skip && *a.skip) {                // a level without this exchange: empty streams
+        if (lane_id() == 0) a.counts[s] = 0;
+        return;
+    }
     const SlotGeom sg = slot_geom(a, s);
     const int64_t G = sg.nbits / GB;
     const int r = (int)(sg.nbits % GB);
@@ -323,11 +345,14 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
     const int64_t K = (nch + 31) / 32;
     const int64_t c_lo = (int64_t)lane * K, c_hi = (c_lo + K < nch) ? c_lo + K : nch;
     Agg mine{0, -1, -1, -1};
+    bool bits = false;                                  // a chunk of the lane holds a set bit
     for (int64_t c = c_lo; c < c_hi; ++c) {
         const ChunkSum cs = sum_of(c);
         Agg one{(int64_t)cs.heads, cs.last_head, (int)(cs.types & 0xff), (int)((cs.types >> 8) & 0xff)};
         mine = combine(mine, one);
+        bits |= !(cs.heads == 1 && (cs.types & 0xff) == G_ZERO);   // not one zero run
     }
+    bits = __any_sync(0xffffffffu, bits);
     Agg incl = mine;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -359,6 +384,10 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
         const int nxt = (c + 1 < nch) ? (int)(sum_of(c + 1).types & 0xff) : G_NONE;
         cb.next_type = nxt;
         bases[(int64_t)s * cps + c] = cb;
+        if (a.chunk_first) {                // where a decoder of this chunk alone starts
+            a.chunk_first[2 * ((int64_t)s * cps + c)] = merge ? cb.words - 1 : cb.words;
+            a.chunk_first[2 * ((int64_t)s * cps + c) + 1] = merge ? cb.run_start : c * kTile;
+        }
         if (!flags[(int64_t)s * cps + c]) {
             // an all-zero chunk: its zero run opens a word here unless it merges
             if (!merge && ub && (cb.words & 31) == 0) ub[cb.words >> 5] = c * kTile;
@@ -378,12 +407,19 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
         if (r > 0) {
             const uint64_t pos = (uint64_t)(sg.src0 + G * GB);
             W y = T::tail(a.frontier, pos, r);
+            if (a.invert_frontier) y = ~y & (W)((W(1) << r) - W(1));
             if (sg.dirb && y) y &= T::tail(sg.dirb, (uint64_t)(G * GB), r);
+            if (a.dir_clear) {              // the tail words no chunk of the write pass owns
+                uint32_t* d = a.dir_clear + (int64_t)s * a.dir_stride;
+                for (int64_t w = (G * GB + 31) >> 5; w < (sg.nbits + 31) >> 5; ++w) d[w] = 0u;
+            }
             if (setbits && y) atomicAdd(setbits, (unsigned long long)T::popc(y));
             if (ub && (total & 31) == 0) ub[total >> 5] = G;
             out[total++] = T::to_active(y, r);
+            bits |= y != W(0);
         }
         a.counts[s] = total;
+        if (a.slot_bits) a.slot_bits[s] = bits ? 1 : 0;
         if (a.wah_words) atomicAdd(a.wah_words, (unsigned long long)total);
     }
     if (!a.plan_base) return;
@@ -441,7 +477,7 @@ __device__ __forceinline__ void lane_cwords(const Stage32& st, uint32_t (&c)[32]
     if (st.d) {
         const uint32_t* d = st.d + 31 * lane;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) c[k] = __funnelshift_r(f[k], f[k + 1], sh) & d[k];
+        for (int k = 0; k < 32; ++k) c[k] = (__funnelshift_r(f[k], f[k + 1], sh) ^ st.fx) & d[k];
     } else {
 #pragma unroll
         for (int k = 0; k < 32; ++k) c[k] = __funnelshift_r(f[k], f[k + 1], sh);
@@ -477,6 +513,7 @@ __device__ __forceinline__ int mask_type(uint32_t zm, uint32_t om, int i) {
 
 __global__ void __launch_bounds__(kEW) enc_chunk_sums32(EncodeArgs a, ChunkSum* sums, uint8_t* flags, int64_t cps,
                                                         unsigned long long* setbits) {
+    if (a.skip && *a.skip) return;
     __shared__ __align__(16) uint32_t s_f[kEW / 32][kStageWords];
     __shared__ __align__(16) uint32_t s_d[kEW / 32][kStageWords];
     const int64_t n = (int64_t)a.nslots * cps;
@@ -492,7 +529,7 @@ __global__ void __launch_bounds__(kEW) enc_chunk_sums32(EncodeArgs a, ChunkSum* 
         const int64_t tb = c * kTile;
         bool live = false;
         int64_t tend = tb;
-        if (tb < G) {
+        if (tb < G && !(a.slot_live && !a.slot_live[s])) {
             tend = (tb + kTile < G) ? tb + kTile : G;
             bool nz = true;
             if (a.fsum) {
@@ -572,6 +609,7 @@ __global__ void __launch_bounds__(kEW) enc_chunk_write32(EncodeArgs a, const Chu
     __shared__ __align__(16) uint32_t s_f[kEW / 32][kStageWords];
     __shared__ __align__(16) uint32_t s_d[kEW / 32][kStageWords];
     static_assert(kOutWords + kOutWords / 32 + 1 <= kStageWords, "output words overflow the frontier buffer");
+    if (a.skip && *a.skip) return;
     const int64_t n = (int64_t)a.nslots * cps;
     const int lane = (int)lane_id();
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -592,6 +630,7 @@ __global__ void __launch_bounds__(kEW) enc_chunk_write32(EncodeArgs a, const Chu
         const int ng = (int)(tend - tb);
         uint32_t cwd[32];
         lane_cwords(st, cwd);
+        if (a.dir_clear) clear_consumed(a, s, (31 * tb) >> 5, (31 * tend + 31) >> 5, st.d);
         __syncwarp();           // the frontier buffer now takes the output words
         uint32_t zm, om, vm;
         lane_masks(cwd, ng, zm, om, vm);
@@ -684,6 +723,7 @@ __device__ __forceinline__ Stage32 stage_chunk63(const EncodeArgs& a, const Slot
     Stage32 st;
     st.f = fbuf;
     st.off = (uint32_t)(fbit0 - 32 * fw0);
+    st.fx = a.invert_frontier ? 0xffffffffu : 0u;
     st.tb = tb;
     st.d = nullptr;
     if (sg.dirb) {
@@ -709,7 +749,7 @@ __device__ __forceinline__ void half_cwords63(const Stage32& st, int h, uint32_t
     if (st.d) {
         const uint32_t* d = st.d + w0;
 #pragma unroll
-        for (int k = 0; k < 33; ++k) c[k] = __funnelshift_r(f[k], f[k + 1], sh) & d[k];
+        for (int k = 0; k < 33; ++k) c[k] = (__funnelshift_r(f[k], f[k + 1], sh) ^ st.fx) & d[k];
     } else {
 #pragma unroll
         for (int k = 0; k < 33; ++k) c[k] = __funnelshift_r(f[k], f[k + 1], sh);
@@ -746,6 +786,7 @@ __device__ __forceinline__ void lane_masks63(const uint32_t (&c0)[33], const uin
 
 __global__ void __launch_bounds__(kEW64) enc_chunk_sums64(EncodeArgs a, ChunkSum* sums, uint8_t* flags, int64_t cps,
                                                           unsigned long long* setbits) {
+    if (a.skip && *a.skip) return;
     __shared__ __align__(16) uint32_t s_f[kEW64 / 32][kStage64];
     __shared__ __align__(16) uint32_t s_d[kEW64 / 32][kStage64];
     const int64_t n = (int64_t)a.nslots * cps;
@@ -761,7 +802,7 @@ __global__ void __launch_bounds__(kEW64) enc_chunk_sums64(EncodeArgs a, ChunkSum
         const int64_t tb = c * kTile;
         bool live = false;
         int64_t tend = tb;
-        if (tb < G) {
+        if (tb < G && !(a.slot_live && !a.slot_live[s])) {
             tend = (tb + kTile < G) ? tb + kTile : G;
             bool nz = true;
             if (a.fsum) {
@@ -817,6 +858,7 @@ __global__ void __launch_bounds__(kEW64) enc_chunk_write64(EncodeArgs a, const C
     __shared__ __align__(16) uint32_t s_f[kEW64 / 32][kStage64];
     __shared__ __align__(16) uint32_t s_d[kEW64 / 32][kStage64];
     static_assert(2 * (kOutWords + kOutWords / 32 + 1) <= kStage64, "output words overflow the frontier buffer");
+    if (a.skip && *a.skip) return;
     const int64_t n = (int64_t)a.nslots * cps;
     const int lane = (int)lane_id();
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -838,6 +880,7 @@ __global__ void __launch_bounds__(kEW64) enc_chunk_write64(EncodeArgs a, const C
         uint32_t c0[33], c1[33];
         half_cwords63(st, 0, c0);
         half_cwords63(st, 1, c1);
+        if (a.dir_clear) clear_consumed(a, s, (63 * tb) >> 5, (63 * tend + 31) >> 5, st.d);
         uint32_t zm, om, vm;
         lane_masks63(c0, c1, ng, zm, om, vm, nullptr);
         const int r0 = 32 * lane;

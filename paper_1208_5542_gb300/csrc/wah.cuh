@@ -16,6 +16,10 @@ namespace bfsgb {
 
 enum GroupType : int { G_ZERO = 0, G_ONE = 1, G_LIT = 2, G_NONE = 3 };
 
+// Groups per chunk of the data-parallel encoder (its unit of work, and the
+// unit of the chunk index it records for decoders of one chunk).
+constexpr int kEncChunkGroups = 1024;
+
 // Position of the set bit of rank k in x (k = 0 is the lowest set bit),
 // by halving on popcounts; k must be < popc(x).
 __device__ __forceinline__ int select32(uint32_t v, int k) {

@@ -43,7 +43,8 @@ class LevelStats(ctypes.Structure):
                 ("raw_bytes", i64), ("wah_bytes", i64), ("edges_scanned", i64), ("row_wah_bytes", i64),
                 ("ms_compress_sieve", ctypes.c_float), ("ms_communication", ctypes.c_float),
                 ("ms_traversing", ctypes.c_float), ("ms_reducing", ctypes.c_float),
-                ("bottom_up", i32), ("reserved", i32)]
+                ("bottom_up", i32), ("ms_row_compress", ctypes.c_float), ("ms_row_fold", ctypes.c_float),
+                ("reserved", i32)]
 
 
 class BatchStats(ctypes.Structure):
@@ -59,7 +60,8 @@ class ServerStats(ctypes.Structure):
 class RunStats(ctypes.Structure):
     _fields_ = [("capacity_levels", i32), ("n_levels", i32), ("timing", i32), ("reserved", i32),
                 ("levels", P(LevelStats)), ("trace_words", vp), ("trace_capacity", i64),
-                ("trace_counts", vp), ("trace_used", i64)]
+                ("trace_counts", vp), ("trace_used", i64), ("row_trace_words", vp), ("row_trace_capacity", i64),
+                ("row_trace_counts", vp), ("row_trace_used", i64)]
 
 
 _SIGS = {

@@ -23,3 +23,35 @@ def test_status_strings_and_defaults_without_gpu():
     o = native.Options()
     lib.bfs_options_default(ctypes.byref(o))
     assert (o.grid_r, o.grid_c, o.mode, o.wah_word_bits) == (1, 1, 2, 32)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the size and field offsets
+    that a C compiler gives the header's structures."""
+    import os
+    import subprocess
+
+    structs = {"bfs_options": native.Options, "bfs_graph_info_t": native.GraphInfo,
+               "bfs_level_stats": native.LevelStats, "bfs_run_stats": native.RunStats,
+               "bfs_batch_stats": native.BatchStats, "bfs_server_stats_t": native.ServerStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "bfs_gb300.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(native.PKG), "include")
+    subprocess.check_call(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {}
+    for line in out:
+        if line:
+            c, f, v = line.split()
+            got[(c, f)] = int(v)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)

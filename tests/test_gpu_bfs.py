@@ -5,7 +5,7 @@ import torch
 
 import graphgen
 import oracle
-from tests.golden_io import bfs_example
+from tests.golden_io import bfs_example, row_buffer_example
 
 pytestmark = pytest.mark.gpu
 
@@ -26,10 +26,15 @@ def _run(g, root, **kw):
     return parent.cpu().numpy(), level.cpu().numpy(), st
 
 
-def _unpack_trace(st, wah_bits):
-    """GPU trace -> list (per exchange) of lists (per slot) of word values."""
-    words = st.trace_words[: st.trace_used].cpu().numpy().view(np.uint32)
-    counts = st.trace_counts.cpu().numpy()
+def _unpack_trace(st, wah_bits, rows=False):
+    """GPU trace (column streams, or the row buffers of the fold with ``rows``) ->
+    list (per exchange) of lists (per slot) of word values."""
+    if rows:
+        words = st.row_trace_words[: st.row_trace_used].cpu().numpy().view(np.uint32)
+        counts = st.row_trace_counts.cpu().numpy()
+    else:
+        words = st.trace_words[: st.trace_used].cpu().numpy().view(np.uint32)
+        counts = st.trace_counts.cpu().numpy()
     per = wah_bits // 32
     out, off = [], 0
     for k in range(counts.shape[0]):
@@ -60,13 +65,22 @@ def test_paper_example(mode, p, wah):
     bfs = _lib()
     d = bfs_example()
     g = bfs.Graph.from_edges(d["n"], d["src"], d["dst"], p=p, mode=mode, wah_bits=wah)
-    parent, level, st = _run(g, d["root"], stats=True, trace_capacity=4096)
+    parent, level, st = _run(g, d["root"], stats=True, trace_capacity=4096, row_trace_capacity=4096)
     assert level.tolist() == d["levels"]
     assert parent.tolist() == d["parents_min"]
     if mode:
         go = oracle.csr(d["n"], d["src"], d["dst"])
         _, _, tr = oracle.dist_bfs(go, p, d["root"], mode=ORACLE_MODE[mode], w=wah, trace=True)
         _check_trace(_unpack_trace(st, wah), tr)
+    if mode == 2:
+        # the row buffers of the fold: the hand-derived words of the fixture (p = 1, 2)
+        # and the oracle's (every p)
+        _, _, _, rows = oracle.dist_bfs(go, p, d["root"], mode=oracle.COMPRESS_SIEVE, w=wah, rows=True)
+        got = _unpack_trace(st, wah, rows=True)
+        _check_trace(got, rows)
+        want = row_buffer_example().get(p)
+        if want is not None:
+            assert [[[int(x) for x in sl] for sl in lvl] for lvl in got] == [[[x] for x in lvl] for lvl in want]
 
 
 def test_directories_match_eq4():
@@ -105,14 +119,21 @@ def test_kronecker_traces_bit_exact(mode, p, wah):
     go = oracle.csr(n, src, dst)
     g = bfs.Graph.from_edges(n, src, dst, p=p, mode=mode, wah_bits=wah)
     for r in graphgen.pick_roots(n, src, dst, 3):
-        lv, pa, tr = oracle.dist_bfs(go, p, int(r), mode=ORACLE_MODE[mode], w=wah, trace=True)
-        parent, level, st = _run(g, int(r), stats=True, trace_capacity=1 << 22)
+        if mode == 2:
+            lv, pa, tr, rows = oracle.dist_bfs(go, p, int(r), mode=oracle.COMPRESS_SIEVE, w=wah, trace=True,
+                                               rows=True)
+        else:
+            lv, pa, tr = oracle.dist_bfs(go, p, int(r), mode=ORACLE_MODE[mode], w=wah, trace=True)
+        parent, level, st = _run(g, int(r), stats=True, trace_capacity=1 << 22, row_trace_capacity=1 << 22)
         assert (level == lv).all() and (parent == pa).all()
         _check_trace(_unpack_trace(st, wah), tr)
+        if mode == 2:
+            _check_trace(_unpack_trace(st, wah, rows=True), rows)
         # per-level statistics agree with the oracle's streams
         for k, ls in enumerate(st.levels):
             assert ls["frontier_vertices"] == int((lv == k).sum())
             assert ls["wah_bytes"] == sum(len(x) for x in tr[k]) * wah // 8
+            assert ls["row_wah_bytes"] == (sum(len(x) for x in rows[k]) * wah // 8 if mode == 2 else 0)
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
@@ -281,32 +302,62 @@ def test_sieved_away_chunk_inside_a_zero_run():
         assert (level == lv).all() and (parent == pa).all()
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
-@pytest.mark.parametrize("scale,p", [(14, 4), (16, 8), (13, 7)])
-def test_compressed_row_exchange_never_changes_the_result(mode, scale, p):
-    """With the row exchange on, every CTA's partial next bitmap of a block-row
-    (sieved by not(pi)) travels as a WAH row buffer and the row is folded by
-    OR-decoding them; levels and parents stay those of the oracle."""
+@pytest.mark.parametrize("scale,p,wah", [(14, 4, 32), (13, 7, 64), (16, 2, 32), (21, 2, 32)])
+def test_row_buffers_bit_exact(scale, p, wah):
+    """COMPRESS_SIEVE with the row exchange of the fold (the default): every row
+    buffer -- the WAH stream of what block (i,j) reached, sieved by not(pi_i) --
+    word for word the oracle's, on ragged ranges (p = 7), 64-bit words, the
+    shared-memory row window (scale 16) and the global visiting path (scale 21:
+    ranges of 1M vertices); with the row exchange off the search is the same
+    and carries no row buffers."""
     bfs = _lib()
-    n, src, dst = graphgen.edges(scale, 16)
+    n, src, dst = graphgen.edges(scale, 16 if scale < 20 else 8)
     go = oracle.csr(n, src, dst)
-    g = bfs.Graph.from_edges(n, src, dst, p=p, mode=mode)
-    g.set_row_exchange(True)
-    for r in graphgen.pick_roots(n, src, dst, 3):
-        lv, pa = oracle.bfs(go, int(r))
-        parent, level, st = _run(g, int(r), stats=True)
+    g = bfs.Graph.from_edges(n, src, dst, p=p, mode=2, wah_bits=wah)
+    cap = 1 << 24
+    for r in graphgen.pick_roots(n, src, dst, 2):
+        lv, pa, tr, rows = oracle.dist_bfs(go, p, int(r), mode=oracle.COMPRESS_SIEVE, w=wah, trace=True,
+                                           rows=True, max_levels=64, trace_cap=cap)
+        parent, level, st = _run(g, int(r), stats=True, trace_capacity=2 * cap, row_trace_capacity=2 * cap)
         assert (level == lv).all() and (parent == pa).all()
-        assert sum(ls["row_wah_bytes"] for ls in st.levels) > 0
+        _check_trace(_unpack_trace(st, wah), tr)
+        _check_trace(_unpack_trace(st, wah, rows=True), rows)
+        parent, level, _ = _run(g, int(r))             # the graph-launched level loop
+        assert (level == lv).all() and (parent == pa).all()
     g.set_row_exchange(False)
     parent, level, st = _run(g, int(r), stats=True)
     assert (level == lv).all() and (parent == pa).all()
     assert sum(ls["row_wah_bytes"] for ls in st.levels) == 0
 
 
+def test_row_buffers_bench_launch_configuration_scale24():
+    """Kronecker scale 24 on the 16 x 16 grid: the parent array exceeds half of
+    L2 and the ranges (1M vertices) exceed the row window, so the expansion
+    sweeps the block-rows in turn on its global visiting path -- the bench's
+    launch configuration at scale 26.  Every row buffer of one search
+    bit-exact with the oracle's."""
+    bfs = _lib()
+    n, src, dst = graphgen.edges(24, 16)
+    p = 16
+    g = bfs.Graph.from_edges(n, src, dst, p=p, mode=2)
+    r = int(graphgen.pick_roots(n, src, dst, 1)[0])
+    cap = 1 << 26
+    parent, level, st = _run(g, r, stats=True, row_trace_capacity=cap)
+    rows_gpu = _unpack_trace(st, 32, rows=True)
+    del g
+    torch.cuda.empty_cache()
+    go = oracle.csr(n, src, dst)
+    del src, dst
+    lv, pa, _, rows = oracle.dist_bfs(go, p, r, mode=oracle.COMPRESS_SIEVE, rows=True, max_levels=64,
+                                      trace_cap=cap)
+    assert (level == lv).all() and (parent == pa).all()
+    _check_trace(rows_gpu, rows)
+
+
 def test_scale22_grid8_64bit_words_streams_bit_exact():
     """The scale-22 configuration: Kronecker scale 22, 8x8 grid, COMPRESS_SIEVE
     with 64-bit WAH words.  Levels and parents of two roots, and every exchanged
-    stream of the first, bit-exact with the oracle's Alg. 3."""
+    stream and row buffer of the first, bit-exact with the oracle's Alg. 3."""
     bfs = _lib()
     n, src, dst = graphgen.edges(22, 16)
     go = oracle.csr(n, src, dst)
@@ -314,11 +365,12 @@ def test_scale22_grid8_64bit_words_streams_bit_exact():
     g = bfs.Graph.from_edges(n, src, dst, p=p, mode=2, wah_bits=wah)
     roots = graphgen.pick_roots(n, src, dst, 2)
     cap = 32 * (2 * p * p + n * p // (wah - 1) + 8)
-    lv, pa, tr = oracle.dist_bfs(go, p, int(roots[0]), mode=oracle.COMPRESS_SIEVE, w=wah, trace=True,
-                                 max_levels=32, trace_cap=cap)
-    parent, level, st = _run(g, int(roots[0]), stats=True, trace_capacity=cap * 2)
+    lv, pa, tr, rows = oracle.dist_bfs(go, p, int(roots[0]), mode=oracle.COMPRESS_SIEVE, w=wah, trace=True,
+                                       max_levels=32, trace_cap=cap, rows=True)
+    parent, level, st = _run(g, int(roots[0]), stats=True, trace_capacity=cap * 2, row_trace_capacity=cap * 2)
     assert (level == lv).all() and (parent == pa).all()
     _check_trace(_unpack_trace(st, wah), tr)
+    _check_trace(_unpack_trace(st, wah, rows=True), rows)
     lv, pa = oracle.bfs(go, int(roots[1]))
     parent, level, _ = _run(g, int(roots[1]))
     assert (level == lv).all() and (parent == pa).all()
