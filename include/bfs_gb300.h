@@ -74,9 +74,13 @@ typedef struct {
     int32_t grid_c;          /* virtual grid columns; must equal grid_r (square grid, Eq. 1-2) */
     int32_t mode;            /* BFS_MODE_* */
     int32_t wah_word_bits;   /* 32 (31-bit groups, Table 3) or 64 (63-bit groups) */
-    int32_t autotune;        /* reserved, 0 */
-    int32_t debug_checks;    /* 1: kernels verify internal invariants and report
-                                BFS_ERR_CORRUPT instead of continuing */
+    int32_t autotune;        /* 1: the first bfs_run_batch on the graph runs bfs_batch_autotune
+                                on its own roots and keeps the fastest launch shape */
+    int32_t debug_checks;    /* 1: bfs_run checks its outputs before returning (bfs_check_search,
+                                plus: the reached vertices are those the search visited) and
+                                reports BFS_ERR_CORRUPT.  The device-side bounds and stream checks
+                                of the kernels (a sieved vertex without a column, a malformed
+                                row buffer, a full piece list) run in every mode. */
     int32_t row_exchange;    /* 1: compressed row exchange of the fold in COMPRESS_SIEVE mode
                                 (see bfs_graph_set_row_exchange) */
 } bfs_options;
@@ -240,6 +244,9 @@ typedef struct {
     float ms_row_compress;       /* row exchange: sieve by not(pi) + compress of the partials */
     float ms_row_fold;           /* row exchange: decompress + OR of the row buffers (the fold) */
     int32_t reserved;
+    int64_t compress_chunks;     /* chunks of 1024 groups the column sieve + compress read (each:
+                                    the chunk's frontier and directory bits) */
+    int64_t row_compress_chunks; /* chunks the row sieve + compress read (partial and visited bits) */
 } bfs_level_stats;
 
 typedef struct {
@@ -287,6 +294,19 @@ typedef struct {
 BFS_API bfs_status bfs_run(bfs_graph_t g, int32_t root, int32_t *parent, int32_t *level,
                    bfs_run_stats *stats, void *cuda_stream);
 
+/*
+ * Check the outputs of a search from `root` (the definition of level[] and
+ * parent[] in Sec. II and the output specification of Alg. 1): level[root] = 0
+ * and parent[root] = root; an unreached vertex has level -1 and parent -1; a
+ * reached vertex v != root has level > 0 and a parent in [0, n) whose level is
+ * level[v] - 1.  (Whether parent -> v is an entry of the graph is not checked.)
+ * parent/level: device, length n.  Synchronises `cuda_stream`.  Allocates a
+ * few bytes of scratch.  Errors: BFS_ERR_CORRUPT with the number of failing
+ * vertices and the smallest one in bfs_last_error(); BFS_ERR_INVALID_ARG.
+ */
+BFS_API bfs_status bfs_check_search(bfs_graph_t g, int32_t root, const int32_t *parent, const int32_t *level,
+                                    void *cuda_stream);
+
 /* Counters of one batched search. */
 typedef struct {
     int32_t n_levels;            /* levels performed (the deepest search's depth + 1) */
@@ -333,11 +353,13 @@ BFS_API bfs_status bfs_batch_autotune(bfs_graph_t g, const int32_t *roots, int32
  * batched search each; a server thread runs one level of every running lane
  * per iteration, each graph on its own stream (their work overlaps on the
  * GPU), admits queued queries into free lanes at every iteration boundary and
- * retires lanes whose frontier emptied.  Every result is the level vector of
- * a single search from the query's root, the same as bfs_run alone.
+ * retires lanes whose frontier emptied.  Every result is the level and
+ * parent vectors of a single search from the query's root, the same as
+ * bfs_run alone.
  * Graphs are admitted against `hbm_budget_bytes` by footprint (layout + lane
- * state + level rows; the lane count is halved until it fits); results not
- * yet collected count against the budget and hold back new admissions.
+ * state + level and parent rows; the lane count is halved until it fits);
+ * results not yet collected count against the budget and hold back new
+ * admissions.
  * All waits are bounded.  Thread-safe.
  */
 typedef struct {
@@ -354,17 +376,44 @@ BFS_API bfs_status bfs_server_create(int64_t hbm_budget_bytes, int32_t max_lanes
 /* Make `g` resident; the server holds it (BFS_ERR_BUSY for other calls on it)
  * until bfs_server_destroy.  BFS_ERR_OUT_OF_MEMORY if it does not fit. */
 BFS_API bfs_status bfs_server_add_graph(bfs_server_t s, bfs_graph_t g, int32_t *graph_id);
-/* Queue a query; BFS_ERR_BUSY when the queue is full, BFS_ERR_NOT_FOUND for an unknown graph. */
+/* Queue a query; BFS_ERR_BUSY when the queue is full (the rejection is counted
+ * in bfs_server_stats_t.rejected), BFS_ERR_NOT_FOUND for an unknown graph,
+ * BFS_ERR_INVALID_ARG for a root outside the graph. */
 BFS_API bfs_status bfs_server_submit(bfs_server_t s, int32_t graph_id, int32_t root, int64_t *ticket);
+/* Flags of bfs_server_submit_ex. */
+enum {
+    BFS_QUERY_PARENTS = 1        /* also compute the query's parent vector (one more reduction per
+                                    newly reached vertex and candidate edge in its lane) */
+};
+/* bfs_server_submit with flags (0 or BFS_QUERY_PARENTS); bfs_server_submit is flags = 0. */
+BFS_API bfs_status bfs_server_submit_ex(bfs_server_t s, int32_t graph_id, int32_t root, int32_t flags,
+                                        int64_t *ticket);
+/* Queued (not yet admitted) queries accepted before bfs_server_submit returns
+ * BFS_ERR_BUSY: 1 .. 1,048,576 (the default). */
+BFS_API bfs_status bfs_server_set_queue_limit(bfs_server_t s, int64_t limit);
 BFS_API bfs_status bfs_server_poll(bfs_server_t s, int64_t ticket, int32_t *done);
-/* Wait at most timeout_us for the query (BFS_ERR_TIMEOUT otherwise), copy its
- * level vector (n int32) to `level` (host or device; may be NULL) and release
- * it.  `parent` must be NULL: the server returns levels only. */
+/* Wait at most timeout_us for the query (BFS_ERR_TIMEOUT otherwise; the query
+ * stays valid and can be waited for again), copy its level vector (n int32) to
+ * `level` and, for a query submitted with BFS_QUERY_PARENTS, its parent vector
+ * (n int32: the smallest neighbour one level closer to the root, the root
+ * itself for the root, -1 if unreached) to `parent` (each host or device, or
+ * NULL), and release it.  A non-NULL `parent` for a query submitted without
+ * the flag is BFS_ERR_INVALID_ARG (the query is kept). */
 BFS_API bfs_status bfs_server_wait(bfs_server_t s, int64_t ticket, int64_t timeout_us, int32_t *level,
                                    int32_t *parent);
 BFS_API bfs_status bfs_server_stats(bfs_server_t s, bfs_server_stats_t *stats);
 /* Stop the server thread, drop uncollected results, release the graphs. */
 BFS_API bfs_status bfs_server_destroy(bfs_server_t s);
+
+/*
+ * Failure injection for tests of the error paths (no counterpart in the
+ * paper): the k-th device allocation the library makes from now on (k >= 1;
+ * allocations of graphs, search workspaces, batches, server lanes and codec
+ * scratch) fails as if the device were out of memory, and the call that made
+ * it returns BFS_ERR_OUT_OF_MEMORY after releasing what it had allocated.
+ * k = 0 disarms.  Process-wide; not for production use.
+ */
+BFS_API bfs_status bfs_debug_fail_allocation(int64_t k);
 
 /*
  * WAH-encode one bitmap (Sec. IV, Table 3) on the device.

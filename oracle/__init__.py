@@ -8,7 +8,8 @@ Each function follows a passage of the paper:
 
 * :func:`csr` -- the adjacency the search runs on (Sec. VII-A), tuples
   symmetrised with self-loops kept twice and duplicates kept.
-* :func:`bfs_levels` -- BFS hop distances (Sec. II), -1 when unreachable.
+* :func:`bfs_levels` -- BFS hop distances (Sec. II), -1 when unreachable;
+  :func:`bfs_sample` the same search stopped after a budget of scanned entries.
 * :func:`parents` -- the deterministic parent: the smallest neighbour on the
   previous level (the paper's (select,max) semiring of Sec. III-A picks the
   largest; ``use_max=True`` gives that reading).
@@ -65,6 +66,7 @@ def _load():
                 "oracle_csr_size": (_i64, [_i64, _int]),
                 "oracle_csr": (_int, [_i64, _i64, _ptr, _ptr, _int, _ptr, _ptr]),
                 "oracle_bfs_levels": (_i64, [_i64, _ptr, _ptr, ctypes.c_int32, _ptr]),
+                "oracle_bfs_sample": (_i64, [_i64, _ptr, _ptr, ctypes.c_int32, _i64, _ptr]),
                 "oracle_parents": (None, [_i64, _ptr, _ptr, _ptr, ctypes.c_int32, _int, _ptr]),
                 "oracle_range_begin": (_i64, [_i64, _int, _int]),
                 "oracle_range_len": (_i64, [_i64, _int, _int]),
@@ -120,6 +122,16 @@ def bfs_levels(g: CSR, root: int) -> np.ndarray:
     if rc < 0:
         raise ValueError("oracle_bfs_levels: bad root")
     return level
+
+
+def bfs_sample(g: CSR, root: int, budget: int):
+    """``(level, scanned)``: the queue BFS stopped once ``budget`` adjacency
+    entries were scanned; assigned levels are final, the rest -1."""
+    level = np.empty(g.n, dtype=np.int32)
+    k = _load().oracle_bfs_sample(g.n, _p(g.row_ptr), _p(g.col), root, int(budget), _p(level))
+    if k < 0:
+        raise ValueError("oracle_bfs_sample: bad root")
+    return level, int(k)
 
 
 def parents(g: CSR, level: np.ndarray, root: int, use_max: bool = False) -> np.ndarray:

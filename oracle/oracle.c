@@ -12,6 +12,8 @@
  *                            the reverse entry too (a self-loop gives two).
  *   oracle_bfs_levels     -- BFS as defined in Sec. II: hop distance from the
  *                            source; unreachable vertices get -1.
+ *   oracle_bfs_sample     -- the same search stopped after a budget of scanned
+ *                            entries (a bounded sample for timing).
  *   oracle_parents        -- deterministic parent: the smallest (or, for the
  *                            paper's (select,max) semiring of Sec. III-A, the
  *                            largest) neighbour on the previous level.
@@ -100,6 +102,36 @@ int64_t oracle_bfs_levels(int64_t n, const int64_t *row_ptr, const int32_t *col,
     }
     free(queue);
     return tail;
+}
+
+/* A bounded sample of oracle_bfs_levels for timing: the same queue BFS, which
+ * stops dequeuing once `budget` adjacency entries have been scanned (the vertex
+ * being scanned is finished).  Vertices dequeue in level order, so every level
+ * it assigns is the final one; unassigned vertices keep -1.  Returns the
+ * entries scanned, or -1 for a bad root. */
+int64_t oracle_bfs_sample(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t root,
+                          int64_t budget, int32_t *level)
+{
+    if (root < 0 || root >= n) return -1;
+    for (int64_t v = 0; v < n; ++v) level[v] = -1;
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!queue) return -2;
+    int64_t head = 0, tail = 0, scanned = 0;
+    level[root] = 0;
+    queue[tail++] = root;
+    while (head < tail && scanned < budget) {
+        int32_t u = queue[head++];
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            int32_t v = col[e];
+            if (level[v] < 0) {
+                level[v] = level[u] + 1;
+                queue[tail++] = v;
+            }
+        }
+        scanned += row_ptr[u + 1] - row_ptr[u];
+    }
+    free(queue);
+    return scanned;
 }
 
 /* Parent of every reached v != root: the smallest (use_max = 0) or largest

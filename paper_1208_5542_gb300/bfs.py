@@ -63,22 +63,23 @@ class Graph:
 
     # ------------------------------------------------------------ creation --
     @staticmethod
-    def _options(p, mode, wah_bits, debug):
+    def _options(p, mode, wah_bits, debug, autotune=False):
         o = native.Options()
         native.lib().bfs_options_default(ctypes.byref(o))
         o.grid_r = o.grid_c = int(p)
         o.mode = int(mode)
         o.wah_word_bits = int(wah_bits)
         o.debug_checks = int(bool(debug))
+        o.autotune = int(bool(autotune))
         return o
 
     @classmethod
     def from_edges(cls, n, src, dst, symmetrize=True, p=1, mode=MODE_COMPRESS_SIEVE, wah_bits=32,
-                   debug=False, stream=None) -> "Graph":
+                   debug=False, stream=None, autotune=False) -> "Graph":
         src, dst = _as_i32(src), _as_i32(dst)
         if len(src) != len(dst):
             raise ValueError("src and dst differ in length")
-        o = cls._options(p, mode, wah_bits, debug)
+        o = cls._options(p, mode, wah_bits, debug, autotune)
         h = ctypes.c_void_p()
         check(native.lib().bfs_graph_create_edges(int(n), len(src), _ptr(src) if len(src) else None,
                                                   _ptr(dst) if len(dst) else None, int(bool(symmetrize)),
@@ -203,6 +204,11 @@ class Graph:
                 out_stats.row_trace_counts = out_stats.row_trace_counts[: out_stats.n_levels]
         return parent, level, out_stats
 
+    def check_search(self, root: int, parent, level, stream=None):
+        """Raise BfsError(BFS_ERR_CORRUPT) unless (parent, level) -- int32 CUDA
+        tensors -- pass the level/parent checks of ``bfs_check_search``."""
+        check(native.lib().bfs_check_search(self._h, int(root), _ptr(parent), _ptr(level), _stream_ptr(stream)))
+
     # -------------------------------------------------------------- batch --
     def run_batch(self, roots, parents: bool = False, levels=None, stream=None):
         """Up to 64 searches at once; returns ``(levels [k, n], parents [k, n] | None, stats)``."""
@@ -288,9 +294,10 @@ class Server:
         self._n[int(gid.value)] = graph.n
         return int(gid.value)
 
-    def submit(self, graph_id: int, root: int) -> int:
+    def submit(self, graph_id: int, root: int, parents: bool = False) -> int:
         t = ctypes.c_int64()
-        check(native.lib().bfs_server_submit(self._h, int(graph_id), int(root), ctypes.byref(t)))
+        check(native.lib().bfs_server_submit_ex(self._h, int(graph_id), int(root),
+                                                native.QUERY_PARENTS if parents else 0, ctypes.byref(t)))
         return int(t.value)
 
     def poll(self, ticket: int) -> bool:
@@ -298,12 +305,20 @@ class Server:
         check(native.lib().bfs_server_poll(self._h, int(ticket), ctypes.byref(d)))
         return bool(d.value)
 
-    def wait(self, ticket: int, n: int, timeout_s: float = 30.0, out=None):
-        """Level vector (int32 CUDA tensor of length n, or ``out``) of a finished query."""
+    def wait(self, ticket: int, n: int, timeout_s: float = 30.0, out=None, parents: bool = False,
+             timeout_us: int | None = None):
+        """Level vector (int32 CUDA tensor of length n, or ``out``) of a finished
+        query; with ``parents`` the pair ``(level, parent)``."""
         if out is None:
             out = torch.empty(n, dtype=torch.int32, device="cuda")
-        check(native.lib().bfs_server_wait(self._h, int(ticket), int(timeout_s * 1e6), _ptr(out), None))
-        return out
+        par = torch.empty(n, dtype=torch.int32, device="cuda") if parents else None
+        us = int(timeout_s * 1e6) if timeout_us is None else int(timeout_us)
+        check(native.lib().bfs_server_wait(self._h, int(ticket), us, _ptr(out),
+                                           _ptr(par) if par is not None else None))
+        return (out, par) if parents else out
+
+    def set_queue_limit(self, limit: int):
+        check(native.lib().bfs_server_set_queue_limit(self._h, int(limit)))
 
     def stats(self) -> dict:
         st = native.ServerStats()
@@ -320,6 +335,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def debug_fail_allocation(k: int):
+    """Make the k-th device allocation of the library fail (0 disarms); tests only."""
+    check(native.lib().bfs_debug_fail_allocation(int(k)))
 
 
 def measure_scatter_reads(region_bytes: int = 512 << 10, iterations: int = 4096, stream=None) -> float:

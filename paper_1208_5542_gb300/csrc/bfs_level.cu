@@ -146,7 +146,7 @@ __device__ __forceinline__ int64_t range_begin(const LevelArgs& a, int64_t b) {
 // and the next bit live in shared memory; without, the visited word is read
 // through the read-only path (pi does not change during the expansion) and
 // the next bit is a reduction at L2.
-template <bool WIN, bool DEDUP>
+template <bool WIN, bool DEDUP, bool ROWX>
 struct Visitor {
     const uint32_t* s_pi;
     uint32_t* s_t;
@@ -184,7 +184,7 @@ struct Visitor {
             return;
         }
         piw = DEDUP ? seen(a, v) : 0xffffffffu;
-        if (DEDUP && tb) tw = seen_t(v);
+        if (DEDUP && ROWX) tw = seen_t(v);
     }
     // Visit of a fresh v from u, given an earlier read pv of its parent: when
     // pv <= u the visit changes nothing (pv != -1 means v already has a
@@ -192,7 +192,7 @@ struct Visitor {
     // parent, and the visitor that read -1 sets the next bit.  The visitor of
     // the first update read -1, so the bit is always set.
     __device__ __forceinline__ void mark(const LevelArgs& a, int32_t v, int32_t u, uint32_t pv, uint32_t tw) const {
-        if (tb) {
+        if (ROWX) {
             // Row exchange: every block that reaches v records it in its own
             // partial t_{i,j}.  The bit is already there when the word read
             // first has it, or when the parent read first lies in [jb, u]: a
@@ -220,8 +220,8 @@ struct Visitor {
 constexpr int kIlp = 4;
 
 // All 32 lanes expand one column: kIlp x 32 consecutive entries per step.
-template <bool WIN, bool DEDUP>
-__device__ __forceinline__ void warp_column(const LevelArgs& a, const Visitor<WIN, DEDUP>& vis, int32_t u, int64_t beg,
+template <bool WIN, bool DEDUP, bool ROWX>
+__device__ __forceinline__ void warp_column(const LevelArgs& a, const Visitor<WIN, DEDUP, ROWX>& vis, int32_t u, int64_t beg,
                                             uint32_t len) {
     const int32_t* col = a.ir + beg;
     for (uint32_t e = lane_id(); e < len; e += 32 * kIlp) {
@@ -244,8 +244,8 @@ __device__ __forceinline__ void warp_column(const LevelArgs& a, const Visitor<WI
 // least kCoop entries are expanded by the whole warp one after the other; the
 // short ones share the warp through a load-balanced search over their entry
 // counts, 32 consecutive entries of the concatenated columns per step.
-template <bool WIN, bool DEDUP>
-__device__ __forceinline__ void warp_expand(const LevelArgs& a, const Visitor<WIN, DEDUP>& vis, int row, int32_t u,
+template <bool WIN, bool DEDUP, bool ROWX>
+__device__ __forceinline__ void warp_expand(const LevelArgs& a, const Visitor<WIN, DEDUP, ROWX>& vis, int row, int32_t u,
                                             int64_t beg, uint32_t len, unsigned long long& edges,
                                             unsigned long long& hits) {
     const uint32_t lane = lane_id();
@@ -274,7 +274,7 @@ __device__ __forceinline__ void warp_expand(const LevelArgs& a, const Visitor<WI
     while (coop) {
         const int src = __ffs(coop) - 1;
         coop &= coop - 1;
-        warp_column<WIN, DEDUP>(a, vis, __shfl_sync(0xffffffffu, u, src), __shfl_sync(0xffffffffu, beg, src),
+        warp_column<WIN, DEDUP, ROWX>(a, vis, __shfl_sync(0xffffffffu, u, src), __shfl_sync(0xffffffffu, beg, src),
                          __shfl_sync(0xffffffffu, len, src));
     }
     if (len >= kCoop) len = 0;
@@ -471,7 +471,7 @@ __device__ __forceinline__ void row_affine(const LevelArgs& a, unsigned long lon
 // one stream, decoded by one warp: a warp scan of run lengths from the
 // chunk's group base places every word, a scan of item counts numbers the
 // decoded vertices, and the warp expands them 32 at a time.
-template <typename W, bool WIN, bool DEDUP>
+template <typename W, bool WIN, bool DEDUP, bool ROWX>
 __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
     if (a.ctl->dedup != (DEDUP ? 1 : 0) || a.ctl->bu) return;   // another variant expands this level
     using T = Wah<W>;
@@ -540,8 +540,8 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
         const uint32_t items = __shfl_sync(0xffffffffu, cincl, 31);
         nitems += c;
         const BlockView bv = block_view(a, s);
-        const Visitor<WIN, DEDUP> vis{s_pi, s_t, range_begin(a, row),
-                                      a.row_exchange ? a.tblk + s * a.dir_stride : nullptr, (uint32_t)jb};
+        const Visitor<WIN, DEDUP, ROWX> vis{s_pi, s_t, range_begin(a, row), ROWX ? a.tblk + s * a.dir_stride : nullptr,
+                                            (uint32_t)jb};
         // items q0 .. q0+31, one per lane: decode, look up the column and
         // prefetch its entries; the next batch's lookups and prefetches are
         // issued before this batch is expanded
@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
             int64_t bn = 0;
             uint32_t ln = 0;
             if (q0 + 32 < items) item(q0 + 32, un, bn, ln);
-            warp_expand<WIN, DEDUP>(a, vis, row, u, begin, len, edges, hits);
+            warp_expand<WIN, DEDUP, ROWX>(a, vis, row, u, begin, len, edges, hits);
             u = un;
             begin = bn;
             len = ln;
@@ -616,8 +616,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
         if (items == 0) return;
         nitems += cnt;
         const BlockView bv = block_view(a, b);
-        const Visitor<WIN, DEDUP> vis{s_pi, s_t, range_begin(a, row),
-                                      a.row_exchange ? a.tblk + b * a.dir_stride : nullptr, (uint32_t)jb};
+        const Visitor<WIN, DEDUP, false> vis{s_pi, s_t, range_begin(a, row), nullptr, (uint32_t)jb};
         auto item = [&](uint32_t q0, int32_t& u, int64_t& begin, uint32_t& len) {
             const uint32_t q = q0 + lane_id();
             const int o = owner_lane(cexcl, q < items ? q : items - 1);
@@ -642,7 +641,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
             int64_t bn = 0;
             uint32_t ln = 0;
             if (q0 + 32 < items) item(q0 + 32, un, bn, ln);
-            warp_expand<WIN, DEDUP>(a, vis, row, u, begin, len, edges, hits);
+            warp_expand<WIN, DEDUP, false>(a, vis, row, u, begin, len, edges, hits);
             u = un;
             begin = bn;
             len = ln;
@@ -653,7 +652,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_plain(LevelArgs a) {
 }
 
 // Pieces of long columns, row by row: one warp per piece.
-template <bool WIN, bool DEDUP>
+template <bool WIN, bool DEDUP, bool ROWX>
 __global__ void __launch_bounds__(kXT, 1) expand_pieces(LevelArgs a) {
     if (a.ctl->dedup != (DEDUP ? 1 : 0) || a.ctl->bu) return;   // another variant expands this level
     extern __shared__ uint32_t s_win[];
@@ -666,10 +665,10 @@ __global__ void __launch_bounds__(kXT, 1) expand_pieces(LevelArgs a) {
     auto do_unit = [&](int row, int64_t x) {
         const Item it = a.pieces[a.row_piece_base[row] + x];
         const uint32_t j = (uint32_t)it.u / (uint32_t)a.nb;               // the piece's source range
-        const Visitor<WIN, DEDUP> vis{s_pi, s_t, range_begin(a, row),
-                                      a.row_exchange ? a.tblk + ((int64_t)row * a.p + j) * a.dir_stride : nullptr,
-                                      (uint32_t)range_begin(a, j)};
-        warp_column<WIN, DEDUP>(a, vis, it.u, it.begin, it.len);
+        const Visitor<WIN, DEDUP, ROWX> vis{s_pi, s_t, range_begin(a, row),
+                                            ROWX ? a.tblk + ((int64_t)row * a.p + j) * a.dir_stride : nullptr,
+                                            (uint32_t)range_begin(a, j)};
+        warp_column<WIN, DEDUP, ROWX>(a, vis, it.u, it.begin, it.len);
     };
     row_affine<WIN>(a, a.row_piece_next, 1, units_in_row, do_unit, s_pi, s_t, s_row);
 }
@@ -1211,6 +1210,42 @@ __global__ void trace_copy(const uint32_t* __restrict__ xbuf, int64_t slot_cap_u
     }
 }
 
+// The output checks of bfs_check_search: root level 0 and its own parent;
+// an unreached vertex -1 / -1; a reached one a parent in [0, n) one level
+// closer to the root.  out[0] counts failures, out[1] keeps the smallest
+// failing vertex, out[2] counts the reached vertices.
+__global__ void __launch_bounds__(kNT) verify_search(const int32_t* __restrict__ parent,
+                                                     const int32_t* __restrict__ level, int64_t n, int32_t root,
+                                                     unsigned long long* out) {
+    unsigned long long bad = 0, reached = 0, first = ~0ull;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t lv = level[v], pv = parent[v];
+        bool ok;
+        if (v == root) ok = lv == 0 && pv == root;
+        else if (lv < 0) ok = lv == -1 && pv == -1;
+        else ok = lv > 0 && pv >= 0 && (int64_t)pv < n && level[pv] == lv - 1;
+        reached += lv >= 0;
+        if (!ok) {
+            ++bad;
+            if ((unsigned long long)v < first) first = (unsigned long long)v;
+        }
+    }
+    bad = warp_sum(bad);
+    reached = warp_sum(reached);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, first, d);
+        first = y < first ? y : first;
+    }
+    if (lane_id() == 0) {
+        if (bad) atomicAdd(out, bad);
+        if (first != ~0ull) atomicMin(out + 1, first);
+        if (reached) atomicAdd(out + 2, reached);
+    }
+}
+
+__global__ void visited_count(const LevelCtl* c, unsigned long long* out) { out[3] = (unsigned long long)c->visited; }
+
 int sm_count() {
     static int cached = 0;
     if (!cached) {
@@ -1243,14 +1278,46 @@ bfs_status allow_smem(K kernel, size_t dyn) {
     return BFS_OK;
 }
 
+// The expansion of a level: with the row window one kernel; without, the two
+// variants (with and without reading the parent first), of which the level's
+// device-side choice runs and the other returns at once.
+template <typename W, bool ROWX>
+void launch_expand_wah(const LevelArgs& a, bool win, int grid, size_t dyn, cudaStream_t s) {
+    if (win) {
+        expand_wah<W, true, false, ROWX><<<grid, kXT, dyn, s>>>(a);
+    } else {
+        expand_wah<W, false, true, ROWX><<<grid, kXT, 0, s>>>(a);
+        expand_wah<W, false, false, ROWX><<<grid, kXT, 0, s>>>(a);
+    }
+}
+
+template <bool ROWX>
+void launch_expand_pieces(const LevelArgs& a, bool win, int grid, size_t dyn, cudaStream_t s) {
+    if (win) {
+        expand_pieces<true, false, ROWX><<<grid, kXT, dyn, s>>>(a);
+    } else {
+        expand_pieces<false, true, ROWX><<<grid, kXT, 0, s>>>(a);
+        expand_pieces<false, false, ROWX><<<grid, kXT, 0, s>>>(a);
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- workspace --
+bfs_status ensure_workspace_once(bfs_graph* g);
+
+// All of the search workspace or none of it: a failed allocation releases the rest.
 bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
     (void)st;
+    if (g->W.bm_words) return BFS_OK;
+    const bfs_status rc = ensure_workspace_once(g);
+    if (rc != BFS_OK) free_workspace(g);
+    return rc;
+}
+
+bfs_status ensure_workspace_once(bfs_graph* g) {
     Workspace& W = g->W;
     const Layout& L = g->L;
-    if (W.bm_words) return BFS_OK;
     const int p = L.p;
     const int64_t p2 = (int64_t)p * p;
     W.bm_words = ((L.n + 31) / 32 + 4 + 3) / 4 * 4;
@@ -1308,10 +1375,13 @@ bfs_status ensure_workspace(bfs_graph* g, cudaStream_t st) {
     W.win_words = (window_bytes(win) + static_bytes <= (size_t)kSmemLimit) ? win : 0;
     if (W.win_words) {
         const size_t dyn = window_bytes(W.win_words);
-        BFS_TRY(allow_smem(expand_wah<uint32_t, true, false>, dyn));
-        BFS_TRY(allow_smem(expand_wah<unsigned long long, true, false>, dyn));
+        BFS_TRY(allow_smem(expand_wah<uint32_t, true, false, false>, dyn));
+        BFS_TRY(allow_smem(expand_wah<unsigned long long, true, false, false>, dyn));
+        BFS_TRY(allow_smem(expand_wah<uint32_t, true, false, true>, dyn));
+        BFS_TRY(allow_smem(expand_wah<unsigned long long, true, false, true>, dyn));
+        BFS_TRY(allow_smem(expand_pieces<true, false, true>, dyn));
         BFS_TRY(allow_smem(expand_plain<true, false>, dyn));
-        BFS_TRY(allow_smem(expand_pieces<true, false>, dyn));
+        BFS_TRY(allow_smem(expand_pieces<true, false, false>, dyn));
     }
     return BFS_OK;
 }
@@ -1357,6 +1427,28 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
     return ms;
 }
 
+// Run the output checks on device outputs; with ctl, the reached count must
+// also equal the vertices the search visited.
+bfs_status check_outputs(int64_t n, int32_t root, const int32_t* parent, const int32_t* level, const LevelCtl* ctl,
+                         cudaStream_t st) {
+    DevBuf out;
+    BFS_TRY(out.alloc(4 * sizeof(unsigned long long)));
+    unsigned long long init[4] = {0ull, ~0ull, 0ull, 0ull};
+    BFS_CUDA_TRY(cudaMemcpyAsync(out.ptr, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    verify_search<<<(int)std::min<int64_t>((n + kNT - 1) / kNT, (int64_t)sm_count() * 8), kNT, 0, st>>>(
+        parent, level, n, root, out.as<unsigned long long>());
+    if (ctl) visited_count<<<1, 1, 0, st>>>(ctl, out.as<unsigned long long>());
+    BFS_CUDA_TRY(cudaGetLastError());
+    unsigned long long h[4];
+    BFS_CUDA_TRY(cudaMemcpyAsync(h, out.ptr, sizeof(h), cudaMemcpyDeviceToHost, st));
+    BFS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h[0])
+        return set_error(BFS_ERR_CORRUPT, "%llu vertices fail the level/parent checks (first: vertex %llu)", h[0], h[1]);
+    if (ctl && h[2] != h[3])
+        return set_error(BFS_ERR_CORRUPT, "%llu vertices reached but %llu visited by the search", h[2], h[3]);
+    return BFS_OK;
+}
+
 bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* level, bfs_run_stats* stats,
                       cudaStream_t st) {
     Layout& L = g->L;
@@ -1376,14 +1468,18 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     // the compressed row exchange of the fold belongs to DIR-WAH (COMPRESS_SIEVE)
     const bool rowx = g->row_exchange && mode == BFS_MODE_COMPRESS_SIEVE;
     if (rowx && !W.tblk.ptr) {
-        // allocated once: captured level loops keep the addresses
+        // allocated once (all or none): captured level loops keep the addresses
         const int64_t cap32 = L.nb / 31 + 2, cap64 = L.nb / 63 + 2;
         W.row_cap = cap32;
-        BFS_TRY(W.tblk.alloc(sizeof(uint32_t) * (size_t)(p2 * L.dir_stride)));
-        BFS_TRY(W.rowbuf.alloc((size_t)p2 * std::max<int64_t>(4 * cap32, 8 * cap64)));
-        BFS_TRY(W.rowcount.alloc(sizeof(int64_t) * (size_t)p2));
-        BFS_TRY(W.rowfirst.alloc(sizeof(int64_t) * 2 * (size_t)(p2 * W.enc_cps)));
-        BFS_TRY(W.rowlive.alloc((size_t)p2));
+        bfs_status rc = W.rowbuf.alloc((size_t)p2 * std::max<int64_t>(4 * cap32, 8 * cap64));
+        if (rc == BFS_OK) rc = W.rowcount.alloc(sizeof(int64_t) * (size_t)p2);
+        if (rc == BFS_OK) rc = W.rowfirst.alloc(sizeof(int64_t) * 2 * (size_t)(p2 * W.enc_cps));
+        if (rc == BFS_OK) rc = W.rowlive.alloc((size_t)p2);
+        if (rc == BFS_OK) rc = W.tblk.alloc(sizeof(uint32_t) * (size_t)(p2 * L.dir_stride));
+        if (rc != BFS_OK) {
+            W.tblk.release(); W.rowbuf.release(); W.rowcount.release(); W.rowfirst.release(); W.rowlive.release();
+            return rc;
+        }
         BFS_CUDA_TRY(cudaMemsetAsync(W.tblk.ptr, 0, W.tblk.bytes, st));
         W.tblk_dirty = false;
     }
@@ -1539,8 +1635,10 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             }
             BFS_CUDA_TRY(cudaGetLastError());
         } else {
-            // the exchanged-vertex count is a statistic: only the stepwise loop asks for it
-            BFS_TRY(launch_wah_encode_parallel(ea, wbits, W.enc_sums.ptr, W.enc_bases.ptr, W.enc_cps,
+            // the exchanged-vertex and chunk counts are statistics: only the stepwise loop asks for them
+            EncodeArgs eh = ea;
+            eh.live_chunks = host ? ctr + C_ENC_CHUNKS : nullptr;
+            BFS_TRY(launch_wah_encode_parallel(eh, wbits, W.enc_sums.ptr, W.enc_bases.ptr, W.enc_cps,
                                                W.enc_flags.ptr, host ? ctr + C_EXCHANGED : nullptr, sm_count() * 6, s));
             if (bu_kernels) {           // a bottom-up level reads the streams as bitmaps
                 clear_gbits<<<sm_count() * 4, kNT, 0, s>>>(a);
@@ -1561,28 +1659,16 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             }
             if (host && timing) cudaEventRecord(W.ev[2], s);
             if (wbits == 32) {
-                if (win) {
-                    expand_wah<uint32_t, true, false><<<xgrid, kXT, dyn, s>>>(a);
-                } else {
-                    expand_wah<uint32_t, false, true><<<xgrid, kXT, 0, s>>>(a);
-                    expand_wah<uint32_t, false, false><<<xgrid, kXT, 0, s>>>(a);
-                }
+                if (rowx) launch_expand_wah<uint32_t, true>(a, win, xgrid, dyn, s);
+                else launch_expand_wah<uint32_t, false>(a, win, xgrid, dyn, s);
             } else {
-                if (win) {
-                    expand_wah<unsigned long long, true, false><<<xgrid, kXT, dyn, s>>>(a);
-                } else {
-                    expand_wah<unsigned long long, false, true><<<xgrid, kXT, 0, s>>>(a);
-                    expand_wah<unsigned long long, false, false><<<xgrid, kXT, 0, s>>>(a);
-                }
+                if (rowx) launch_expand_wah<unsigned long long, true>(a, win, xgrid, dyn, s);
+                else launch_expand_wah<unsigned long long, false>(a, win, xgrid, dyn, s);
             }
             BFS_CUDA_TRY(cudaGetLastError());
         }
-        if (win) {
-            expand_pieces<true, false><<<xgrid, kXT, dyn, s>>>(a);
-        } else {
-            expand_pieces<false, true><<<xgrid, kXT, 0, s>>>(a);
-            expand_pieces<false, false><<<xgrid, kXT, 0, s>>>(a);
-        }
+        if (rowx) launch_expand_pieces<true>(a, win, xgrid, dyn, s);
+        else launch_expand_pieces<false>(a, win, xgrid, dyn, s);
         BFS_CUDA_TRY(cudaGetLastError());
         if (bu_kernels) {
             expand_bottom_up<<<sm_count() * 8, kNT, 0, s>>>(a);
@@ -1592,7 +1678,9 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         if (rowx) {
             // the row exchange: every block's partial, sieved by not(pi_i), WAH-encoded
             // into its row buffer; the fold OR-decodes the buffers of each block-row into t
-            BFS_TRY(launch_wah_encode_parallel(ra, wbits, W.enc_sums.ptr, W.enc_bases.ptr, W.enc_cps, W.enc_flags.ptr,
+            EncodeArgs rh = ra;
+            rh.live_chunks = host ? ctr + C_ROW_CHUNKS : nullptr;
+            BFS_TRY(launch_wah_encode_parallel(rh, wbits, W.enc_sums.ptr, W.enc_bases.ptr, W.enc_cps, W.enc_flags.ptr,
                                                nullptr, sm_count() * 6, s));
             if (host && timing) cudaEventRecord(W.ev[5], s);
             if (host && row_tracing && k < stats->capacity_levels) {
@@ -1686,6 +1774,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         if (h[C_ERROR])
             return set_error(BFS_ERR_CORRUPT, "device invariant check failed (code %llu)",
                              (unsigned long long)h[C_ERROR]);
+        if (g->debug_checks) return check_outputs(L.n, root, parent, level, ctl, st);
         return BFS_OK;
     }
 
@@ -1713,6 +1802,8 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             ls.edges_scanned = (int64_t)h[C_EDGES];
             ls.row_wah_bytes = (int64_t)h[C_ROW_WORDS] * (wbits / 8);
             ls.bottom_up = h[C_BOTTOM_UP] ? 1 : 0;
+            ls.compress_chunks = (int64_t)h[C_ENC_CHUNKS];
+            ls.row_compress_chunks = (int64_t)h[C_ROW_CHUNKS];
             if (timing) {
                 ls.ms_compress_sieve = elapsed(W.ev[0], W.ev[1]);
                 ls.ms_communication = elapsed(W.ev[1], W.ev[2]);
@@ -1728,6 +1819,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         frontier = (int64_t)h[C_NEXT_COUNT];
         if (frontier == 0 || k + 1 >= max_levels) break;
     }
+    if (g->debug_checks) return check_outputs(L.n, root, parent, level, ctl, st);
     return BFS_OK;
 }
 
@@ -1735,6 +1827,15 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
 }  // namespace bfsgb
 
 using namespace bfsgb;
+
+extern "C" bfs_status bfs_check_search(bfs_graph_t g, int32_t root, const int32_t* parent, const int32_t* level,
+                                       void* stream) {
+    if (!g) return set_error(BFS_ERR_INVALID_ARG, "graph is NULL");
+    if (root < 0 || (int64_t)root >= g->L.n) return set_error(BFS_ERR_INVALID_ARG, "root %d outside [0, %lld)", root, (long long)g->L.n);
+    if (!is_device_pointer(parent) || !is_device_pointer(level))
+        return set_error(BFS_ERR_INVALID_ARG, "parent and level must be device pointers");
+    return check_outputs(g->L.n, root, parent, level, nullptr, static_cast<cudaStream_t>(stream));
+}
 
 extern "C" bfs_status bfs_run(bfs_graph_t g, int32_t root, int32_t* parent, int32_t* level, bfs_run_stats* stats,
                               void* stream) {
@@ -1753,9 +1854,10 @@ extern "C" bfs_status bfs_run(bfs_graph_t g, int32_t root, int32_t* parent, int3
         return rs;
     }
     Workspace& W = g->W;
-    if (!W.tmp_parent.ptr) {
-        BFS_TRY(W.tmp_parent.alloc(sizeof(int32_t) * g->L.n));
-        BFS_TRY(W.tmp_level.alloc(sizeof(int32_t) * g->L.n));
+    if (!W.tmp_parent.ptr || !W.tmp_level.ptr) {
+        bfs_status rc = W.tmp_parent.alloc(sizeof(int32_t) * g->L.n);
+        if (rc == BFS_OK) rc = W.tmp_level.alloc(sizeof(int32_t) * g->L.n);
+        if (rc != BFS_OK) { W.tmp_parent.release(); W.tmp_level.release(); return rc; }
     }
     {
         const bfs_status rs = run_search(g, root, W.tmp_parent.as<int32_t>(), W.tmp_level.as<int32_t>(), stats, st);

@@ -7,6 +7,7 @@
 // of those counts gives the block-local column offsets; set counts give the
 // directory V_{i,j} (Eq. 4); a scan of directory popcounts gives the rank of
 // every nonempty column; the entries are then scattered column by column.
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 #include <new>
@@ -48,9 +49,17 @@ bool is_device_pointer(const void* p) {
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
+// Allocation-failure injection (bfs_debug_fail_allocation): the armed
+// allocation fails as if the device were out of memory.  0 = disarmed.
+std::atomic<int64_t> g_fail_countdown{0};
+
 bfs_status DevBuf::alloc(size_t nbytes) {
     release();
     if (nbytes == 0) nbytes = 16;
+    int64_t k = g_fail_countdown.load();
+    while (k > 0 && !g_fail_countdown.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 1) return set_error(BFS_ERR_OUT_OF_MEMORY, "cudaMalloc(%zu bytes): injected failure", nbytes);
     cudaError_t e = cudaMalloc(&ptr, nbytes);
     if (e != cudaSuccess) {
         ptr = nullptr;
@@ -512,7 +521,8 @@ bfs_status create_common(int64_t n, int64_t m, const int32_t* src, const int32_t
     g->L.p = o.grid_r;
     g->mode = o.mode;
     g->wah_bits = o.wah_word_bits;
-    g->debug_checks = o.debug_checks;
+    g->debug_checks = o.debug_checks ? 1 : 0;
+    g->autotune = o.autotune ? 1 : 0;
     g->row_exchange = o.row_exchange ? 1 : 0;
     g->symmetric = symmetrize ? 1 : 0;
     cudaGetDevice(&g->device);
@@ -577,6 +587,12 @@ const char* bfs_status_string(bfs_status s) {
         case BFS_ERR_NOT_FOUND: return "BFS_ERR_NOT_FOUND";
     }
     return "BFS_ERR_UNKNOWN";
+}
+
+bfs_status bfs_debug_fail_allocation(int64_t k) {
+    if (k < 0) return set_error(BFS_ERR_INVALID_ARG, "k must be >= 0");
+    g_fail_countdown.store(k);
+    return BFS_OK;
 }
 
 bfs_status bfs_last_error(char* buf, int64_t len) {

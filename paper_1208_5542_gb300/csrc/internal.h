@@ -95,6 +95,8 @@ enum Counter : int {
     C_ROW_WORDS,         // WAH words of the compressed row exchange
     C_NEXT_DEGREE,       // degree sum of the next frontier (direction choice)
     C_BOTTOM_UP,         // 1: this level ran bottom-up
+    C_ENC_CHUNKS,        // chunks read by the column encoder (statistics only)
+    C_ROW_CHUNKS,        // chunks read by the row encoder (statistics only)
     C_NUM
 };
 
@@ -152,7 +154,9 @@ struct bfs_graph {
     bfsgb::Workspace W;
     int mode = BFS_MODE_COMPRESS_SIEVE;
     int wah_bits = 32;
-    int debug_checks = 0;
+    int debug_checks = 0;        // 1: bfs_run checks its outputs (bfs_check_search) before returning
+    int autotune = 0;            // 1: the first bfs_run_batch picks the batch launch shape
+    bool batch_tuned = false;
     int row_exchange = 0;
     int symmetric = 0;           // built with symmetrize = 1: in-neighbours = out-neighbours
     int direction = BFS_DIRECTION_TOP_DOWN;
@@ -201,6 +205,7 @@ struct EncodeArgs {
                                 //   group and that word's first group, 2 entries
     const int32_t* skip;        // or nullptr: the passes do nothing while *skip != 0 (the counts
                                 //   are set to 0)
+    unsigned long long* live_chunks;   // or nullptr: chunks the passes read are counted here
     uint8_t* slot_bits;         // or nullptr: the scan writes 1 for a slot whose stream carries a set bit
     const uint8_t* slot_live;   // or nullptr: a slot with slot_live[s] == 0 is all zero (not read)
 };

@@ -58,6 +58,7 @@ struct MsState {
     int32_t max_levels;         // iteration limit (n + 1 at most)
     int32_t* levels;            // [n_roots][n]
     int32_t* parents;           // [n_roots][n] or nullptr
+    unsigned long long parent_mask;  // lanes whose parents are computed (with parents != nullptr)
     // per level
     int32_t cur;                // index of the current f / act buffers
     int32_t level;              // k
@@ -144,7 +145,7 @@ struct MsVisit {
         if (!nb) return;
         atomicOr(s->nxt + v, nb);
         if (s->parents) {
-            unsigned long long m = nb;
+            unsigned long long m = nb & s->parent_mask;
             while (m) {
                 const int r = __ffsll((long long)m) - 1;
                 m &= m - 1;
@@ -371,12 +372,15 @@ __global__ void ms_admit_clear(MsState* S, unsigned long long mask, const int32_
         const int r = lanes[q];
         if (r < 0 || r >= 64) { ms_fault(S, 7, (uint64_t)x, (uint64_t)r); continue; }
         s.levels[(int64_t)r * s.n + (x - q * s.n)] = -1;
+        if (s.parents) s.parents[(int64_t)r * s.n + (x - q * s.n)] = -1;
     }
     if (tid == 0) s.alive = 0;
 }
 
-// Admission, phase B: lane lanes[q] starts from roots[q] at this iteration.
-__global__ void ms_admit_roots(MsState* S, const int32_t* lanes, const int32_t* roots, int nlanes) {
+// Admission, phase B: lane lanes[q] starts from roots[q] at this iteration,
+// computing parents when want_parents[q] != 0.
+__global__ void ms_admit_roots(MsState* S, const int32_t* lanes, const int32_t* roots, const int32_t* want_parents,
+                               int nlanes) {
     MsState& s = *S;
     const int q = threadIdx.x;
     if (q >= nlanes) return;
@@ -384,9 +388,12 @@ __global__ void ms_admit_roots(MsState* S, const int32_t* lanes, const int32_t* 
     const int32_t v = roots[q];
     if (r < 0 || r >= 64 || (uint64_t)(uint32_t)v >= (uint64_t)s.n) { ms_fault(S, 4, (uint64_t)r, (uint32_t)v); return; }
     const unsigned long long bit = 1ull << r;
+    if (want_parents[q]) atomicOr(&s.parent_mask, bit);
+    else atomicAnd(&s.parent_mask, ~bit);
     atomicOr(s.vis + v, bit);
     const unsigned long long old = atomicOr(s.f[s.cur] + v, bit);
     s.levels[(int64_t)r * s.n + v] = 0;
+    if (s.parents) s.parents[(int64_t)r * s.n + v] = v;
     s.lane_start[r] = s.level;
     if (old == 0ull) {
         const unsigned long long pos = atomicAdd(&s.act_count[s.cur], 1ull);
@@ -557,6 +564,7 @@ struct MsCall {
     int32_t max_levels;
     int32_t* levels;
     int32_t* parents;
+    unsigned long long parent_mask;
 };
 
 bfs_status ms_run(bfs_graph* g, const int32_t* roots_host, int32_t n_roots, int32_t* levels, int32_t* parents,
@@ -567,7 +575,8 @@ bfs_status ms_run(bfs_graph* g, const int32_t* roots_host, int32_t n_roots, int3
     BFS_TRY(ms_build_graph(g, wp, st));
     // per-call fields of the state block
     BFS_CUDA_TRY(cudaMemcpyAsync(c->roots.ptr, roots_host, sizeof(int32_t) * n_roots, cudaMemcpyHostToDevice, st));
-    MsCall call{c->roots.as<int32_t>(), n_roots, (int32_t)std::min<int64_t>(g->L.n + 1, 0x7fffffff), levels, parents};
+    MsCall call{c->roots.as<int32_t>(), n_roots, (int32_t)std::min<int64_t>(g->L.n + 1, 0x7fffffff), levels, parents,
+                parents ? ~0ull : 0ull};
     BFS_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(c->state.ptr) + offsetof(MsState, roots), &call,
                                  sizeof(MsCall), cudaMemcpyHostToDevice, st));
     BFS_CUDA_TRY(cudaGraphLaunch(c->exec[wp], st));
@@ -604,6 +613,10 @@ extern "C" bfs_status bfs_run_batch(bfs_graph_t g, const int32_t* roots, int32_t
     for (int r = 0; r < n_roots; ++r)
         if (hroots[r] < 0 || (int64_t)hroots[r] >= g->L.n)
             return set_error(BFS_ERR_INVALID_ARG, "root %d outside [0, %lld)", hroots[r], (long long)g->L.n);
+    if (g->autotune && !g->batch_tuned) {       // bfs_options.autotune: tune on the first batch's roots
+        g->batch_tuned = true;
+        BFS_TRY(bfs_batch_autotune(g, hroots, n_roots, levels, nullptr, nullptr, stream));
+    }
     int expect = 0;
     if (!g->busy.compare_exchange_strong(expect, 1)) return set_error(BFS_ERR_BUSY, "another search on this graph is running");
     bfs_status rc = ms_run(g, hroots, n_roots, levels, parents, stats, st);
@@ -685,7 +698,9 @@ struct ServeGraph {
     int lanes = 0;
     cudaStream_t stream = nullptr;
     DevBuf levels;                   // [lanes][n]
-    DevBuf admit;                    // lanes[64], roots[64]
+    DevBuf parents;                  // [lanes][n]: the smallest previous-level neighbour
+    DevBuf admit;                    // lanes[64], roots[64], want_parents[64]
+    bool lane_parents[64] = {};      // the query running in lane r asked for parents
     int32_t* h_admit = nullptr;      // pinned staging of `admit`
     unsigned long long* h_alive = nullptr;   // pinned copy of the alive mask
     cudaGraphExec_t step = nullptr;  // expand, pieces, reduce, step end
@@ -703,8 +718,9 @@ struct Request {
     int32_t graph = 0;
     int32_t root = 0;
     int state = 0;                   // 0 queued, 1 running, 2 done
+    bool parents = false;            // submitted with BFS_QUERY_PARENTS
     std::chrono::steady_clock::time_point t_submit, t_done;
-    int32_t* result = nullptr;       // device [n] once done
+    int32_t* result = nullptr;       // device, once done: the level row (n), then the parent row (n) if asked
 };
 
 }  // namespace
@@ -724,6 +740,7 @@ struct bfs_server {
     bool failed = false;
     char fail_msg[256] = {0};
     int64_t next_ticket = 1;
+    int64_t queue_limit = 1 << 20;   // queued requests accepted before BFS_ERR_BUSY
     int64_t submitted = 0, completed = 0, rejected = 0, queued = 0;
     int64_t iterations = 0;
     int peak_lanes = 0;
@@ -735,7 +752,7 @@ struct bfs_server {
 namespace bfsgb {
 namespace {
 
-constexpr int64_t kMaxQueued = 1 << 20;
+constexpr int64_t kMaxQueued = 1 << 20;      // default queue limit (bfs_server_set_queue_limit)
 
 bfs_status build_step_graph(ServeGraph* sg) {
     MsContext* c = sg->g->ms;
@@ -764,6 +781,7 @@ void release_graph(ServeGraph* sg) {
     if (sg->h_alive) cudaFreeHost(sg->h_alive);
     if (sg->stream) cudaStreamDestroy(sg->stream);
     sg->levels.release();
+    sg->parents.release();
     sg->admit.release();
     if (sg->g) sg->g->busy.store(0);
 }
@@ -794,9 +812,13 @@ bool finish_iteration(bfs_server* s, ServeGraph* sg) {
     for (int r = 0; r < sg->lanes; ++r) {
         if (!(done & (1ull << r))) continue;
         void* buf = nullptr;
-        if (cudaMallocAsync(&buf, sizeof(int32_t) * n, sg->stream) != cudaSuccess) { fail(s, "result allocation failed"); return false; }
+        const int rows = sg->lane_parents[r] ? 2 : 1;
+        if (cudaMallocAsync(&buf, rows * sizeof(int32_t) * n, sg->stream) != cudaSuccess) { fail(s, "result allocation failed"); return false; }
         cudaMemcpyAsync(buf, sg->levels.as<int32_t>() + (int64_t)r * n, sizeof(int32_t) * n,
                         cudaMemcpyDeviceToDevice, sg->stream);
+        if (rows == 2)
+            cudaMemcpyAsync(static_cast<int32_t*>(buf) + n, sg->parents.as<int32_t>() + (int64_t)r * n,
+                            sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, sg->stream);
         fin.push_back({sg->lane_ticket[r], static_cast<int32_t*>(buf)});
         sg->lane_ticket[r] = -1;
     }
@@ -811,7 +833,7 @@ bool finish_iteration(bfs_server* s, ServeGraph* sg) {
         q.state = 2;
         q.result = f.second;
         q.t_done = now;
-        s->results_bytes += sizeof(int32_t) * n;
+        s->results_bytes += (q.parents ? 2 : 1) * sizeof(int32_t) * n;
         ++s->completed;
         s->lat_us.push_back(std::chrono::duration<double, std::micro>(now - q.t_submit).count());
     }
@@ -824,9 +846,10 @@ bool launch_iteration(bfs_server* s, ServeGraph* sg) {
     // admission into free lanes, while the results would fit in the budget
     int nadm = 0;
     unsigned long long mask = 0;
-    const int64_t row = 4 * sg->g->L.n;
     for (int r = 0; r < sg->lanes && !sg->pending.empty(); ++r) {
         if (sg->running & (1ull << r)) continue;
+        // the result of a lane: its level row (and parent row)
+        const int64_t row = (s->req[sg->pending.front()].parents ? 8 : 4) * sg->g->L.n;
         if (s->used + s->results_bytes + row > s->budget) break;     // wait for results to be collected
         const int64_t t = sg->pending.front();
         sg->pending.pop_front();
@@ -837,6 +860,8 @@ bool launch_iteration(bfs_server* s, ServeGraph* sg) {
         sg->running |= 1ull << r;
         sg->h_admit[nadm] = r;
         sg->h_admit[64 + nadm] = q.root;
+        sg->h_admit[128 + nadm] = q.parents ? 1 : 0;
+        sg->lane_parents[r] = q.parents;
         mask |= 1ull << r;
         ++nadm;
     }
@@ -844,11 +869,11 @@ bool launch_iteration(bfs_server* s, ServeGraph* sg) {
     MsState* S = sg->g->ms->state.as<MsState>();
     if (nadm) {
         int32_t* d = sg->admit.as<int32_t>();
-        if (cudaMemcpyAsync(d, sg->h_admit, sizeof(int32_t) * 128, cudaMemcpyHostToDevice, sg->stream) != cudaSuccess) {
+        if (cudaMemcpyAsync(d, sg->h_admit, sizeof(int32_t) * 192, cudaMemcpyHostToDevice, sg->stream) != cudaSuccess) {
             lk.unlock(); fail(s, "admission copy failed"); return false;
         }
         ms_admit_clear<<<ms_sm_count() * 4, kMT, 0, sg->stream>>>(S, mask, d, nadm);
-        ms_admit_roots<<<1, 64, 0, sg->stream>>>(S, d, d + 64, nadm);
+        ms_admit_roots<<<1, 64, 0, sg->stream>>>(S, d, d + 64, d + 128, nadm);
     } else {
         ms_clear_alive<<<1, 1, 0, sg->stream>>>(S);
     }
@@ -951,7 +976,7 @@ bfs_status bfs_server_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id
     int lanes = s->max_lanes;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        while (lanes > 0 && s->used + layout + lane_state + 4 * n * (int64_t)lanes > s->budget) lanes /= 2;
+        while (lanes > 0 && s->used + layout + lane_state + 8 * n * (int64_t)lanes > s->budget) lanes /= 2;
     }
     if (lanes == 0) {
         delete sg;
@@ -959,11 +984,12 @@ bfs_status bfs_server_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id
         return set_error(BFS_ERR_OUT_OF_MEMORY, "graph does not fit the server's HBM budget");
     }
     sg->lanes = lanes;
-    sg->footprint = layout + lane_state + 4 * n * (int64_t)lanes;
+    sg->footprint = layout + lane_state + 8 * n * (int64_t)lanes;
     bfs_status rc = ms_ensure(g);
     if (rc == BFS_OK) rc = sg->levels.alloc(sizeof(int32_t) * n * lanes);
-    if (rc == BFS_OK) rc = sg->admit.alloc(sizeof(int32_t) * 128);
-    if (rc == BFS_OK && cudaMallocHost(reinterpret_cast<void**>(&sg->h_admit), sizeof(int32_t) * 128) != cudaSuccess)
+    if (rc == BFS_OK) rc = sg->parents.alloc(sizeof(int32_t) * n * lanes);
+    if (rc == BFS_OK) rc = sg->admit.alloc(sizeof(int32_t) * 192);
+    if (rc == BFS_OK && cudaMallocHost(reinterpret_cast<void**>(&sg->h_admit), sizeof(int32_t) * 192) != cudaSuccess)
         rc = set_error(BFS_ERR_OUT_OF_MEMORY, "pinned host allocation");
     if (rc == BFS_OK && cudaMallocHost(reinterpret_cast<void**>(&sg->h_alive), sizeof(unsigned long long) * 5) != cudaSuccess)
         rc = set_error(BFS_ERR_OUT_OF_MEMORY, "pinned host allocation");
@@ -971,7 +997,8 @@ bfs_status bfs_server_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id
         rc = set_error(BFS_ERR_CUDA, "stream creation failed");
     if (rc == BFS_OK) {
         MsState* S = g->ms->state.as<MsState>();
-        MsCall call{g->ms->roots.as<int32_t>(), lanes, 0x7fffffff, sg->levels.as<int32_t>(), nullptr};
+        MsCall call{g->ms->roots.as<int32_t>(), lanes, 0x7fffffff, sg->levels.as<int32_t>(), sg->parents.as<int32_t>(),
+                    0ull};
         if (cudaMemcpyAsync(reinterpret_cast<char*>(S) + offsetof(MsState, roots), &call, sizeof(call),
                             cudaMemcpyHostToDevice, sg->stream) != cudaSuccess)
             rc = set_error(BFS_ERR_CUDA, "state copy failed");
@@ -995,17 +1022,23 @@ bfs_status bfs_server_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id
 }
 
 bfs_status bfs_server_submit(bfs_server_t s, int32_t graph_id, int32_t root, int64_t* ticket) {
+    return bfs_server_submit_ex(s, graph_id, root, 0, ticket);
+}
+
+bfs_status bfs_server_submit_ex(bfs_server_t s, int32_t graph_id, int32_t root, int32_t flags, int64_t* ticket) {
     if (!s || !ticket) return set_error(BFS_ERR_INVALID_ARG, "NULL argument");
+    if (flags & ~BFS_QUERY_PARENTS) return set_error(BFS_ERR_INVALID_ARG, "unknown query flags 0x%x", flags);
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->failed) return set_error(BFS_ERR_CUDA, "server failed: %s", s->fail_msg);
     if (graph_id < 0 || graph_id >= (int32_t)s->graphs.size()) return set_error(BFS_ERR_NOT_FOUND, "unknown graph id %d", graph_id);
     ServeGraph* sg = s->graphs[graph_id];
     if (root < 0 || (int64_t)root >= sg->g->L.n) return set_error(BFS_ERR_INVALID_ARG, "root %d outside [0, %lld)", root, (long long)sg->g->L.n);
-    if (s->queued >= kMaxQueued) { ++s->rejected; return set_error(BFS_ERR_BUSY, "server queue is full"); }
+    if (s->queued >= s->queue_limit) { ++s->rejected; return set_error(BFS_ERR_BUSY, "server queue is full"); }
     const int64_t t = s->next_ticket++;
     Request q;
     q.graph = graph_id;
     q.root = root;
+    q.parents = (flags & BFS_QUERY_PARENTS) != 0;
     q.t_submit = std::chrono::steady_clock::now();
     s->req.emplace(t, q);
     sg->pending.push_back(t);
@@ -1013,6 +1046,14 @@ bfs_status bfs_server_submit(bfs_server_t s, int32_t graph_id, int32_t root, int
     ++s->submitted;
     *ticket = t;
     s->cv_work.notify_one();
+    return BFS_OK;
+}
+
+bfs_status bfs_server_set_queue_limit(bfs_server_t s, int64_t limit) {
+    if (!s || limit < 1 || limit > kMaxQueued)
+        return set_error(BFS_ERR_INVALID_ARG, "queue limit outside [1, %lld]", (long long)kMaxQueued);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->queue_limit = limit;
     return BFS_OK;
 }
 
@@ -1027,10 +1068,11 @@ bfs_status bfs_server_poll(bfs_server_t s, int64_t ticket, int32_t* done) {
 
 bfs_status bfs_server_wait(bfs_server_t s, int64_t ticket, int64_t timeout_us, int32_t* level, int32_t* parent) {
     if (!s) return set_error(BFS_ERR_INVALID_ARG, "NULL server");
-    if (parent) return set_error(BFS_ERR_INVALID_ARG, "the server returns levels only (parent must be NULL)");
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->req.find(ticket);
     if (it == s->req.end()) return set_error(BFS_ERR_NOT_FOUND, "unknown ticket %lld", (long long)ticket);
+    if (parent && !it->second.parents)
+        return set_error(BFS_ERR_INVALID_ARG, "request %lld was submitted without BFS_QUERY_PARENTS", (long long)ticket);
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
     while (s->req[ticket].state != 2 && !s->failed) {
         if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && s->req[ticket].state != 2)
@@ -1041,13 +1083,17 @@ bfs_status bfs_server_wait(bfs_server_t s, int64_t ticket, int64_t timeout_us, i
     s->req.erase(ticket);
     ServeGraph* sg = s->graphs[q.graph];
     const int64_t n = sg->g->L.n;
-    s->results_bytes -= sizeof(int32_t) * n;
+    s->results_bytes -= (q.parents ? 2 : 1) * sizeof(int32_t) * n;
     lk.unlock();
     bfs_status rc = BFS_OK;
     // the result was allocated stream-ordered and completed before the request
     // was marked done: copy it out and free it stream-ordered on the legacy stream
     if (level) {
         cudaError_t e = cudaMemcpyAsync(level, q.result, sizeof(int32_t) * n, cudaMemcpyDefault, 0);
+        if (e != cudaSuccess) rc = cuda_error(e, "result copy", __FILE__, __LINE__);
+    }
+    if (parent && rc == BFS_OK) {
+        cudaError_t e = cudaMemcpyAsync(parent, q.result + n, sizeof(int32_t) * n, cudaMemcpyDefault, 0);
         if (e != cudaSuccess) rc = cuda_error(e, "result copy", __FILE__, __LINE__);
     }
     cudaFreeAsync(q.result, 0);

@@ -547,6 +547,7 @@ __global__ void __launch_bounds__(kEW) enc_chunk_sums32(EncodeArgs a, ChunkSum* 
         }
         if (lane == 0) flags[q] = live ? 1 : 0;
         if (!live) continue;
+        if (lane == 0 && a.live_chunks) atomicAdd(a.live_chunks, 1ull);
         const Stage32 st = stage_chunk(a, sg, tb, tend, s_f[threadIdx.x >> 5], s_d[threadIdx.x >> 5]);
         const int ng = (int)(tend - tb);
         uint32_t cwd[32];
@@ -820,6 +821,7 @@ __global__ void __launch_bounds__(kEW64) enc_chunk_sums64(EncodeArgs a, ChunkSum
         }
         if (lane == 0) flags[q] = live ? 1 : 0;
         if (!live) continue;
+        if (lane == 0 && a.live_chunks) atomicAdd(a.live_chunks, 1ull);
         const Stage32 st = stage_chunk63(a, sg, tb, tend, s_f[threadIdx.x >> 5], s_d[threadIdx.x >> 5]);
         const int ng = (int)(tend - tb);
         uint32_t c0[33], c1[33];

@@ -26,6 +26,7 @@ STATUS = ["BFS_OK", "BFS_ERR_INVALID_ARG", "BFS_ERR_OUT_OF_MEMORY", "BFS_ERR_CUD
           "BFS_ERR_CORRUPT", "BFS_ERR_BUSY", "BFS_ERR_NOT_FOUND"]
 MODE_PLAIN, MODE_COMPRESS, MODE_COMPRESS_SIEVE = 0, 1, 2
 DIRECTION_TOP_DOWN, DIRECTION_HYBRID, DIRECTION_BOTTOM_UP = 0, 1, 2
+QUERY_PARENTS = 1
 
 
 class Options(ctypes.Structure):
@@ -44,7 +45,7 @@ class LevelStats(ctypes.Structure):
                 ("ms_compress_sieve", ctypes.c_float), ("ms_communication", ctypes.c_float),
                 ("ms_traversing", ctypes.c_float), ("ms_reducing", ctypes.c_float),
                 ("bottom_up", i32), ("ms_row_compress", ctypes.c_float), ("ms_row_fold", ctypes.c_float),
-                ("reserved", i32)]
+                ("reserved", i32), ("compress_chunks", i64), ("row_compress_chunks", i64)]
 
 
 class BatchStats(ctypes.Structure):
@@ -78,11 +79,15 @@ _SIGS = {
     "bfs_graph_set_direction": (ctypes.c_int, [vp, i32, i32, i32]),
     "bfs_graph_directory": (ctypes.c_int, [vp, i32, i32, vp, vp]),
     "bfs_run": (ctypes.c_int, [vp, i32, vp, vp, P(RunStats), vp]),
+    "bfs_check_search": (ctypes.c_int, [vp, i32, vp, vp, vp]),
+    "bfs_debug_fail_allocation": (ctypes.c_int, [i64]),
+    "bfs_server_set_queue_limit": (ctypes.c_int, [vp, i64]),
     "bfs_run_batch": (ctypes.c_int, [vp, vp, i32, vp, vp, P(BatchStats), vp]),
     "bfs_batch_autotune": (ctypes.c_int, [vp, vp, i32, vp, P(i32), P(i32), vp]),
     "bfs_server_create": (ctypes.c_int, [i64, i32, P(vp)]),
     "bfs_server_add_graph": (ctypes.c_int, [vp, vp, P(i32)]),
     "bfs_server_submit": (ctypes.c_int, [vp, i32, i32, P(i64)]),
+    "bfs_server_submit_ex": (ctypes.c_int, [vp, i32, i32, i32, P(i64)]),
     "bfs_server_poll": (ctypes.c_int, [vp, i64, P(i32)]),
     "bfs_server_wait": (ctypes.c_int, [vp, i64, i64, vp, vp]),
     "bfs_server_stats": (ctypes.c_int, [vp, P(ServerStats)]),

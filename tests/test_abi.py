@@ -55,3 +55,10 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_failure_injection_arguments_without_gpu():
+    build.build()
+    lib = native.lib()
+    assert native.STATUS[lib.bfs_debug_fail_allocation(-1)] == "BFS_ERR_INVALID_ARG"
+    assert lib.bfs_debug_fail_allocation(0) == 0

@@ -44,13 +44,16 @@ def test_reference_config_matches_the_gpu_arm():
 
 
 def test_compression_factor_is_the_mean_of_the_level_ratios():
-    """Sec. VI-A: C = (1/d) sum_i 1/C_i with C_i = raw / compressed at level i."""
+    """Sec. VI-A: C = (1/d) sum_i 1/C_i with C_i = raw / compressed at level i of
+    one search (d levels); the line reports its mean over the searches."""
     sys.path.insert(0, ROOT)
     import bench
-    exch = [{"level": 0, "wah_over_raw": 0.001}, {"level": 1, "wah_over_raw": 0.5},
-            {"level": 2, "wah_over_raw": 1.03}, {"level": 3, "wah_over_raw": None}]
-    got = bench.compression_factor(exch, 2)
-    assert got == {"symbol": "C'", "value": round((0.001 + 0.5 + 1.03) / 3, 6), "levels": 3}
-    assert bench.compression_factor(exch, 1)["symbol"] == "C"
-    assert bench.compression_factor(exch, 0) is None
+    one = [0.001, 0.5, 1.03, None]
+    two = [0.002, 0.9]
+    got = bench.compression_factor([one, two], 2)
+    want = ((0.001 + 0.5 + 1.03) / 3 + (0.002 + 0.9) / 2) / 2
+    assert got == {"symbol": "C'", "value": round(want, 6), "searches": 2, "levels_per_search": 2.5}
+    assert bench.compression_factor([one], 1)["symbol"] == "C"
+    assert bench.compression_factor([one], 0) is None
     assert bench.compression_factor([], 2) is None
+    assert bench.compression_factor([[None]], 2) is None

@@ -146,3 +146,23 @@ def test_self_loops_and_duplicates_counted_twice():
     g = oracle.csr(3, src, dst)
     assert g.degree().tolist() == [2, 5, 1]     # 0-1 twice, 1-1 self-loop twice, 1-2
     assert sorted(g.col[g.row_ptr[1]:g.row_ptr[2]].tolist()) == [0, 0, 1, 1, 2]
+
+
+def test_bounded_sample_is_a_prefix_of_the_search():
+    """oracle_bfs_sample: with an unlimited budget it is oracle_bfs_levels; with a
+    small one every level it assigns is the full search's, the assigned levels
+    form a prefix (all of levels < L, some of level L), and it scanned at least
+    the budget unless the component ended."""
+    n, src, dst = graphgen.edges(12, 16)
+    g = oracle.csr(n, src, dst)
+    root = int(graphgen.pick_roots(n, src, dst, 1)[0])
+    full = oracle.bfs_levels(g, root)
+    lv, k = oracle.bfs_sample(g, root, 1 << 62)
+    assert (lv == full).all() and k == int(g.degree()[full >= 0].sum())
+    for budget in (1, 50, 5000, 40000):
+        lv, k = oracle.bfs_sample(g, root, budget)
+        got = lv >= 0
+        assert (lv[got] == full[got]).all()
+        top = lv.max()
+        assert ((full < top) & (full >= 0) <= got).all()
+        assert k >= min(budget, int(g.degree()[full >= 0].sum()))
