@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--beta", type=int, default=24, help="hybrid: top-down again once the frontier < n / beta")
     ap.add_argument("--row-exchange", default="off", choices=["on", "off"],
                     help="the value arm's fold: off = local to the block-row (Alg. 3), on = row buffers")
+    ap.add_argument("--format", default="wah", choices=["wah", "adaptive"],
+                    help="the value arm's exchanged slices: WAH streams, or the smallest of WAH / vector / raw")
     ap.add_argument("--roots", type=int, default=0, help="override the number of roots")
     ap.add_argument("--extra-steps", type=int, default=5, help="timed steps of the row-exchange and hybrid arms")
     ap.add_argument("--no-plain", action="store_true")
@@ -409,10 +411,11 @@ def main():
     level = torch.empty(n, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def configure(mode, rowx, direction):
+    def configure(mode, rowx, direction, adaptive=None):
         g.set_mode(mode, args.wah_bits)
         g.set_row_exchange(rowx)
         g.set_direction(DIRECTIONS[direction], args.alpha, args.beta)
+        g.set_exchange_format(args.format == "adaptive" if adaptive is None else adaptive)
 
     if args.profile_run:
         # one untimed search per arm from the first root (for ncu), with the
@@ -446,11 +449,11 @@ def main():
             sts.append(st)
         return times, ms_, sts
 
-    def timed(mode, rowx, direction, steps, warmup, record=True):
+    def timed(mode, rowx, direction, steps, warmup, record=True, adaptive=None):
         """Warm-up, then `steps` timed steps (the library's CUDA-graph level loop,
         no statistics); then one recording pass (the stepwise loop with per-level
         statistics and phase events) outside the timed steps."""
-        configure(mode, rowx, direction)
+        configure(mode, rowx, direction, adaptive)
         for _ in range(warmup):
             step()
         if world > 1:
@@ -577,6 +580,25 @@ def main():
                                            validate_all(g, roots, parent, level, src_d, dst_d, n, dev, stream,
                                                         torch), "roots": len(roots)}}
             arms["hybrid"] = hy
+        if args.wah_bits == 32:
+            # the level-adaptive exchange format: every slice as the smallest of its
+            # WAH stream, sparse vector and raw bitmap
+            ad = {"format": "adaptive (WAH / sparse vector / raw bitmap per slice and level)",
+                  "steps": args.extra_steps}
+            for name, direction in (("top_down", args.direction), ("hybrid", "hybrid")):
+                if name == "hybrid" and args.direction != "top_down":
+                    continue
+                h = timed(2, value_rowx, direction, args.extra_steps, 2, record=name == "top_down",
+                          adaptive=args.format != "adaptive")
+                ad[name] = {"value": round(h["gteps"], 4), "ms_per_step": round(h["ms_per_step"], 3),
+                            "validation": {"invariant_and_min_parent_roots":
+                                           validate_all(g, roots, parent, level, src_d, dst_d, n, dev, stream,
+                                                        torch), "roots": len(roots)}}
+                if h["stats"]:
+                    ex_b = sum(ls["wah_bytes"] for st in h["stats"] for ls in st.levels)
+                    raw_b = sum(ls["raw_bytes"] for st in h["stats"] for ls in st.levels)
+                    ad[name]["exchange_over_raw"] = round(ex_b / raw_b, 6) if raw_b else None
+            arms["adaptive" if args.format != "adaptive" else "wah_format"] = ad
         configure(args.mode, value_rowx, args.direction)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -641,7 +663,8 @@ def main():
         "config": workload_config(args, n, len(src), len(roots)),
         "method": {"step": "one search per root", "l2": "flushed (256 MiB write) before every search",
                    "parallelism": f"replicas x{world}",
-                   "fold": "row buffers (2D fold)" if value_rowx else "local to the block-row (Alg. 3)"},
+                   "fold": "row buffers (2D fold)" if value_rowx else "local to the block-row (Alg. 3)",
+                   "exchange_format": args.format},
         "plain_gpu": plain,
         **arms,
         "roofline": roofline,

@@ -139,6 +139,8 @@ typedef struct {
     int32_t row_exchange;
     int64_t range_size;      /* ceil(n / p) */
     int64_t nonempty_columns;/* sum over blocks of |V_{i,j}| (set directory bits) */
+    int32_t exchange_format; /* BFS_FORMAT_* */
+    int32_t direction;       /* BFS_DIRECTION_* */
 } bfs_graph_info_t;
 
 BFS_API bfs_status bfs_graph_info(bfs_graph_t g, bfs_graph_info_t *info);
@@ -170,6 +172,33 @@ BFS_API bfs_status bfs_graph_set_mode(bfs_graph_t g, int32_t mode, int32_t wah_w
  * safe while a search on `g` is running.
  */
 BFS_API bfs_status bfs_graph_set_row_exchange(bfs_graph_t g, int32_t enabled);
+
+/* Format of the exchanged column slices (bfs_graph_set_exchange_format). */
+enum {
+    BFS_FORMAT_WAH = 0,          /* every slice a WAH stream (Sec. IV; Alg. 2, 3) */
+    BFS_FORMAT_ADAPTIVE = 1      /* per slice and level the smallest of its WAH stream, sparse vector
+                                    and raw bitmap */
+};
+
+/*
+ * The level-adaptive exchange format.  Sec. II sets the bitmap against the
+ * sparse vector as the two ways to hold a frontier (Table 2: which is smaller
+ * depends on the frontier's density) and Sec. V-A notes that a sieved slice is
+ * very sparse; Alg. 1 sends the raw bitmap.  With BFS_FORMAT_ADAPTIVE every
+ * exchanged slice of the column exchange (COMPRESS and COMPRESS_SIEVE) goes,
+ * level by level, as the smallest in bytes of
+ *   0  its WAH stream (32-bit words, as with BFS_FORMAT_WAH),
+ *   1  its sparse vector: the offsets of its set bits within the slice, in
+ *      increasing order, one uint32 each,
+ *   2  its raw bitmap: ceil(bits/32) uint32 words, bit b = bit b%32 of word b/32,
+ * the lower number on a tie.  The choice is made on the device from the
+ * slice's WAH size and set-bit count; the expansion (and the bottom-up stream
+ * decode) reads all three.  The exchange trace then holds each slot's
+ * elements and, in bfs_run_stats.trace_formats, its format.  Needs 32-bit WAH
+ * words (bfs_run returns BFS_ERR_INVALID_ARG with 64-bit words).  The row
+ * buffers of the fold stay WAH.  Not safe while a search on `g` is running.
+ */
+BFS_API bfs_status bfs_graph_set_exchange_format(bfs_graph_t g, int32_t format);
 
 /* Direction of each level (bfs_graph_set_direction). */
 enum {
@@ -264,6 +293,8 @@ typedef struct {
     int64_t trace_capacity;      /* uint32 elements available in trace_words */
     int64_t *trace_counts;       /* device, capacity_levels * slots entries */
     int64_t trace_used;          /* out: uint32 elements written */
+    uint8_t *trace_formats;      /* device, capacity_levels * slots entries, or NULL: the format of
+                                    every traced slot (BFS_FORMAT_ADAPTIVE's 0 / 1 / 2; 0 otherwise) */
     /* Optional row-buffer trace (device pointers, or NULL; COMPRESS_SIEVE with the
      * row exchange on): for each level k, the row buffers of the fold packed in
      * slot order (slot = i*p + j: the WAH stream of the vertices of range i that

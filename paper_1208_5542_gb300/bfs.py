@@ -42,6 +42,7 @@ class SearchStats:
     levels: list = field(default_factory=list)      # dicts, one per exchange
     trace_words: torch.Tensor | None = None         # int32 view of the packed streams
     trace_counts: torch.Tensor | None = None        # [levels, slots] int64
+    trace_formats: torch.Tensor | None = None       # [levels, slots] uint8 (adaptive format: 0 WAH, 1 vector, 2 raw)
     trace_used: int = 0
     row_trace_words: torch.Tensor | None = None     # int32 view of the packed row buffers of the fold
     row_trace_counts: torch.Tensor | None = None    # [levels, p*p] int64
@@ -127,6 +128,12 @@ class Graph:
     def set_row_exchange(self, enabled: bool):
         check(native.lib().bfs_graph_set_row_exchange(self._h, int(bool(enabled))))
 
+    def set_exchange_format(self, adaptive: bool):
+        """Every exchanged slice as the smallest of WAH stream, sparse vector and raw
+        bitmap (True), or always WAH (False, the default)."""
+        check(native.lib().bfs_graph_set_exchange_format(self._h, native.FORMAT_ADAPTIVE if adaptive
+                                                         else native.FORMAT_WAH))
+
     def set_direction(self, policy: int, alpha: int = 14, beta: int = 24):
         """Top-down (the default), hybrid top-down / bottom-up, or bottom-up levels."""
         check(native.lib().bfs_graph_set_direction(self._h, int(policy), int(alpha), int(beta)))
@@ -181,7 +188,9 @@ class Graph:
                 rs.trace_words = _ptr(tw)
                 rs.trace_capacity = int(trace_capacity)
                 rs.trace_counts = _ptr(tc)
-                out_stats.trace_words, out_stats.trace_counts = tw, tc
+                tf = torch.zeros((max_levels, slots), dtype=torch.uint8, device="cuda")
+                rs.trace_formats = _ptr(tf)
+                out_stats.trace_words, out_stats.trace_counts, out_stats.trace_formats = tw, tc, tf
             if row_trace_capacity:
                 rw = torch.zeros(int(row_trace_capacity), dtype=torch.int32, device="cuda")
                 rcn = torch.zeros((max_levels, self.p * self.p), dtype=torch.int64, device="cuda")
@@ -200,6 +209,7 @@ class Graph:
             out_stats.row_trace_used = int(rs.row_trace_used)
             if out_stats.trace_counts is not None:
                 out_stats.trace_counts = out_stats.trace_counts[: out_stats.n_levels]
+                out_stats.trace_formats = out_stats.trace_formats[: out_stats.n_levels]
             if out_stats.row_trace_counts is not None:
                 out_stats.row_trace_counts = out_stats.row_trace_counts[: out_stats.n_levels]
         return parent, level, out_stats

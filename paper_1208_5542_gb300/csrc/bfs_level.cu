@@ -103,6 +103,7 @@ struct LevelArgs {
     int64_t* chunk_base;
     int64_t chunks_per_slot;
     int64_t* slot_unit_base;            // p*p + 1: WAH units of slot s are [base[s], base[s+1])
+    const uint8_t* fmt;                 // per-slot format of the level-adaptive exchange, or nullptr (WAH)
     // work distribution (per level)
     unsigned long long* row_next;       // p
     unsigned long long* row_piece_count;// p
@@ -515,24 +516,37 @@ __global__ void __launch_bounds__(kXT, 1) expand_wah(LevelArgs a) {
         const int64_t count = a.xcount[stream];
         const int64_t xw = k * 32 + lane_id();
         const W y = (xw < count) ? in[xw] : W(0);
-        // groups of a slot fit in 32 bits (n < 2^31)
-        const uint32_t glen = (xw < count) ? (uint32_t)word_groups<W>(y) : 0u;
-        const uint32_t gincl = warp_incl_sum(glen);
-        const int64_t gs = a.chunk_base[stream * a.chunks_per_slot + k] + (int64_t)(gincl - glen);
-        // per lane: its word's vertices as (first vertex of the word, bits in
-        // group order; a 1-fill is a run, marked by an empty bit pattern)
+        // per lane: its element's vertices as (first vertex, bits in group
+        // order; a 1-fill is a run, marked by an empty bit pattern)
         uint32_t c = 0;
         W wbits = W(0);
         int64_t wbase = 0;
-        if (xw < count) {
-            if (gs < G) {
-                wbase = gs * GB;
-                if (is_fill<W>(y)) c = (y & T::VAL) ? (uint32_t)(glen * GB) : 0u;
-                else { wbits = T::from_payload(y); c = (uint32_t)T::popc(wbits); }
-            } else if (r > 0) {
-                wbase = G * GB;
-                wbits = T::from_active(y, r);                     // the active word
-                c = (uint32_t)T::popc(wbits);
+        const int fm = a.fmt ? (int)a.fmt[stream] : FMT_WAH;
+        if (fm == FMT_WAH) {
+            // groups of a slot fit in 32 bits (n < 2^31)
+            const uint32_t glen = (xw < count) ? (uint32_t)word_groups<W>(y) : 0u;
+            const uint32_t gincl = warp_incl_sum(glen);
+            const int64_t gs = a.chunk_base[stream * a.chunks_per_slot + k] + (int64_t)(gincl - glen);
+            if (xw < count) {
+                if (gs < G) {
+                    wbase = gs * GB;
+                    if (is_fill<W>(y)) c = (y & T::VAL) ? (uint32_t)(glen * GB) : 0u;
+                    else { wbits = T::from_payload(y); c = (uint32_t)T::popc(wbits); }
+                } else if (r > 0) {
+                    wbase = G * GB;
+                    wbits = T::from_active(y, r);                     // the active word
+                    c = (uint32_t)T::popc(wbits);
+                }
+            }
+        } else if (xw < count) {
+            const uint32_t e = (uint32_t)y;
+            if (fm == FMT_LIST) {                                     // one vertex offset
+                wbase = e;
+                c = 1;
+            } else {                                                  // 32 bits of the raw slice
+                wbase = xw * 32;
+                wbits = (W)e;
+                c = (uint32_t)__popc(e);
             }
         }
         const uint32_t cincl = warp_incl_sum(c);
@@ -881,10 +895,18 @@ __global__ void __launch_bounds__(kNT) decode_streams(LevelArgs a) {
         const int64_t count = a.xcount[s];
         const int64_t xw = k * 32 + lane_id();
         const W y = (xw < count) ? in[xw] : W(0);
+        uint32_t* dst = a.gbits;
+        const int fm = a.fmt ? (int)a.fmt[s] : FMT_WAH;
+        if (fm != FMT_WAH) {                     // a vertex offset, or 32 bits of the raw slice
+            if (xw < count) {
+                if (fm == FMT_LIST) or_bits<uint32_t>(dst, jb + (int64_t)(uint32_t)y, 1u);
+                else or_bits<uint32_t>(dst, jb + 32 * xw, (uint32_t)y);
+            }
+            continue;
+        }
         const uint32_t glen = (xw < count) ? (uint32_t)word_groups<W>(y) : 0u;
         const uint32_t gincl = warp_incl_sum(glen);
         const int64_t gs = a.chunk_base[s * a.chunks_per_slot + k] + (int64_t)(gincl - glen);
-        uint32_t* dst = a.gbits;
         bool one = false;
         if (xw < count) {
             if (gs < G) {
@@ -1173,7 +1195,8 @@ __global__ void set_root(int32_t* level, int32_t* parent, uint32_t* pi, uint32_t
 // ctr[cursor] is the trace's fill, kept from level to level.
 __global__ void __launch_bounds__(kNT) trace_offsets(const int64_t* __restrict__ counts, int nslots, int u32_per_word,
                                                      int64_t* __restrict__ slot_off, int64_t* __restrict__ trace_counts,
-                                                     unsigned long long* ctr, int cursor, int64_t capacity) {
+                                                     unsigned long long* ctr, int cursor, int64_t capacity,
+                                                     const uint8_t* fmt, uint8_t* trace_fmt) {
     __shared__ unsigned long long red[kNT / 32 + 1];
     const unsigned long long used = ctr[cursor];
     unsigned long long carry = 0;
@@ -1185,6 +1208,7 @@ __global__ void __launch_bounds__(kNT) trace_offsets(const int64_t* __restrict__
         if (s < nslots) {
             slot_off[s] = (int64_t)(used + carry + ex);
             trace_counts[s] = counts[s];
+            if (trace_fmt) trace_fmt[s] = fmt ? fmt[s] : (uint8_t)FMT_WAH;
         }
         carry += tot;
     }
@@ -1335,6 +1359,7 @@ bfs_status ensure_workspace_once(bfs_graph* g) {
     BFS_TRY(W.xcount.alloc(sizeof(int64_t) * p2));
     BFS_TRY(W.chunk_base.alloc(sizeof(int64_t) * p2 * W.chunks_per_slot));
     BFS_TRY(W.units.alloc(sizeof(int64_t) * (p2 + 1)));              // slot unit bases
+    BFS_TRY(W.xfmt.alloc((size_t)p2));
     W.enc_cps = parallel_encode_chunks(L.nb, 32);                       // 31-bit groups: the most chunks
     BFS_TRY(W.enc_sums.alloc(parallel_encode_sum_bytes() * p2 * W.enc_cps));
     BFS_TRY(W.enc_bases.alloc(parallel_encode_base_bytes() * p2 * W.enc_cps));
@@ -1395,6 +1420,7 @@ void free_workspace(bfs_graph* g) {
     W.tblk_dirty = false;
     W.enc_sums.release(); W.enc_bases.release(); W.enc_flags.release(); W.enc_done.release(); W.ctl.release();
     W.gbits.release();
+    W.xfmt.release();
     for (auto& c : W.sgraph) {
         if (c.exec) cudaGraphExecDestroy(c.exec);
         if (c.graph) cudaGraphDestroy(c.graph);
@@ -1488,6 +1514,9 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         W.tblk_dirty = false;
     }
     const int64_t row_cap = (wbits == 32) ? L.nb / 31 + 2 : L.nb / 63 + 2;
+    const bool adaptive = g->adaptive && mode != BFS_MODE_PLAIN;
+    if (adaptive && wbits != 32)
+        return set_error(BFS_ERR_INVALID_ARG, "the level-adaptive exchange format needs 32-bit WAH words");
     const bool row_tracing = stats && rowx && stats->row_trace_words && stats->row_trace_counts;
     const size_t dyn = win ? window_bytes(W.win_words) : 0;
     // bottom-up levels: degrees (direction choice) and the decoded streams
@@ -1579,6 +1608,9 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     ea.plan_done = W.enc_done.as<unsigned int>();
     ea.frontier_words = W.bm_words;
     if (rowx) ea.slot_bits = W.rowlive.as<uint8_t>();    // the row encoder skips blocks that expanded nothing
+    ea.adaptive = adaptive ? 1 : 0;
+    ea.fmt = W.xfmt.as<uint8_t>();
+    a.fmt = adaptive ? W.xfmt.as<uint8_t>() : nullptr;
 
     // the row encoder: slot s = i*p + j is the partial t_{i,j} (the directory
     // operand, consumed and cleared) sieved by not(pi_i) (the frontier operand
@@ -1651,7 +1683,9 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
                 const int u32pw = wbits / 32;
                 trace_offsets<<<1, kNT, 0, s>>>(W.xcount.as<int64_t>(), nslots, u32pw, slot_off.as<int64_t>(),
                                                 stats->trace_counts + (int64_t)k * nslots, ctr, C_TRACE_USED,
-                                                stats->trace_capacity);
+                                                stats->trace_capacity, a.fmt,
+                                                stats->trace_formats ? stats->trace_formats + (int64_t)k * nslots
+                                                                     : nullptr);
                 dim3 tg(8, std::min(nslots, 65535));
                 trace_copy<<<tg, kNT, 0, s>>>(W.xbuf.as<uint32_t>(), slot_cap * u32pw, W.xcount.as<int64_t>(), nslots,
                                               u32pw, slot_off.as<int64_t>(), stats->trace_words, stats->trace_capacity);
@@ -1687,7 +1721,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
                 const int u32pw = wbits / 32;
                 trace_offsets<<<1, kNT, 0, s>>>(W.rowcount.as<int64_t>(), (int)p2, u32pw, slot_off.as<int64_t>(),
                                                 stats->row_trace_counts + (int64_t)k * p2, ctr, C_ROW_TRACE_USED,
-                                                stats->row_trace_capacity);
+                                                stats->row_trace_capacity, nullptr, nullptr);
                 dim3 tg(8, (unsigned)std::min<int64_t>(p2, 65535));
                 trace_copy<<<tg, kNT, 0, s>>>(static_cast<const uint32_t*>(W.rowbuf.ptr), row_cap * u32pw,
                                               W.rowcount.as<int64_t>(), (int)p2, u32pw, slot_off.as<int64_t>(),
@@ -1721,7 +1755,8 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         SearchGraph* sg = nullptr;
         for (auto& c : W.sgraph)
             if (c.exec && c.mode == mode && c.wbits == wbits && c.rowx == (int)rowx &&
-                c.bottom_up == (int)bu_kernels && c.parent == parent && c.level == level)
+                c.bottom_up == (int)bu_kernels && c.adaptive == (int)adaptive && c.parent == parent &&
+                c.level == level)
                 sg = &c;
         if (!sg) {
             SearchGraph& c = W.sgraph[W.sgraph_next];
@@ -1762,6 +1797,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             c.wbits = wbits;
             c.rowx = rowx ? 1 : 0;
             c.bottom_up = bu_kernels ? 1 : 0;
+            c.adaptive = adaptive ? 1 : 0;
             c.parent = parent;
             c.level = level;
             sg = &c;

@@ -678,7 +678,7 @@ bfs_status bfs_graph_footprint(bfs_graph_t g, int64_t* bytes) {
     b += (int64_t)(W.pi.bytes + W.fa.bytes + W.fb.bytes + W.fsum.bytes + W.xbuf.bytes + W.xcount.bytes +
                    W.chunk_base.bytes + W.units.bytes + W.counters.bytes + W.tmp_parent.bytes + W.tmp_level.bytes +
                    W.pieces.bytes + W.level_scratch.bytes + W.row_meta.bytes + W.tblk.bytes + W.rowbuf.bytes +
-                   W.rowcount.bytes + W.rowfirst.bytes + W.rowlive.bytes + W.enc_sums.bytes + W.enc_bases.bytes + W.enc_flags.bytes +
+                   W.rowcount.bytes + W.rowfirst.bytes + W.rowlive.bytes + W.xfmt.bytes + W.enc_sums.bytes + W.enc_bases.bytes + W.enc_flags.bytes +
                    W.enc_done.bytes + W.gbits.bytes);
     *bytes = b;
     return BFS_OK;
@@ -694,6 +694,8 @@ bfs_status bfs_graph_info(bfs_graph_t g, bfs_graph_info_t* info) {
     info->wah_word_bits = g->wah_bits;
     info->range_size = g->L.nb;
     info->row_exchange = g->row_exchange;
+    info->exchange_format = g->adaptive ? BFS_FORMAT_ADAPTIVE : BFS_FORMAT_WAH;
+    info->direction = g->direction;
     info->nonempty_columns = g->L.nnzc_total;
     return BFS_OK;
 }
@@ -714,6 +716,16 @@ bfs_status bfs_graph_set_row_exchange(bfs_graph_t g, int32_t enabled) {
     if (g->busy.load()) return set_error(BFS_ERR_BUSY, "graph is in use");
     std::lock_guard<std::mutex> lk(g->mu);
     g->row_exchange = enabled ? 1 : 0;
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_set_exchange_format(bfs_graph_t g, int32_t format) {
+    if (!g) return set_error(BFS_ERR_INVALID_ARG, "graph is NULL");
+    if (format != BFS_FORMAT_WAH && format != BFS_FORMAT_ADAPTIVE)
+        return set_error(BFS_ERR_INVALID_ARG, "unknown exchange format %d", format);
+    if (g->busy.load()) return set_error(BFS_ERR_BUSY, "graph is in use");
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->adaptive = format == BFS_FORMAT_ADAPTIVE ? 1 : 0;
     return BFS_OK;
 }
 

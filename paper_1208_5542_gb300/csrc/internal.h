@@ -105,7 +105,7 @@ enum Counter : int {
 struct SearchGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int mode = -1, wbits = 0, rowx = 0, bottom_up = 0;
+    int mode = -1, wbits = 0, rowx = 0, bottom_up = 0, adaptive = 0;
     int32_t* parent = nullptr;
     int32_t* level = nullptr;
 };
@@ -134,6 +134,7 @@ struct Workspace {
     DevBuf enc_done;             // slots finished by the encoder's scan
     DevBuf ctl;                  // the level values kept on the device
     DevBuf gbits;                // exchanged streams decoded into one bitmap (bottom-up levels)
+    DevBuf xfmt;                 // per-slot format of the level-adaptive exchange
     SearchGraph sgraph[2];       // level loops as CUDA graphs, most recent configurations
     int sgraph_next = 0;
     int64_t enc_cps = 0;         // encoder chunks per slot
@@ -158,6 +159,7 @@ struct bfs_graph {
     int autotune = 0;            // 1: the first bfs_run_batch picks the batch launch shape
     bool batch_tuned = false;
     int row_exchange = 0;
+    int adaptive = 0;            // level-adaptive exchange format (bfs_graph_set_exchange_format)
     int symmetric = 0;           // built with symmetrize = 1: in-neighbours = out-neighbours
     int direction = BFS_DIRECTION_TOP_DOWN;
     int alpha = 14, beta = 24;   // switch thresholds of the hybrid
@@ -206,6 +208,10 @@ struct EncodeArgs {
     const int32_t* skip;        // or nullptr: the passes do nothing while *skip != 0 (the counts
                                 //   are set to 0)
     unsigned long long* live_chunks;   // or nullptr: chunks the passes read are counted here
+    int adaptive;               // 1: each slot goes as the smallest of WAH stream, sparse vector of
+                                //    set-bit offsets and raw bitmap (32-bit words only); the scan
+                                //    writes the choice to fmt[s] and counts[s] = its elements
+    uint8_t* fmt;               // per-slot format (SliceFormat), with adaptive
     uint8_t* slot_bits;         // or nullptr: the scan writes 1 for a slot whose stream carries a set bit
     const uint8_t* slot_live;   // or nullptr: a slot with slot_live[s] == 0 is all zero (not read)
 };

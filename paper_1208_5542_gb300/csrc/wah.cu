@@ -282,12 +282,14 @@ struct ChunkSum {
     uint32_t heads;
     uint32_t types;        // first type | last type << 8
     int64_t last_head;     // group index of the chunk's last head
+    uint32_t ones;         // set bits of the chunk (adaptive format only)
 };
 struct ChunkBase {
     int64_t words;         // index of the next word to open at the chunk's first group
     int64_t run_start;     // start group of the run open before the chunk
     int32_t prev_type;     // type of the group before the chunk (-1 at the slot start)
     int32_t next_type;     // type of the group after the chunk (G_NONE at the slot end)
+    int64_t ones_before;   // set bits of the slot before the chunk (adaptive format only)
 };
 
 
@@ -324,6 +326,7 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
         cs.heads = 1;                                   // an all-zero chunk: one zero run
         cs.types = G_ZERO | (G_ZERO << 8);
         cs.last_head = c * kTile;
+        cs.ones = 0;
         return cs;
     };
     // Lane l takes chunks [l*K, (l+1)*K) in order.  Pass 1: the lane's summary
@@ -346,13 +349,21 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
     const int64_t c_lo = (int64_t)lane * K, c_hi = (c_lo + K < nch) ? c_lo + K : nch;
     Agg mine{0, -1, -1, -1};
     bool bits = false;                                  // a chunk of the lane holds a set bit
+    int64_t my_ones = 0;                                // set bits of the lane's chunks (adaptive)
     for (int64_t c = c_lo; c < c_hi; ++c) {
         const ChunkSum cs = sum_of(c);
         Agg one{(int64_t)cs.heads, cs.last_head, (int)(cs.types & 0xff), (int)((cs.types >> 8) & 0xff)};
         mine = combine(mine, one);
         bits |= !(cs.heads == 1 && (cs.types & 0xff) == G_ZERO);   // not one zero run
+        if (a.adaptive) my_ones += cs.ones;
     }
     bits = __any_sync(0xffffffffu, bits);
+    int64_t ones_before = 0, ones_total = 0;
+    if (a.adaptive) {
+        const int64_t oi = warp_incl_sum(my_ones);
+        ones_before = oi - my_ones;
+        ones_total = __shfl_sync(0xffffffffu, oi, 31);
+    }
     Agg incl = mine;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -369,6 +380,23 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
     before_me.f = __shfl_up_sync(0xffffffffu, incl.f, 1);
     before_me.l = __shfl_up_sync(0xffffffffu, incl.l, 1);
     if (lane == 0) before_me = Agg{0, -1, -1, -1};
+    // the trailing r bits of the slot (every lane), and the format of the slot
+    W y = W(0);
+    if (r > 0) {
+        const uint64_t pos = (uint64_t)(sg.src0 + G * GB);
+        y = T::tail(a.frontier, pos, r);
+        if (a.invert_frontier) y = ~y & (W)((W(1) << r) - W(1));
+        if (sg.dirb && y) y &= T::tail(sg.dirb, (uint64_t)(G * GB), r);
+    }
+    const int64_t wah_total = __shfl_sync(0xffffffffu, incl.w, 31) + (r > 0 ? 1 : 0);
+    int fm = FMT_WAH;
+    if (a.adaptive) {
+        // the smallest in bytes, the lower format on a tie (every element is 4 bytes)
+        const int64_t list_total = ones_total + T::popc(y), raw_total = (sg.nbits + 31) >> 5;
+        fm = (wah_total <= list_total && wah_total <= raw_total) ? FMT_WAH
+             : (list_total <= raw_total ? FMT_LIST : FMT_RAW);
+    }
+    if (fm != FMT_WAH) ub = nullptr;                    // no WAH units in this slot
     int64_t words = before_me.w, hmax = before_me.h;
     int prev_last = before_me.l;
     for (int64_t c = c_lo; c < c_hi; ++c) {
@@ -383,12 +411,14 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
         cb.prev_type = prev_last;
         const int nxt = (c + 1 < nch) ? (int)(sum_of(c + 1).types & 0xff) : G_NONE;
         cb.next_type = nxt;
+        cb.ones_before = ones_before;
+        if (a.adaptive) ones_before += sum_of(c).ones;
         bases[(int64_t)s * cps + c] = cb;
         if (a.chunk_first) {                // where a decoder of this chunk alone starts
             a.chunk_first[2 * ((int64_t)s * cps + c)] = merge ? cb.words - 1 : cb.words;
             a.chunk_first[2 * ((int64_t)s * cps + c) + 1] = merge ? cb.run_start : c * kTile;
         }
-        if (!flags[(int64_t)s * cps + c]) {
+        if (!flags[(int64_t)s * cps + c] && fm == FMT_WAH) {
             // an all-zero chunk: its zero run opens a word here unless it merges
             if (!merge && ub && (cb.words & 31) == 0) ub[cb.words >> 5] = c * kTile;
             if (nxt != G_ZERO) {     // the run ends at the chunk's last group
@@ -405,20 +435,25 @@ __global__ void enc_chunk_scan(EncodeArgs a, const ChunkSum* sums, const uint8_t
     if (lane == 0) {
         int64_t total = words;
         if (r > 0) {
-            const uint64_t pos = (uint64_t)(sg.src0 + G * GB);
-            W y = T::tail(a.frontier, pos, r);
-            if (a.invert_frontier) y = ~y & (W)((W(1) << r) - W(1));
-            if (sg.dirb && y) y &= T::tail(sg.dirb, (uint64_t)(G * GB), r);
             if (a.dir_clear) {              // the tail words no chunk of the write pass owns
                 uint32_t* d = a.dir_clear + (int64_t)s * a.dir_stride;
                 for (int64_t w = (G * GB + 31) >> 5; w < (sg.nbits + 31) >> 5; ++w) d[w] = 0u;
             }
             if (setbits && y) atomicAdd(setbits, (unsigned long long)T::popc(y));
-            if (ub && (total & 31) == 0) ub[total >> 5] = G;
-            out[total++] = T::to_active(y, r);
+            if (fm == FMT_WAH) {
+                if (ub && (total & 31) == 0) ub[total >> 5] = G;
+                out[total++] = T::to_active(y, r);
+            }
             bits |= y != W(0);
         }
+        if (fm == FMT_LIST) {               // the offsets of the trailing bits close the vector
+            total = ones_total;
+            for (W x = y; x; x &= x - W(1)) out[total++] = (W)(G * GB + T::select(x, 0));
+        } else if (fm == FMT_RAW) {
+            total = (sg.nbits + 31) >> 5;   // written by enc_raw32
+        }
         a.counts[s] = total;
+        if (a.fmt) a.fmt[s] = (uint8_t)fm;
         if (a.slot_bits) a.slot_bits[s] = bits ? 1 : 0;
         if (a.wah_words) atomicAdd(a.wah_words, (unsigned long long)total);
     }
@@ -511,6 +546,26 @@ __device__ __forceinline__ int mask_type(uint32_t zm, uint32_t om, int i) {
     return ((zm >> i) & 1u) ? G_ZERO : (((om >> i) & 1u) ? G_ONE : G_LIT);
 }
 
+// Set bits of the lane's valid groups (ng groups in the chunk): its 31 words,
+// the last lane's cut at the chunk end.
+__device__ __forceinline__ uint32_t lane_popc(const uint32_t (&c)[32], int ng) {
+    const int nv = ng - 32 * (int)lane_id();
+    uint32_t cnt = 0;
+    if (nv >= 32) {
+#pragma unroll
+        for (int k = 0; k < 31; ++k) cnt += __popc(c[k]);
+    } else if (nv > 0) {
+        const int nbits = nv * 31;
+#pragma unroll
+        for (int k = 0; k < 31; ++k) {
+            const int left = nbits - 32 * k;
+            const uint32_t m = left >= 32 ? 0xffffffffu : (left > 0 ? (1u << left) - 1u : 0u);
+            cnt += __popc(c[k] & m);
+        }
+    }
+    return cnt;
+}
+
 __global__ void __launch_bounds__(kEW) enc_chunk_sums32(EncodeArgs a, ChunkSum* sums, uint8_t* flags, int64_t cps,
                                                         unsigned long long* setbits) {
     if (a.skip && *a.skip) return;
@@ -552,26 +607,13 @@ __global__ void __launch_bounds__(kEW) enc_chunk_sums32(EncodeArgs a, ChunkSum* 
         const int ng = (int)(tend - tb);
         uint32_t cwd[32];
         lane_cwords(st, cwd);
-        // set bits of the lane's groups (a statistic, when asked for): its 31
-        // words, the last lane's cut at the chunk end
-        if (setbits) {
-            const int nv = ng - 32 * lane;
-            if (nv >= 32) {
-                uint32_t cnt = 0;
-#pragma unroll
-                for (int k = 0; k < 31; ++k) cnt += __popc(cwd[k]);
-                ones += cnt;
-            } else if (nv > 0) {
-                const int nbits = nv * 31;
-                uint32_t cnt = 0;
-#pragma unroll
-                for (int k = 0; k < 31; ++k) {
-                    const int left = nbits - 32 * k;
-                    const uint32_t m = left >= 32 ? 0xffffffffu : (left > 0 ? (1u << left) - 1u : 0u);
-                    cnt += __popc(cwd[k] & m);
-                }
-                ones += cnt;
-            }
+        // set bits of the lane's groups (a statistic when asked for, and the
+        // size of the sparse vector with the adaptive format): its 31 words,
+        // the last lane's cut at the chunk end
+        uint32_t lane_ones = 0;
+        if (setbits || a.adaptive) {
+            lane_ones = lane_popc(cwd, ng);
+            ones += lane_ones;
         }
         uint32_t zm, om, vm;
         lane_masks(cwd, ng, zm, om, vm);
@@ -585,11 +627,13 @@ __global__ void __launch_bounds__(kEW) enc_chunk_sums32(EncodeArgs a, ChunkSum* 
         const int lastl = (ng - 1) >> 5;                       // the lane holding the chunk's last group
         const int lastty = mask_type(__shfl_sync(0xffffffffu, zm, lastl), __shfl_sync(0xffffffffu, om, lastl),
                                      (ng - 1) & 31);
+        const uint32_t chunk_ones = a.adaptive ? warp_sum(lane_ones) : 0u;
         if (lane == 0) {
             ChunkSum cs;
             cs.heads = (uint32_t)heads;
             cs.types = (uint32_t)mask_type(zm, om, 0) | ((uint32_t)lastty << 8);
             cs.last_head = lh >= 0 ? tb + lh : -1;
+            cs.ones = chunk_ones;
             sums[q] = cs;
         }
         __syncwarp();           // the staging buffers are reused by the next chunk
@@ -619,6 +663,8 @@ __global__ void __launch_bounds__(kEW) enc_chunk_write32(EncodeArgs a, const Chu
     for (int64_t q = wid; q < n; q += nw) {
         if (!flags[q]) continue;
         const int s = (int)((uint32_t)q / (uint32_t)cps);          // slots x chunks fit in 32 bits
+        const int fm = a.adaptive ? (int)a.fmt[s] : FMT_WAH;
+        if (fm == FMT_RAW) continue;                                // enc_raw32 writes the raw words
         const int64_t c = (int64_t)((uint32_t)q - (uint32_t)s * (uint32_t)cps);
         const SlotGeom sg = slot_geom(a, s);
         const int64_t G = sg.nbits / 31;
@@ -632,6 +678,27 @@ __global__ void __launch_bounds__(kEW) enc_chunk_write32(EncodeArgs a, const Chu
         uint32_t cwd[32];
         lane_cwords(st, cwd);
         if (a.dir_clear) clear_consumed(a, s, (31 * tb) >> 5, (31 * tend + 31) >> 5, st.d);
+        if (fm == FMT_LIST) {
+            // the sparse vector: every set bit's offset in the slice, in order; the
+            // lane's bits start at bit 31 * (tb + 32 * lane) of the slice
+            const uint32_t mine = lane_popc(cwd, ng);
+            const uint32_t incl = warp_incl_sum(mine);
+            int64_t at = cb.ones_before + (int64_t)(incl - mine);
+            const int nv = ng - 32 * lane;
+            const int nbits = nv >= 32 ? 992 : (nv > 0 ? nv * 31 : 0);
+            const uint32_t base = (uint32_t)(31 * (tb + 32 * lane));
+#pragma unroll
+            for (int k = 0; k < 31; ++k) {
+                const int left = nbits - 32 * k;
+                uint32_t x = cwd[k] & (left >= 32 ? 0xffffffffu : (left > 0 ? (1u << left) - 1u : 0u));
+                while (x) {
+                    out[at++] = base + 32u * (uint32_t)k + (uint32_t)(__ffs(x) - 1);
+                    x &= x - 1u;
+                }
+            }
+            __syncwarp();
+            continue;
+        }
         __syncwarp();           // the frontier buffer now takes the output words
         uint32_t zm, om, vm;
         lane_masks(cwd, ng, zm, om, vm);
@@ -945,6 +1012,27 @@ __global__ void __launch_bounds__(kEW64) enc_chunk_write64(EncodeArgs a, const C
     }
 }
 
+// The raw bitmap of every slot whose adaptive format is FMT_RAW: word w =
+// bits 32w .. 32w+31 of the slice (the frontier at the slot's range, sieved by
+// the slot's directory), bits past the slice cleared.
+__global__ void __launch_bounds__(kNT) enc_raw32(EncodeArgs a) {
+    if (a.skip && *a.skip) return;
+    for (int s = blockIdx.y; s < a.nslots; s += gridDim.y) {
+        if (a.fmt[s] != FMT_RAW) continue;
+        const SlotGeom sg = slot_geom(a, s);
+        const int64_t words = (sg.nbits + 31) >> 5;
+        uint32_t* out = static_cast<uint32_t*>(a.out) + (int64_t)s * a.slot_cap;
+        for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < words;
+             w += (int64_t)gridDim.x * blockDim.x) {
+            uint32_t x = bits32_at(a.frontier, (uint64_t)(sg.src0 + 32 * w));
+            if (sg.dirb) x &= __ldg(sg.dirb + w);
+            const int64_t left = sg.nbits - 32 * w;
+            if (left < 32) x &= (1u << left) - 1u;
+            out[w] = x;
+        }
+    }
+}
+
 // ------------------------------------------------------- standalone decode --
 // One CTA decodes the stream into the zeroed output (cta_wah_decode_or);
 // malformed streams set *err.
@@ -977,10 +1065,15 @@ bfs_status launch_wah_encode_parallel(const EncodeArgs& a, int wah_bits, void* s
     ChunkSum* cs = static_cast<ChunkSum*>(sums);
     ChunkBase* cb = static_cast<ChunkBase*>(bases);
     uint8_t* fl = static_cast<uint8_t*>(flags);
+    if (a.adaptive && (wah_bits != 32 || !a.fmt)) return set_error(BFS_ERR_INVALID_ARG, "adaptive format needs 32-bit words");
     if (wah_bits == 32) {
         enc_chunk_sums32<<<grid, kEW, 0, st>>>(a, cs, fl, cps, setbits);
         enc_chunk_scan<uint32_t><<<a.nslots, 32, 0, st>>>(a, cs, fl, cb, cps, setbits);
         enc_chunk_write32<<<grid, kEW, 0, st>>>(a, cb, fl, cps);
+        if (a.adaptive) {
+            dim3 rg(8, (unsigned)std::min(a.nslots, 65535));
+            enc_raw32<<<rg, kNT, 0, st>>>(a);
+        }
     } else {
         enc_chunk_sums64<<<grid * 2, kEW64, 0, st>>>(a, cs, fl, cps, setbits);
         enc_chunk_scan<unsigned long long><<<a.nslots, 32, 0, st>>>(a, cs, fl, cb, cps, setbits);

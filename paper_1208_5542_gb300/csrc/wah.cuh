@@ -20,6 +20,11 @@ enum GroupType : int { G_ZERO = 0, G_ONE = 1, G_LIT = 2, G_NONE = 3 };
 // unit of the chunk index it records for decoders of one chunk).
 constexpr int kEncChunkGroups = 1024;
 
+// Formats of an exchanged slice under the level-adaptive exchange (the
+// smallest of the three; ties to the lower number): its WAH stream (Sec. IV),
+// its sparse vector of set-bit offsets (Sec. II, Table 2), its raw bitmap.
+enum SliceFormat : int { FMT_WAH = 0, FMT_LIST = 1, FMT_RAW = 2 };
+
 // Position of the set bit of rank k in x (k = 0 is the lowest set bit),
 // by halving on popcounts; k must be < popc(x).
 __device__ __forceinline__ int select32(uint32_t v, int k) {

@@ -27,6 +27,7 @@ STATUS = ["BFS_OK", "BFS_ERR_INVALID_ARG", "BFS_ERR_OUT_OF_MEMORY", "BFS_ERR_CUD
 MODE_PLAIN, MODE_COMPRESS, MODE_COMPRESS_SIEVE = 0, 1, 2
 DIRECTION_TOP_DOWN, DIRECTION_HYBRID, DIRECTION_BOTTOM_UP = 0, 1, 2
 QUERY_PARENTS = 1
+FORMAT_WAH, FORMAT_ADAPTIVE = 0, 1
 
 
 class Options(ctypes.Structure):
@@ -36,7 +37,8 @@ class Options(ctypes.Structure):
 
 class GraphInfo(ctypes.Structure):
     _fields_ = [("n_vertices", i64), ("n_entries", i64), ("p", i32), ("mode", i32), ("wah_word_bits", i32),
-                ("row_exchange", i32), ("range_size", i64), ("nonempty_columns", i64)]
+                ("row_exchange", i32), ("range_size", i64), ("nonempty_columns", i64),
+                ("exchange_format", i32), ("direction", i32)]
 
 
 class LevelStats(ctypes.Structure):
@@ -61,7 +63,8 @@ class ServerStats(ctypes.Structure):
 class RunStats(ctypes.Structure):
     _fields_ = [("capacity_levels", i32), ("n_levels", i32), ("timing", i32), ("reserved", i32),
                 ("levels", P(LevelStats)), ("trace_words", vp), ("trace_capacity", i64),
-                ("trace_counts", vp), ("trace_used", i64), ("row_trace_words", vp), ("row_trace_capacity", i64),
+                ("trace_counts", vp), ("trace_used", i64), ("trace_formats", vp),
+                ("row_trace_words", vp), ("row_trace_capacity", i64),
                 ("row_trace_counts", vp), ("row_trace_used", i64)]
 
 
@@ -77,6 +80,7 @@ _SIGS = {
     "bfs_graph_set_mode": (ctypes.c_int, [vp, i32, i32]),
     "bfs_graph_set_row_exchange": (ctypes.c_int, [vp, i32]),
     "bfs_graph_set_direction": (ctypes.c_int, [vp, i32, i32, i32]),
+    "bfs_graph_set_exchange_format": (ctypes.c_int, [vp, i32]),
     "bfs_graph_directory": (ctypes.c_int, [vp, i32, i32, vp, vp]),
     "bfs_run": (ctypes.c_int, [vp, i32, vp, vp, P(RunStats), vp]),
     "bfs_check_search": (ctypes.c_int, [vp, i32, vp, vp, vp]),
