@@ -643,7 +643,7 @@ def main():
     variants = 1 if window else 2
     launches_per_level = (0 if args.mode == 0 else 3) + 2 * variants + 2 + (4 if value_rowx else 0)
     if args.direction != "top_down":     # bottom-up expansion (+ clear and decode of the streams)
-        launches_per_level += 1 if args.mode == 0 else 3
+        launches_per_level += 1 if args.mode == 0 else (4 if args.format == "adaptive" else 3)
     gpu_launches = args.steps * sum(3 + launches_per_level * st.n_levels for st in main_arm["stats"])
 
     configs = None

@@ -897,11 +897,9 @@ __global__ void __launch_bounds__(kNT) decode_streams(LevelArgs a) {
         const W y = (xw < count) ? in[xw] : W(0);
         uint32_t* dst = a.gbits;
         const int fm = a.fmt ? (int)a.fmt[s] : FMT_WAH;
-        if (fm != FMT_WAH) {                     // a vertex offset, or 32 bits of the raw slice
-            if (xw < count) {
-                if (fm == FMT_LIST) or_bits<uint32_t>(dst, jb + (int64_t)(uint32_t)y, 1u);
-                else or_bits<uint32_t>(dst, jb + 32 * xw, (uint32_t)y);
-            }
+        if (fm == FMT_RAW) continue;             // decode_raw_slots ORs the raw slots
+        if (fm == FMT_LIST) {                    // a vertex offset
+            if (xw < count) or_bits<uint32_t>(dst, jb + (int64_t)(uint32_t)y, 1u);
             continue;
         }
         const uint32_t glen = (xw < count) ? (uint32_t)word_groups<W>(y) : 0u;
@@ -933,6 +931,30 @@ __global__ void __launch_bounds__(kNT) decode_streams(LevelArgs a) {
                 atomicOr(dst + w, mask);
             }
         }
+    }
+}
+
+// The raw slots of the level-adaptive exchange decoded into the same bitmap
+// (bottom-up levels only): word w of range j's bits is the OR over the
+// block-rows i of word w of every raw slot (i, j), one reduction per word
+// instead of one per slot.
+__global__ void __launch_bounds__(kNT) decode_raw_slots(LevelArgs a) {
+    if (!a.ctl->bu || !a.fmt) return;
+    const int p = a.p;
+    const bool sieve = a.mode == BFS_MODE_COMPRESS_SIEVE;
+    const uint32_t* xb = static_cast<const uint32_t*>(a.xbuf);
+    const int64_t wpr = (a.nb + 31) >> 5;                          // words of a range's slice
+    const int64_t total = (int64_t)p * wpr;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = x / wpr, w = x - j * wpr;
+        const int64_t jb = range_begin(a, j), jl = range_begin(a, j + 1) - jb;
+        if (32 * w >= jl) continue;
+        uint32_t acc = 0;
+        for (int i = 0; i < (sieve ? p : 1); ++i) {
+            const int64_t s = sieve ? (int64_t)i * p + j : j;
+            if (__ldg(a.fmt + s) == FMT_RAW) acc |= __ldg(xb + s * a.slot_cap + w);
+        }
+        if (acc) or_bits<uint32_t>(a.gbits, jb + 32 * w, acc);
     }
 }
 
@@ -1167,16 +1189,20 @@ __global__ void level_first(LevelCtl* c, int64_t n, int win, int policy, int alp
     c->m_u = entries - c->m_f;
 }
 
+// A search starts from nothing visited -- or, with bottom-up levels, from the
+// vertices without entries marked visited (iso): no level reaches them, and
+// the bottom-up scans skip them.
 __global__ void init_search(int32_t* __restrict__ level, int32_t* __restrict__ parent, int64_t n,
                             uint32_t* __restrict__ pi, uint32_t* __restrict__ fa, uint32_t* __restrict__ fb,
-                            int64_t words, uint8_t* __restrict__ fsum, int64_t fsum_len) {
+                            int64_t words, uint8_t* __restrict__ fsum, int64_t fsum_len,
+                            const uint32_t* __restrict__ iso) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
         level[v] = -1;
         parent[v] = -1;
     }
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < words; w += stride) {
-        pi[w] = 0u;
+        pi[w] = iso ? iso[w] : 0u;
         fa[w] = 0u;
         fb[w] = 0u;
     }
@@ -1532,7 +1558,8 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     if (stats) { stats->n_levels = 0; stats->trace_used = 0; stats->row_trace_used = 0; }
 
     init_search<<<sm_count() * 4, kNT, 0, st>>>(level, parent, L.n, W.pi.as<uint32_t>(), W.fa.as<uint32_t>(),
-                                                W.fb.as<uint32_t>(), W.bm_words, W.fsum.as<uint8_t>(), W.fsum_len);
+                                                W.fb.as<uint32_t>(), W.bm_words, W.fsum.as<uint8_t>(), W.fsum_len,
+                                                bu_kernels ? L.iso.as<uint32_t>() : nullptr);
     BFS_CUDA_TRY(cudaGetLastError());
     set_root<<<1, 1, 0, st>>>(level, parent, W.pi.as<uint32_t>(), W.fa.as<uint32_t>(), W.fsum.as<uint8_t>(), root);
     BFS_CUDA_TRY(cudaGetLastError());
@@ -1676,6 +1703,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
                 clear_gbits<<<sm_count() * 4, kNT, 0, s>>>(a);
                 if (wbits == 32) decode_streams<uint32_t><<<sm_count() * 8, kNT, 0, s>>>(a);
                 else decode_streams<unsigned long long><<<sm_count() * 8, kNT, 0, s>>>(a);
+                if (adaptive) decode_raw_slots<<<sm_count() * 8, kNT, 0, s>>>(a);
                 BFS_CUDA_TRY(cudaGetLastError());
             }
             if (host && timing) cudaEventRecord(W.ev[1], s);

@@ -250,6 +250,19 @@ __global__ void vertex_degrees(const uint32_t* __restrict__ dir, const uint32_t*
     }
 }
 
+// Bitmap of the vertices without entries: no search reaches them from
+// another vertex, and a bottom-up level need not scan them.
+__global__ void isolated_bits(const uint32_t* __restrict__ deg, int64_t n, int64_t words, uint32_t* __restrict__ iso) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t x = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t v = w * 32 + b;
+            if (v < n && deg[v] == 0) x |= 1u << b;
+        }
+        iso[w] = x;
+    }
+}
+
 // Bottom-up layout, step 1: exclusive scan of the degrees in tiles of 1024,
 // in 64 bits, with every tile's total.
 __global__ void __launch_bounds__(1024) degree_tile_scan(const uint32_t* __restrict__ deg, int64_t n,
@@ -449,11 +462,15 @@ bfs_status build_layout(bfs_graph* g, int64_t n, int64_t m, const int32_t* d_src
 bfs_status ensure_degrees(bfs_graph* g, cudaStream_t st) {
     Layout& L = g->L;
     if (L.deg.ptr) return BFS_OK;
-    DevBuf deg;
+    DevBuf deg, iso;
     BFS_TRY(deg.alloc(sizeof(uint32_t) * L.n));
     vertex_degrees<<<grid_for(L.n, 256), 256, 0, st>>>(L.dir.as<uint32_t>(), L.rank.as<uint32_t>(), L.dir_stride,
                                                        L.cp.as<uint32_t>(), L.cp_base_d.as<int64_t>(), L.p, L.nb,
                                                        L.n, deg.as<uint32_t>());
+    BFS_CUDA_TRY(cudaGetLastError());
+    const int64_t iso_words = ((L.n + 31) / 32 + 4 + 3) / 4 * 4;        // the search bitmaps' padded size
+    BFS_TRY(iso.alloc(sizeof(uint32_t) * iso_words));
+    isolated_bits<<<grid_for(iso_words, 256), 256, 0, st>>>(deg.as<uint32_t>(), L.n, iso_words, iso.as<uint32_t>());
     BFS_CUDA_TRY(cudaGetLastError());
     // the bottom-up rows: offsets = scan of the degrees, then the columns
     const int64_t tiles = (L.n + 1 + 1023) / 1024;
@@ -486,6 +503,8 @@ bfs_status ensure_degrees(bfs_graph* g, cudaStream_t st) {
     BFS_CUDA_TRY(cudaStreamSynchronize(st));
     std::swap(L.deg.ptr, deg.ptr);
     std::swap(L.deg.bytes, deg.bytes);
+    std::swap(L.iso.ptr, iso.ptr);
+    std::swap(L.iso.bytes, iso.bytes);
     std::swap(L.bu_ptr.ptr, ptr.ptr);
     std::swap(L.bu_ptr.bytes, ptr.bytes);
     std::swap(L.bu_adj.ptr, adj.ptr);
@@ -674,7 +693,7 @@ bfs_status bfs_graph_footprint(bfs_graph_t g, int64_t* bytes) {
     const Layout& L = g->L;
     const Workspace& W = g->W;
     int64_t b = (int64_t)(L.dir.bytes + L.rank.bytes + L.cp.bytes + L.ir.bytes + L.cp_base_d.bytes + L.ir_base_d.bytes +
-                          L.deg.bytes + L.bu_ptr.bytes + L.bu_adj.bytes);
+                          L.deg.bytes + L.iso.bytes + L.bu_ptr.bytes + L.bu_adj.bytes);
     b += (int64_t)(W.pi.bytes + W.fa.bytes + W.fb.bytes + W.fsum.bytes + W.xbuf.bytes + W.xcount.bytes +
                    W.chunk_base.bytes + W.units.bytes + W.counters.bytes + W.tmp_parent.bytes + W.tmp_level.bytes +
                    W.pieces.bytes + W.level_scratch.bytes + W.row_meta.bytes + W.tblk.bytes + W.rowbuf.bytes +

@@ -65,6 +65,7 @@ struct Layout {
     int64_t nnzc_total = 0; // nonempty columns over all blocks
     DevBuf dir, rank, cp, ir, cp_base_d, ir_base_d;
     DevBuf deg;             // entries per source vertex (uint32, saturated), computed for bottom-up levels
+    DevBuf iso;             // bitmap of the vertices without entries (bottom-up levels mark them visited)
     DevBuf bu_ptr, bu_adj;  // bottom-up levels: the columns of v in blocks (0,i) .. (p-1,i) back to back
                             // (int64 offsets n+1, int32 ids), grouped by range in ascending order
     std::vector<int64_t> cp_base, ir_base, nnzc, nnz_b;   // host copies, p*p
