@@ -80,6 +80,7 @@ def _load():
                 "oracle_adaptive_decode": (_int, [_int, _ptr, _i64, _i64, _int, _ptr]),
                 "oracle_dist_bfs": (_i64, [_i64, _int, _ptr, _ptr, ctypes.c_int32, _int, _int, _int,
                                            _ptr, _ptr, _ptr, _i64, _ptr, _i64, _ptr, _i64, _ptr]),
+                "oracle_dynamic_sieve_stats": (_i64, [_i64, _int, _ptr, _ptr, ctypes.c_int32, _i64, _ptr]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -243,15 +244,29 @@ def adaptive_trace(tr, n: int, p: int, mode: int = COMPRESS_SIEVE, w: int = 32):
     return out
 
 
+def dynamic_sieve_stats(g: CSR, p: int, root: int, max_levels: int = 256):
+    """Per level of the search, by definition: (static pairs, dynamic pairs,
+    entries of the static pairs, entries of the dropped pairs, entries walked by
+    the directory update) -- see oracle_dynamic_sieve_stats."""
+    out = np.zeros(5 * max_levels, dtype=np.int64)
+    k = _load().oracle_dynamic_sieve_stats(g.n, p, _p(g.row_ptr), _p(g.col), root, max_levels, _p(out))
+    if k < 0:
+        raise ValueError("oracle_dynamic_sieve_stats failed")
+    return out[: 5 * k].reshape(k, 5)
+
+
 def dist_bfs(g: CSR, p: int, root: int, mode: int = COMPRESS_SIEVE, w: int = 32,
              use_max: bool = False, trace: bool = False, max_levels: int = 256,
-             trace_cap: int | None = None, rows: bool = False):
+             trace_cap: int | None = None, rows: bool = False, dynamic: bool = False):
     """Algorithm 1/2/3 on a simulated p x p grid.
 
     Returns ``(level, parent, trace)``; ``trace`` is a list (one entry per
     exchange, i.e. per BFS level that had a nonempty frontier) of lists of
     word arrays, indexed by slot: ``i*p + j`` for DIR-WAH (stream from source
     range j to block-row i), ``j`` for WAH.  ``None`` unless ``trace``.
+
+    With ``dynamic=True`` (DIR-WAH only) the cross directory is dynamic: V_{i,j}(u)
+    is cleared once every entry of u into range i leads to a visited vertex.
 
     With ``rows=True`` (DIR-WAH only) a fourth element is returned: the row
     buffers of every level's fold, in the same layout (slot ``i*p + j`` = the
@@ -282,7 +297,9 @@ def dist_bfs(g: CSR, p: int, root: int, mode: int = COMPRESS_SIEVE, w: int = 32,
     else:
         rwords = rcounts = None
         rwp = rcp = rcap = 0
-    rc = lib.oracle_dist_bfs(g.n, p, _p(g.row_ptr), _p(g.col), root, mode, w, int(use_max),
+    if dynamic and mode != COMPRESS_SIEVE:
+        raise ValueError("the dynamic directory sieves DIR-WAH (COMPRESS_SIEVE) only")
+    rc = lib.oracle_dist_bfs(g.n, p, _p(g.row_ptr), _p(g.col), root, 3 if dynamic else mode, w, int(use_max),
                              _p(level), _p(parent), wp, tcap, cp, max_levels, rwp, rcap, rcp)
     if rc < 0:
         raise ValueError(f"oracle_dist_bfs failed ({rc})")

@@ -28,6 +28,9 @@
  *   oracle_adaptive_encode/_decode -- a sieved slice sent as the smallest of
  *                            its WAH stream, its sparse vector (Sec. II,
  *                            Table 2; Sec. V-A) and its raw bitmap (Alg. 1).
+ *   oracle_dynamic_sieve_stats -- the pairs and entries a dynamic cross
+ *                            directory (Sec. V-B's synchronous update) drops,
+ *                            level by level, by definition.
  *   oracle_dist_bfs       -- Algorithms 1, 2 and 3 (BIT, WAH, DIR-WAH) on a
  *                            simulated p x p grid: the frontier exchange
  *                            (raw, compressed, or sieved by f_j (.) V_{i,j}
@@ -520,7 +523,12 @@ int64_t oracle_dist_bfs(int64_t n, int p, const int64_t *row_ptr, const int32_t 
                         uint64_t *trace_words, int64_t trace_cap, int64_t *trace_counts,
                         int64_t max_levels, uint64_t *row_words, int64_t row_cap, int64_t *row_counts)
 {
-    if (n <= 0 || p <= 0 || p > n || root < 0 || root >= n || mode < 0 || mode > 2) return -1;
+    if (n <= 0 || p <= 0 || p > n || root < 0 || root >= n || mode < 0 || mode > 3) return -1;
+    /* mode 3: DIR-WAH with a dynamic cross directory (the reading of Sec. V-B's
+     * synchronous update): V_{i,j}(u) is cleared once every entry of u into
+     * range i leads to a visited vertex; traced and sieved like mode 2 */
+    const int dynamic = (mode == 3);
+    if (dynamic) mode = 2;
     const int64_t nb = range_size(n, p);
     const int rows = (mode == 2 && row_counts != NULL);
     uint8_t *f = (uint8_t *)calloc((size_t)n, 1);        /* current frontier, all ranges */
@@ -540,10 +548,42 @@ int64_t oracle_dist_bfs(int64_t n, int p, const int64_t *row_ptr, const int32_t 
     }
     /* the cross directories of every processor (Eq. 5), static for the graph */
     if (mode == 2) oracle_cross_directory(n, p, row_ptr, col, D);
+    /* dynamic: cnt[i*n + u] = entries u -> v with v in range i not yet visited;
+     * the update walks the entries into every newly visited vertex (in_ptr/in_src) */
+    int64_t *cnt = NULL, *in_ptr = NULL;
+    int32_t *in_src = NULL;
+    if (dynamic) {
+        const int64_t m = row_ptr[n];
+        cnt = (int64_t *)calloc((size_t)n * (size_t)p, sizeof(int64_t));
+        in_ptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+        in_src = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+        int64_t *fillp = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+        if (!cnt || !in_ptr || !in_src || !fillp) {
+            free(cnt); free(in_ptr); free(in_src); free(fillp);
+            free(f); free(pi); free(t); free(tij); free(recv); free(slice); free(dec); free(fold); free(words); free(D);
+            return -1;
+        }
+        for (int64_t u = 0; u < n; ++u)
+            for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                cnt[(size_t)(col[e] / nb) * (size_t)n + (size_t)u] += 1;
+                in_ptr[col[e] + 1] += 1;
+            }
+        for (int64_t v = 0; v < n; ++v) in_ptr[v + 1] += in_ptr[v];
+        for (int64_t v = 0; v < n; ++v) fillp[v] = in_ptr[v];
+        for (int64_t u = 0; u < n; ++u)
+            for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) in_src[fillp[col[e]]++] = (int32_t)u;
+        free(fillp);
+    }
     /* recv[i*n + u] = bit u of the frontier as P_i holds it after the exchange */
     for (int64_t v = 0; v < n; ++v) { level[v] = -1; parent[v] = -1; }
     level[root] = 0; parent[root] = root;
     f[root] = 1; pi[root] = 1;
+    if (dynamic) {                         /* the root is visited before the first exchange */
+        for (int64_t e = in_ptr[root]; e < in_ptr[root + 1]; ++e) {
+            int64_t *c = &cnt[(size_t)(root / nb) * (size_t)n + (size_t)in_src[e]];
+            if (--*c == 0) D[(size_t)(root / nb) * (size_t)n + (size_t)in_src[e]] = 0;
+        }
+    }
     const int64_t slots = (mode == 2) ? (int64_t)p * p : (mode == 1 ? p : 0);
     int64_t k = 0, used = 0, row_used = 0, rc = 0;
     for (;;) {
@@ -623,6 +663,15 @@ int64_t oracle_dist_bfs(int64_t n, int p, const int64_t *row_ptr, const int32_t 
             f[v] = (uint8_t)(t[v] >= 0);
             if (f[v]) { pi[v] = 1; level[v] = (int32_t)(k + 1); parent[v] = t[v]; }
         }
+        /* ---- dynamic directory: every entry u -> v into a newly visited v ---- */
+        if (dynamic)
+            for (int64_t v = 0; v < n; ++v) {
+                if (!f[v]) continue;
+                for (int64_t e = in_ptr[v]; e < in_ptr[v + 1]; ++e) {
+                    const size_t x = (size_t)(v / nb) * (size_t)n + (size_t)in_src[e];
+                    if (--cnt[x] == 0) D[x] = 0;
+                }
+            }
         if (rows && k < max_levels)
             for (int64_t v = 0; v < n; ++v)
                 if (fold[v] != f[v]) { rc = -4; goto done; }
@@ -631,5 +680,66 @@ int64_t oracle_dist_bfs(int64_t n, int p, const int64_t *row_ptr, const int32_t 
     rc = k;
 done:
     free(f); free(pi); free(t); free(tij); free(recv); free(slice); free(dec); free(fold); free(words); free(D);
+    free(cnt); free(in_ptr); free(in_src);
     return rc;
+}
+
+/*
+ * What a dynamic cross directory would drop, by definition, level by level of
+ * the search from root on a p x p grid.  With F_k the frontier of level k and
+ * pi_k the vertices visited when it is exchanged (levels <= k):
+ *   out[5k+0]  pairs (u, i), u in F_k, that the static directory sends
+ *              (u has an entry into range i: V_{i,range(u)}(u) = 1);
+ *   out[5k+1]  pairs a dynamic directory sends (u has an entry into range i
+ *              leading to a vertex not in pi_k);
+ *   out[5k+2]  entries the static pairs make the expansion read;
+ *   out[5k+3]  entries of the dropped pairs (all of them lead to visited
+ *              vertices: the work the dynamic directory saves);
+ *   out[5k+4]  entries into the vertices of F_k, which the update of the
+ *              dynamic directory walks when F_k becomes visited.
+ * Returns the number of levels written (at most max_levels), -1 on bad input.
+ */
+int64_t oracle_dynamic_sieve_stats(int64_t n, int p, const int64_t *row_ptr, const int32_t *col, int32_t root,
+                                   int64_t max_levels, int64_t *out)
+{
+    if (n <= 0 || p <= 0 || p > n || root < 0 || root >= n) return -1;
+    const int64_t nb = range_size(n, p);
+    int32_t *level = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t *in_deg = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int64_t *to_range = (int64_t *)calloc((size_t)p, sizeof(int64_t));
+    int64_t *fresh_in_range = (int64_t *)calloc((size_t)p, sizeof(int64_t));
+    if (!level || !in_deg || !to_range || !fresh_in_range) {
+        free(level); free(in_deg); free(to_range); free(fresh_in_range);
+        return -1;
+    }
+    oracle_bfs_levels(n, row_ptr, col, root, level);
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) in_deg[col[e]] += 1;
+    int64_t depth = 0;
+    for (int64_t v = 0; v < n; ++v) if (level[v] + 1 > depth) depth = level[v] + 1;
+    if (depth > max_levels) depth = max_levels;
+    for (int64_t k = 0; k < depth; ++k) {
+        int64_t *o = out + 5 * k;
+        for (int q = 0; q < 5; ++q) o[q] = 0;
+        for (int64_t u = 0; u < n; ++u) {
+            if (level[u] != k) continue;
+            o[4] += in_deg[u];
+            for (int i = 0; i < p; ++i) { to_range[i] = 0; fresh_in_range[i] = 0; }
+            for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                const int32_t v = col[e];
+                const int i = (int)(v / nb);
+                to_range[i] += 1;
+                if (level[v] < 0 || level[v] > k) fresh_in_range[i] += 1;     /* not in pi_k */
+            }
+            for (int i = 0; i < p; ++i) {
+                if (!to_range[i]) continue;
+                o[0] += 1;
+                o[2] += to_range[i];
+                if (fresh_in_range[i]) o[1] += 1;
+                else o[3] += to_range[i];
+            }
+        }
+    }
+    free(level); free(in_deg); free(to_range); free(fresh_in_range);
+    return depth;
 }
