@@ -543,9 +543,12 @@ BFS_API bfs_status bfs_plwah_decode(const uint32_t *words, int64_t nwords, int64
  * expansion's entry rate against the rate the memory system serves.
  *   region_bytes   size of the region read (>= 4096 and <= 1 GiB; the
  *                  expansion reads its visited bitmap slice: n/p/8 bytes)
- *   iterations     reads per thread (>= 1; 4096 is enough for a stable rate)
+ *   iterations     reads per thread (>= 1, rounded up to a multiple of 4; 4096
+ *                  is enough for a stable rate)
  *   reads_per_s    out: reads per second (one 1024-thread CTA per SM, every
- *                  thread reading `iterations` words at hashed addresses)
+ *                  thread reading `iterations` words at pseudo-random addresses
+ *                  -- four xorshift32 sequences, masked into a power-of-two
+ *                  region -- with four reads in flight)
  *   cuda_stream    stream for the launches (NULL: legacy default stream)
  * The region is allocated and freed by the call.  Synchronises `cuda_stream`.
  * Errors: BFS_ERR_INVALID_ARG (NULL output, sizes outside the ranges),
