@@ -124,6 +124,7 @@ struct LevelArgs {
     int64_t row_cap;
     const int64_t* row_count;           // words in each row buffer
     const int64_t* row_first;           // per (slot, chunk): first word and its first group
+    const int64_t* col_first;           // the same for the column slots (bottom-up levels)
     int64_t row_cps;                    // encoder chunks per slot
     int64_t row_bcps;                   // fold chunks per range
     int sweep;                          // all CTAs start at row 0 (rows in turn)
@@ -725,18 +726,24 @@ __device__ __forceinline__ void img_fill(uint32_t* img, uint32_t b0, uint32_t b1
 
 constexpr int kFT = 512;            // threads of the fold CTAs
 
-// The fold of the compressed row exchange: t_i is the OR over j of the row
-// buffers (i, j), each the WAH stream of t_{i,j} & ~pi_i.  One CTA per (range
-// i, chunk c of kEncChunkGroups groups of the range): its warps take the p
-// buffers in turn, start at the word the encoder recorded for the chunk and
+// Chunk-wise OR-decode of exchanged slots.  One CTA per (range b, chunk c of
+// kEncChunkGroups groups of the range): its warps take the p slots that carry
+// range b in turn, start at the word the encoder recorded for the chunk and
 // decode the words covering the chunk's groups (and the active word, in the
-// chunk that holds the range's last bits) into a shared-memory image of t's
-// words; the image is then stored, the words shared with a neighbouring chunk
-// or range ORed.  t is clear before the fold and nothing else writes it on a
-// level with the row exchange.  Malformed buffers set C_ERROR (16).
-template <typename W>
-__global__ void __launch_bounds__(kFT) fold_rows(LevelArgs a) {
-    if (a.ctl->bu) return;
+// chunk that holds the range's last bits) into a shared-memory image of the
+// destination's words; the image is then stored, the words shared with a
+// neighbouring chunk or range ORed.  The destination is clear before.
+//   ROWS = true: the fold of the compressed row exchange on a top-down level --
+//     t_i is the OR over j of the row buffers (i, j), each the WAH stream of
+//     t_{i,j} & ~pi_i; nothing else writes t on such a level.
+//   ROWS = false: the column slots of a bottom-up level decoded into the one
+//     bitmap the bottom-up scan reads -- the OR over the block-rows i of slots
+//     (i, j) (COMPRESS_SIEVE) or slot j (COMPRESS); a raw slot of the adaptive
+//     format is ORed word by word, vector slots are left to decode_streams.
+// Malformed streams set C_ERROR (16).
+template <typename W, bool ROWS>
+__global__ void __launch_bounds__(kFT) fold_slots(LevelArgs a) {
+    if (ROWS ? a.ctl->bu : !a.ctl->bu) return;
     using T = Wah<W>;
     constexpr int GB = T::GB;
     constexpr int64_t CG = kEncChunkGroups;
@@ -748,10 +755,17 @@ __global__ void __launch_bounds__(kFT) fold_rows(LevelArgs a) {
     const int p = a.p;
     const int lane = (int)lane_id(), warp = (int)(threadIdx.x >> 5);
     const int64_t items = (int64_t)p * a.row_bcps;
+    const bool sieve = a.mode == BFS_MODE_COMPRESS_SIEVE;
+    const int nsrc = (ROWS || sieve) ? p : 1;                      // slots carrying one range
+    const void* buf = ROWS ? a.rowbuf : a.xbuf;
+    const int64_t cap = ROWS ? a.row_cap : a.slot_cap;
+    const int64_t* counts = ROWS ? a.row_count : a.xcount;
+    const int64_t* first = ROWS ? a.row_first : a.col_first;
+    uint32_t* dst = ROWS ? a.t : a.gbits;
     for (int64_t q = blockIdx.x; q < items; q += gridDim.x) {
-        const int i = (int)(q / a.row_bcps);
-        const int64_t c = q - (int64_t)i * a.row_bcps;
-        const int64_t ib = range_begin(a, i), nbits = range_begin(a, i + 1) - ib;
+        const int b = (int)(q / a.row_bcps);
+        const int64_t c = q - (int64_t)b * a.row_bcps;
+        const int64_t ib = range_begin(a, b), nbits = range_begin(a, b + 1) - ib;
         const int64_t b0 = c * CBITS;
         if (b0 >= nbits) continue;
         const int64_t b1 = (b0 + CBITS < nbits) ? b0 + CBITS : nbits;
@@ -764,13 +778,26 @@ __global__ void __launch_bounds__(kFT) fold_rows(LevelArgs a) {
         for (int k = threadIdx.x; k < nimg; k += kFT) img[k] = 0u;
         if (threadIdx.x == 0) s_err = 0;
         __syncthreads();
-        for (int j = warp; j < p; j += NW) {
-            const int64_t s = (int64_t)i * p + j;
-            const W* in = static_cast<const W*>(a.rowbuf) + s * a.row_cap;
-            const int64_t count = a.row_count[s];
+        for (int x_src = warp; x_src < nsrc; x_src += NW) {
+            const int64_t s = ROWS ? (int64_t)b * p + x_src : (sieve ? (int64_t)x_src * p + b : (int64_t)b);
+            const int64_t count = counts[s];
+            if (!ROWS && a.fmt) {
+                const int fm = (int)a.fmt[s];
+                if (fm == FMT_LIST) continue;                   // decode_streams ORs the offsets
+                if (fm == FMT_RAW) {                            // the slice's raw words of this chunk
+                    const uint32_t* in = static_cast<const uint32_t*>(a.xbuf) + s * a.slot_cap;
+                    const int64_t w0 = b0 >> 5, w1 = (b1 + 31) >> 5;
+                    for (int64_t w = w0 + lane; w < w1 && w < count; w += 32) {
+                        const uint32_t x = in[w];
+                        if (x) img_or<uint32_t>(img, al + (uint32_t)(32 * w - b0), x);
+                    }
+                    continue;
+                }
+            }
+            const W* in = static_cast<const W*>(buf) + s * cap;
             if (c < nch) {
-                int64_t x0 = a.row_first[2 * (s * a.row_cps + c)];
-                int64_t gpos = a.row_first[2 * (s * a.row_cps + c) + 1];
+                int64_t x0 = first[2 * (s * a.row_cps + c)];
+                int64_t gpos = first[2 * (s * a.row_cps + c) + 1];
                 while (gpos < g_hi) {
                     if (x0 >= count) {                         // the words end before the groups do
                         if (lane == 0) s_err = 1;
@@ -813,8 +840,8 @@ __global__ void __launch_bounds__(kFT) fold_rows(LevelArgs a) {
             const uint32_t x = img[k];
             if (!x) continue;
             const int64_t wlo = (gw0 + k) * 32;
-            if (wlo >= ib + b0 && wlo + 32 <= ib + b1) a.t[gw0 + k] = x;
-            else atomicOr(a.t + gw0 + k, x);
+            if (wlo >= ib + b0 && wlo + 32 <= ib + b1) dst[gw0 + k] = x;
+            else atomicOr(dst + gw0 + k, x);
         }
         if (threadIdx.x == 0 && s_err) atomicOr(a.ctr + C_ERROR, 16ull);
         __syncthreads();
@@ -900,11 +927,9 @@ __global__ void __launch_bounds__(kNT) decode_streams(LevelArgs a) {
         const W y = (xw < count) ? in[xw] : W(0);
         uint32_t* dst = a.gbits;
         const int fm = a.fmt ? (int)a.fmt[s] : FMT_WAH;
-        if (fm == FMT_RAW) continue;             // decode_raw_slots ORs the raw slots
-        if (fm == FMT_LIST) {                    // a vertex offset
-            if (xw < count) or_bits<uint32_t>(dst, jb + (int64_t)(uint32_t)y, 1u);
-            continue;
-        }
+        if (fm != FMT_LIST) continue;            // fold_slots decodes the WAH and raw slots
+        if (xw < count) or_bits<uint32_t>(dst, jb + (int64_t)(uint32_t)y, 1u);   // a vertex offset
+        continue;
         const uint32_t glen = (xw < count) ? (uint32_t)word_groups<W>(y) : 0u;
         const uint32_t gincl = warp_incl_sum(glen);
         const int64_t gs = a.chunk_base[s * a.chunks_per_slot + k] + (int64_t)(gincl - glen);
@@ -934,30 +959,6 @@ __global__ void __launch_bounds__(kNT) decode_streams(LevelArgs a) {
                 atomicOr(dst + w, mask);
             }
         }
-    }
-}
-
-// The raw slots of the level-adaptive exchange decoded into the same bitmap
-// (bottom-up levels only): word w of range j's bits is the OR over the
-// block-rows i of word w of every raw slot (i, j), one reduction per word
-// instead of one per slot.
-__global__ void __launch_bounds__(kNT) decode_raw_slots(LevelArgs a) {
-    if (!a.ctl->bu || !a.fmt) return;
-    const int p = a.p;
-    const bool sieve = a.mode == BFS_MODE_COMPRESS_SIEVE;
-    const uint32_t* xb = static_cast<const uint32_t*>(a.xbuf);
-    const int64_t wpr = (a.nb + 31) >> 5;                          // words of a range's slice
-    const int64_t total = (int64_t)p * wpr;
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = x / wpr, w = x - j * wpr;
-        const int64_t jb = range_begin(a, j), jl = range_begin(a, j + 1) - jb;
-        if (32 * w >= jl) continue;
-        uint32_t acc = 0;
-        for (int i = 0; i < (sieve ? p : 1); ++i) {
-            const int64_t s = sieve ? (int64_t)i * p + j : j;
-            if (__ldg(a.fmt + s) == FMT_RAW) acc |= __ldg(xb + s * a.slot_cap + w);
-        }
-        if (acc) or_bits<uint32_t>(a.gbits, jb + 32 * w, acc);
     }
 }
 
@@ -1449,6 +1450,7 @@ void free_workspace(bfs_graph* g) {
     W.tblk_dirty = false;
     W.enc_sums.release(); W.enc_bases.release(); W.enc_flags.release(); W.enc_done.release(); W.ctl.release();
     W.gbits.release();
+    W.colfirst.release();
     W.xfmt.release();
     for (auto& c : W.sgraph) {
         if (c.exec) cudaGraphExecDestroy(c.exec);
@@ -1552,9 +1554,11 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     const bool bu_kernels = g->direction != BFS_DIRECTION_TOP_DOWN;
     if (bu_kernels) BFS_TRY(ensure_degrees(g, st));
     const int64_t g_words = (W.bm_words + 3) / 4 * 4;
-    if (bu_kernels && !W.gbits.ptr) {
-        // allocated once: captured level loops keep its address
-        BFS_TRY(W.gbits.alloc(sizeof(uint32_t) * (size_t)g_words));
+    if (bu_kernels && (!W.gbits.ptr || !W.colfirst.ptr)) {
+        // allocated once (both or neither): captured level loops keep the addresses
+        bfs_status rc = W.gbits.alloc(sizeof(uint32_t) * (size_t)g_words);
+        if (rc == BFS_OK) rc = W.colfirst.alloc(sizeof(int64_t) * 2 * (size_t)(p2 * W.enc_cps));
+        if (rc != BFS_OK) { W.gbits.release(); W.colfirst.release(); return rc; }
     }
     DevBuf slot_off;
     if (tracing || row_tracing) BFS_TRY(slot_off.alloc(sizeof(int64_t) * (size_t)std::max<int64_t>(nslots, p2)));
@@ -1640,6 +1644,8 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     if (rowx) ea.slot_bits = W.rowlive.as<uint8_t>();    // the row encoder skips blocks that expanded nothing
     ea.adaptive = adaptive ? 1 : 0;
     ea.fmt = W.xfmt.as<uint8_t>();
+    if (bu_kernels) ea.chunk_first = W.colfirst.as<int64_t>();   // the bottom-up decode starts chunk by chunk
+    a.col_first = W.colfirst.as<int64_t>();
     a.fmt = adaptive ? W.xfmt.as<uint8_t>() : nullptr;
 
     // the row encoder: slot s = i*p + j is the partial t_{i,j} (the directory
@@ -1704,9 +1710,11 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
                                                W.enc_flags.ptr, host ? ctr + C_EXCHANGED : nullptr, sm_count() * 6, s));
             if (bu_kernels) {           // a bottom-up level reads the streams as bitmaps
                 clear_gbits<<<sm_count() * 4, kNT, 0, s>>>(a);
-                if (wbits == 32) decode_streams<uint32_t><<<sm_count() * 8, kNT, 0, s>>>(a);
-                else decode_streams<unsigned long long><<<sm_count() * 8, kNT, 0, s>>>(a);
-                if (adaptive) decode_raw_slots<<<sm_count() * 8, kNT, 0, s>>>(a);
+                const int64_t fitems = (int64_t)p * a.row_bcps;
+                const int fgrid = (int)std::min<int64_t>(std::max<int64_t>(fitems, 1), (int64_t)sm_count() * 4);
+                if (wbits == 32) fold_slots<uint32_t, false><<<fgrid, kFT, 0, s>>>(a);
+                else fold_slots<unsigned long long, false><<<fgrid, kFT, 0, s>>>(a);
+                if (adaptive) decode_streams<uint32_t><<<sm_count() * 8, kNT, 0, s>>>(a);   // vector slots
                 BFS_CUDA_TRY(cudaGetLastError());
             }
             if (host && timing) cudaEventRecord(W.ev[1], s);
@@ -1761,8 +1769,8 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             }
             const int64_t fitems = (int64_t)p * a.row_bcps;
             const int fgrid = (int)std::min<int64_t>(std::max<int64_t>(fitems, 1), (int64_t)sm_count() * 4);
-            if (wbits == 32) fold_rows<uint32_t><<<fgrid, kFT, 0, s>>>(a);
-            else fold_rows<unsigned long long><<<fgrid, kFT, 0, s>>>(a);
+            if (wbits == 32) fold_slots<uint32_t, true><<<fgrid, kFT, 0, s>>>(a);
+            else fold_slots<unsigned long long, true><<<fgrid, kFT, 0, s>>>(a);
             BFS_CUDA_TRY(cudaGetLastError());
             if (host && timing) cudaEventRecord(W.ev[6], s);
         } else if (host && timing) {

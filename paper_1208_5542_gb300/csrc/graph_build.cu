@@ -698,7 +698,7 @@ bfs_status bfs_graph_footprint(bfs_graph_t g, int64_t* bytes) {
                    W.chunk_base.bytes + W.units.bytes + W.counters.bytes + W.tmp_parent.bytes + W.tmp_level.bytes +
                    W.pieces.bytes + W.level_scratch.bytes + W.row_meta.bytes + W.tblk.bytes + W.rowbuf.bytes +
                    W.rowcount.bytes + W.rowfirst.bytes + W.rowlive.bytes + W.xfmt.bytes + W.enc_sums.bytes + W.enc_bases.bytes + W.enc_flags.bytes +
-                   W.enc_done.bytes + W.gbits.bytes);
+                   W.enc_done.bytes + W.gbits.bytes + W.colfirst.bytes);
     *bytes = b;
     return BFS_OK;
 }

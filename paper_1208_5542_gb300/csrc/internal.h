@@ -135,6 +135,7 @@ struct Workspace {
     DevBuf enc_done;             // slots finished by the encoder's scan
     DevBuf ctl;                  // the level values kept on the device
     DevBuf gbits;                // exchanged streams decoded into one bitmap (bottom-up levels)
+    DevBuf colfirst;             // the column encoder's per-chunk first words (bottom-up decode)
     DevBuf xfmt;                 // per-slot format of the level-adaptive exchange
     SearchGraph sgraph[2];       // level loops as CUDA graphs, most recent configurations
     int sgraph_next = 0;
