@@ -725,6 +725,7 @@ __device__ __forceinline__ void img_fill(uint32_t* img, uint32_t b0, uint32_t b1
 }
 
 constexpr int kFT = 512;            // threads of the fold CTAs
+constexpr int kFoldIlp = 4;         // word tiles whose loads a fold warp issues together
 
 // Chunk-wise OR-decode of exchanged slots.  One CTA per (range b, chunk c of
 // kEncChunkGroups groups of the range): its warps take the p slots that carry
@@ -798,33 +799,58 @@ __global__ void __launch_bounds__(kFT) fold_slots(LevelArgs a) {
             if (c < nch) {
                 int64_t x0 = first[2 * (s * a.row_cps + c)];
                 int64_t gpos = first[2 * (s * a.row_cps + c) + 1];
+                // a run length is at most the slot's G groups: clamped to G + 1,
+                // 32 of them sum within 32 bits (a longer fill is malformed and
+                // still clipped to the chunk)
+                const uint32_t lcap = (uint32_t)(G + 1);
                 while (gpos < g_hi) {
                     if (x0 >= count) {                         // the words end before the groups do
                         if (lane == 0) s_err = 1;
                         break;
                     }
-                    const int64_t x = x0 + lane;
-                    const W y = (x < count) ? in[x] : W(0);
-                    const unsigned long long len = (x < count) ? (unsigned long long)word_groups<W>(y) : 0ull;
-                    const unsigned long long incl = warp_incl_sum(len);
-                    const int64_t gs = gpos + (int64_t)(incl - len);
-                    bool one = false;
-                    if (x < count && gs < g_hi && gs + (int64_t)len > g_lo) {
-                        if (!is_fill<W>(y)) img_or<W>(img, al + (uint32_t)((gs - g_lo) * GB), T::from_payload(y));
-                        else one = (y & T::VAL) != W(0);
+                    W y[kFoldIlp];                              // kFoldIlp tiles of 32 words in flight
+#pragma unroll
+                    for (int k = 0; k < kFoldIlp; ++k) {
+                        const int64_t x = x0 + 32 * k + lane;
+                        y[k] = (x < count) ? in[x] : W(0);
                     }
-                    uint32_t m = __ballot_sync(0xffffffffu, one);
-                    while (m) {                                 // 1-fills, by the whole warp
-                        const int o = __ffs(m) - 1;
-                        m &= m - 1;
-                        int64_t f0 = __shfl_sync(0xffffffffu, gs, o);
-                        int64_t f1 = f0 + (int64_t)__shfl_sync(0xffffffffu, len, o);
-                        if (f0 < g_lo) f0 = g_lo;
-                        if (f1 > g_hi) f1 = g_hi;
-                        img_fill(img, al + (uint32_t)((f0 - g_lo) * GB), al + (uint32_t)((f1 - g_lo) * GB));
+#pragma unroll
+                    for (int k = 0; k < kFoldIlp; ++k) {
+                        if (gpos >= g_hi || x0 >= count) break;   // warp-uniform
+                        const int64_t x = x0 + lane;
+                        const bool valid = x < count;
+                        const bool fill = valid && is_fill<W>(y[k]);
+                        uint32_t len = valid ? 1u : 0u, incl;
+                        if (__any_sync(0xffffffffu, fill)) {
+                            if (fill) {
+                                const uint64_t l = word_groups<W>(y[k]);
+                                len = l < lcap ? (uint32_t)l : lcap;
+                            }
+                            incl = warp_incl_sum(len);
+                        } else {
+                            // literals only: one group each; the lanes past the words are a suffix
+                            const uint32_t nvalid = (count - x0 < 32) ? (uint32_t)(count - x0) : 32u;
+                            incl = valid ? (uint32_t)lane + 1u : nvalid;
+                        }
+                        const int64_t gs = gpos + (int64_t)(incl - len);
+                        bool one = false;
+                        if (valid && gs < g_hi && gs + (int64_t)len > g_lo) {
+                            if (!fill) img_or<W>(img, al + (uint32_t)((gs - g_lo) * GB), T::from_payload(y[k]));
+                            else one = (y[k] & T::VAL) != W(0);
+                        }
+                        uint32_t m = __ballot_sync(0xffffffffu, one);
+                        while (m) {                             // 1-fills, by the whole warp
+                            const int o = __ffs(m) - 1;
+                            m &= m - 1;
+                            int64_t f0 = __shfl_sync(0xffffffffu, gs, o);
+                            int64_t f1 = f0 + (int64_t)__shfl_sync(0xffffffffu, len, o);
+                            if (f0 < g_lo) f0 = g_lo;
+                            if (f1 > g_hi) f1 = g_hi;
+                            img_fill(img, al + (uint32_t)((f0 - g_lo) * GB), al + (uint32_t)((f1 - g_lo) * GB));
+                        }
+                        x0 += 32;
+                        gpos += (int64_t)__shfl_sync(0xffffffffu, incl, 31);
                     }
-                    x0 += 32;
-                    gpos += (int64_t)__shfl_sync(0xffffffffu, incl, 31);
                 }
             }
             // the active word holds the range's last r bits
@@ -1112,24 +1138,25 @@ __global__ void __launch_bounds__(kNT) reduce_level(uint32_t* __restrict__ t, ui
         uint32_t x = 0;
         unsigned long long dsum = 0;
         if (w < words) {
-            x = t[w] & ~pi[w];
-            if (x) {
-                pi[w] |= x;
-                uint32_t y = x;
-                while (y) {
-                    const int bpos = __ffs(y) - 1;
-                    y &= y - 1;
-                    const int64_t v = w * 32 + bpos;
-                    if (v < n) {
-                        level[v] = next_level;
-                        if (deg) dsum += __ldg(deg + v);
-                    }
-                }
-            }
+            const uint32_t pw = pi[w];
+            x = t[w] & ~pw;
+            if (x) pi[w] = pw | x;
             f[w] = x;
             t[w] = 0u;
         }
         const uint32_t any = __ballot_sync(0xffffffffu, x != 0u);
+        // the levels (and degrees) of the fresh vertices, one word at a time
+        // by the whole warp: lane l takes bit l (coalesced stores and loads)
+        for (uint32_t m = any; m;) {
+            const int k = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t xk = __shfl_sync(0xffffffffu, x, k);
+            const int64_t v = (gw * 32 + k) * 32 + lane_id();
+            if (((xk >> lane_id()) & 1u) && v < n) {
+                level[v] = next_level;
+                if (deg) dsum += __ldg(deg + v);
+            }
+        }
         const int cnt = warp_sum(__popc(x));
         if (deg) dsum = warp_sum(dsum);
         if (lane_id() == 0) {
