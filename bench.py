@@ -16,7 +16,11 @@ Arms on the same resident graph, each timed the same way:
   row_exchange   DIR-WAH with the fold of every block-row itself a compressed,
                  sieved exchange of per-block row buffers (the 2D partition the
                  paper names in Sec. VIII; the library's default);
-  hybrid         both exchanges with top-down / bottom-up levels (Sec. VIII, IX).
+  hybrid         both exchanges with top-down / bottom-up levels (Sec. VIII, IX);
+  adaptive       every exchanged slice as the smallest of WAH stream, sparse
+                 vector and raw bitmap (Sec. II, Table 2);
+  dynamic_directory  DIR-WAH sieved by the search's dynamic cross directory
+                 (Sec. V-B), with the cost of its update.
 The default run adds the other configurations (Kronecker scale 22 on 8 x 8, the
 Erdos-Renyi scale-26 control, the 64-root batch, the serving stream) under
 "configs".
@@ -411,8 +415,9 @@ def main():
     level = torch.empty(n, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def configure(mode, rowx, direction, adaptive=None):
+    def configure(mode, rowx, direction, adaptive=None, dynamic=False):
         g.set_mode(mode, args.wah_bits)
+        g.set_dynamic_directory(dynamic)
         g.set_row_exchange(rowx)
         g.set_direction(DIRECTIONS[direction], args.alpha, args.beta)
         g.set_exchange_format(args.format == "adaptive" if adaptive is None else adaptive)
@@ -421,13 +426,15 @@ def main():
         # one untimed search per arm from the first root (for ncu), with the
         # per-level counters that give each kernel's algorithmic bytes
         out = {"profile_run": True, "workload": desc, "root": int(roots[0]), "kernel_hash": kernel_hash()}
-        for name, mode, rowx in (("compress_sieve", args.mode, args.row_exchange == "on"), ("plain", 0, False),
-                                 ("row_exchange", 2, True)):
-            configure(mode, rowx, args.direction)
+        for name, mode, rowx, dyn in (("compress_sieve", args.mode, args.row_exchange == "on", False),
+                                      ("plain", 0, False, False), ("row_exchange", 2, True, False),
+                                      ("dynamic_directory", 2, False, True)):
+            configure(mode, rowx, args.direction, dynamic=dyn)
             _, _, st = g.run(int(roots[0]), parent, level, stats=True)
             out[name] = {"levels": st.n_levels, "per_level": [
                 {f: st.levels[k][f] for f in ("edges_scanned", "column_hits", "wah_bytes", "row_wah_bytes",
-                                               "compress_chunks", "row_compress_chunks", "frontier_vertices")}
+                                               "compress_chunks", "row_compress_chunks", "frontier_vertices",
+                                               "exchanged_vertices")}
                 for k in range(st.n_levels)]}
         torch.cuda.synchronize()
         print(json.dumps(out))
@@ -449,11 +456,11 @@ def main():
             sts.append(st)
         return times, ms_, sts
 
-    def timed(mode, rowx, direction, steps, warmup, record=True, adaptive=None):
+    def timed(mode, rowx, direction, steps, warmup, record=True, adaptive=None, dynamic=False):
         """Warm-up, then `steps` timed steps (the library's CUDA-graph level loop,
         no statistics); then one recording pass (the stepwise loop with per-level
         statistics and phase events) outside the timed steps."""
-        configure(mode, rowx, direction, adaptive)
+        configure(mode, rowx, direction, adaptive, dynamic)
         for _ in range(warmup):
             step()
         if world > 1:
@@ -599,6 +606,22 @@ def main():
                     raw_b = sum(ls["raw_bytes"] for st in h["stats"] for ls in st.levels)
                     ad[name]["exchange_over_raw"] = round(ex_b / raw_b, 6) if raw_b else None
             arms["adaptive" if args.format != "adaptive" else "wah_format"] = ad
+        # the dynamic cross directory (Sec. V-B): the sieve drops the vertices whose
+        # every entry into a block-row leads to a visited vertex; its update walks the
+        # entries of every visited vertex once per search
+        dy = timed(2, value_rowx, args.direction, args.extra_steps, 2, dynamic=True)
+        ex_dyn = sum(ls["exchanged_vertices"] for st in dy["stats"] for ls in st.levels)
+        ex_static = sum(ls["exchanged_vertices"] for st in main_arm["stats"] for ls in st.levels)
+        arms["dynamic_directory"] = {
+            "value": round(dy["gteps"], 4), "ms_per_step": round(dy["ms_per_step"], 3), "steps": args.extra_steps,
+            "cost_vs_value": round(dy["ms_per_step"] / main_arm["ms_per_step"] - 1, 4),
+            "exchanged_over_static": round(ex_dyn / ex_static, 4) if ex_static else None,
+            "wah_bytes_per_search": round(sum(ls["wah_bytes"] for st in dy["stats"] for ls in st.levels) / len(roots)),
+            "update_ms_per_search": round(sum(ls["ms_directory_update"] for st in dy["stats"]
+                                              for ls in st.levels) / len(roots), 4),
+            "validation": {"invariant_and_min_parent_roots":
+                           validate_all(g, roots, parent, level, src_d, dst_d, n, dev, stream, torch),
+                           "roots": len(roots)}}
         configure(args.mode, value_rowx, args.direction)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region

@@ -141,6 +141,8 @@ typedef struct {
     int64_t nonempty_columns;/* sum over blocks of |V_{i,j}| (set directory bits) */
     int32_t exchange_format; /* BFS_FORMAT_* */
     int32_t direction;       /* BFS_DIRECTION_* */
+    int32_t dynamic_directory; /* 1: the sieve reads the search's dynamic cross directory */
+    int32_t reserved;
 } bfs_graph_info_t;
 
 BFS_API bfs_status bfs_graph_info(bfs_graph_t g, bfs_graph_info_t *info);
@@ -199,6 +201,34 @@ enum {
  * buffers of the fold stay WAH.  Not safe while a search on `g` is running.
  */
 BFS_API bfs_status bfs_graph_set_exchange_format(bfs_graph_t g, int32_t format);
+
+/*
+ * The dynamic cross directory.  Sec. V-B has both sides of the exchange keep
+ * the directories up to date as the search goes on; Alg. 3 sieves every level
+ * with the static V_{i,j} of Eq. 4.  With the dynamic directory on, a search
+ * sieves with its own directories D_{i,j}, where D_{i,j}(u) = 1 while column
+ * u of block A_{i,j} still holds an entry into a vertex that is not visited:
+ * once every entry of u into range i leads to a visited vertex, u can reach
+ * nothing more in block-row i and is no longer sent there.  The sieve of
+ * level k sends f_j (.) D_{i,j} with the visited set of levels 0..k, the
+ * state that updating D after every visit leaves.  A bit matters only at the
+ * exchange that sends its vertex and never comes back once cleared, so the
+ * library evaluates, just before each exchange, the bits of the frontier's
+ * vertices from their definition (a scan of the column that stops at the
+ * first unvisited destination) in a copy of the directories taken at the
+ * search's start.  Levels and parents never change; the exchanged streams
+ * carry fewer vertices (bfs_level_stats.exchanged_vertices), and the scans
+ * cost time before each exchange (bfs_level_stats.ms_directory_update).
+ *   enabled: 1, or 0 (the default: the static directory of Alg. 3).
+ * Applies to COMPRESS_SIEVE searches (bfs_run), directed or undirected
+ * graphs, top-down and bottom-up levels, with or without the row exchange
+ * and either exchange format; PLAIN and COMPRESS searches have no sieve, and
+ * the batched and served searches keep the static directory.  The first
+ * search with it allocates the copy (p*p directory bitmaps), kept with the
+ * graph and counted by bfs_graph_footprint.  Not safe while a search on `g`
+ * is running.
+ */
+BFS_API bfs_status bfs_graph_set_dynamic_directory(bfs_graph_t g, int32_t enabled);
 
 /* Direction of each level (bfs_graph_set_direction). */
 enum {
@@ -272,7 +302,8 @@ typedef struct {
     int32_t bottom_up;           /* 1: the level ran bottom-up (bfs_graph_set_direction) */
     float ms_row_compress;       /* row exchange: sieve by not(pi) + compress of the partials */
     float ms_row_fold;           /* row exchange: decompress + OR of the row buffers (the fold) */
-    int32_t reserved;
+    float ms_directory_update;   /* dynamic cross directory: the frontier's bits evaluated before
+                                    the exchange (bfs_graph_set_dynamic_directory; 0 without it) */
     int64_t compress_chunks;     /* chunks of 1024 groups the column sieve + compress read (each:
                                     the chunk's frontier and directory bits) */
     int64_t row_compress_chunks; /* chunks the row sieve + compress read (partial and visited bits) */

@@ -134,6 +134,11 @@ class Graph:
         check(native.lib().bfs_graph_set_exchange_format(self._h, native.FORMAT_ADAPTIVE if adaptive
                                                          else native.FORMAT_WAH))
 
+    def set_dynamic_directory(self, enabled: bool):
+        """Sieve with the search's dynamic cross directory (True) or the static
+        directories of Eq. 4 (False, the default); COMPRESS_SIEVE only."""
+        check(native.lib().bfs_graph_set_dynamic_directory(self._h, int(bool(enabled))))
+
     def set_direction(self, policy: int, alpha: int = 14, beta: int = 24):
         """Top-down (the default), hybrid top-down / bottom-up, or bottom-up levels."""
         check(native.lib().bfs_graph_set_direction(self._h, int(policy), int(alpha), int(beta)))

@@ -874,6 +874,117 @@ __global__ void __launch_bounds__(kFT) fold_slots(LevelArgs a) {
     }
 }
 
+// ----------------------------------------------------- dynamic directory --
+// The dynamic cross directory (Sec. V-B): D_{i,j}(u) = 1 while column u of
+// block (i,j) still holds an entry into a vertex that is not visited; the
+// sieve of exchange k sends f_j (.) D_{i,j}.  A bit matters only at the
+// exchange that sends u (u is in one frontier only), and a cleared bit stays
+// clear (the visited set only grows), so the bits of the frontier's vertices
+// are evaluated from their definition just before the exchange: D starts as a
+// copy of V each search, and every (u, i) with f_j(u) = D_{i,j}(u) = 1 whose
+// column reaches only visited vertices is cleared.  pi holds the vertices
+// visited up to this level, which is the state the synchronous update of
+// every earlier visit leaves (the entries into the visited vertices have all
+// been counted).  PLAIN-style units: (block (i,j), 32 words of range j), one
+// warp; each item (u, i) is decided by its lane (the column's first kDynLane
+// entries) and, for the rest of a long column, by the whole warp, stopping at
+// the first unvisited destination.
+constexpr uint32_t kDynStep = 8;      // entries a lane tests together
+constexpr uint32_t kDynLane = 64;     // entries a lane tests before the warp takes over
+
+__global__ void __launch_bounds__(kNT) dyn_sieve(LevelArgs a, uint32_t* __restrict__ ddir,
+                                                 const uint8_t* __restrict__ fsum) {
+    const int p = a.p;
+    const int64_t units = (int64_t)p * p * a.plain_upb;
+    const int64_t gw0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t gstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = (int)lane_id();
+    for (int64_t x = gw0; x < units; x += gstride) {
+        const int64_t b = x / a.plain_upb, c = x - b * a.plain_upb;
+        const int j = (int)(b % p);
+        const int64_t jb = range_begin(a, j), jl = range_begin(a, j + 1) - jb;
+        if (c * 1024 >= jl) continue;
+        const int64_t g0 = jb + c * 1024;               // the unit's first global bit
+        if (!fsum[g0 >> 10] && !fsum[(g0 + 1023) >> 10]) continue;   // no frontier bit (warp-uniform)
+        const int64_t w = c * 32 + lane;
+        uint32_t bits = 0;
+        if (w * 32 < jl) {
+            bits = bits32_at_cg(a.f, (uint64_t)(jb + w * 32));
+            const int64_t left = jl - w * 32;
+            if (left < 32) bits &= (1u << left) - 1u;
+            if (bits) bits &= ddir[b * a.dir_stride + w];
+        }
+        const uint32_t cnt = __popc(bits);
+        const uint32_t cincl = warp_incl_sum(cnt);
+        const uint32_t cexcl = cincl - cnt;
+        const uint32_t items = __shfl_sync(0xffffffffu, cincl, 31);
+        if (items == 0) continue;
+        const BlockView bv = block_view(a, b);
+        // the column of item q0 + lane (none past the items); the next round's
+        // lookups are issued before this round's scan, so that they overlap
+        auto lookup = [&](uint32_t q0, int64_t& ul, int64_t& begin, uint32_t& len) {
+            const uint32_t q = q0 + lane;
+            const int o = owner_lane(cexcl, q < items ? q : items - 1);
+            const uint32_t ob = __shfl_sync(0xffffffffu, bits, o);
+            const uint32_t oex = __shfl_sync(0xffffffffu, cexcl, o);
+            ul = -1;
+            begin = 0;
+            len = 0;
+            if (q < items) {
+                ul = (c * 32 + o) * 32 + select32(ob, (int)(q - oex));
+                column_of(a, bv, ul, false, &begin, &len);
+                prefetch_column(a, begin, len);
+            }
+        };
+        int64_t ul, begin;
+        uint32_t len;
+        lookup(0, ul, begin, len);
+        for (uint32_t q0 = 0; q0 < items; q0 += 32) {
+            int64_t ul_n = -1, begin_n = 0;
+            uint32_t len_n = 0;
+            if (q0 + 32 < items) lookup(q0 + 32, ul_n, begin_n, len_n);
+            uint32_t e = 0;
+            bool alive = ul < 0;
+            // the lane scans its column kDynStep entries at a time (their loads
+            // in flight together) up to kDynLane entries
+            while (!alive && e < len && e < kDynLane) {
+                int32_t v[kDynStep];
+#pragma unroll
+                for (uint32_t k = 0; k < kDynStep; ++k) v[k] = (e + k < len) ? __ldg(a.ir + begin + e + k) : -1;
+#pragma unroll
+                for (uint32_t k = 0; k < kDynStep; ++k)
+                    if (v[k] >= 0 && !((__ldg(a.pi + ((uint32_t)v[k] >> 5)) >> ((uint32_t)v[k] & 31u)) & 1u))
+                        alive = true;
+                e += kDynStep;
+            }
+            // the rest of the long columns whose first kDynLane entries are all
+            // visited: the whole warp, 32 entries a step, until an unvisited one
+            uint32_t m = __ballot_sync(0xffffffffu, !alive && e < len);
+            while (m) {
+                const int l = __ffs(m) - 1;
+                m &= m - 1;
+                const int64_t lb = __shfl_sync(0xffffffffu, begin, l);
+                const uint32_t ll = __shfl_sync(0xffffffffu, len, l);
+                bool found = false;
+                for (uint32_t e0 = kDynLane; e0 < ll && !found; e0 += 32) {
+                    bool un = false;
+                    if (e0 + lane < ll) {
+                        const uint32_t v = (uint32_t)__ldg(a.ir + lb + e0 + lane);
+                        un = !((__ldg(a.pi + (v >> 5)) >> (v & 31u)) & 1u);
+                    }
+                    found = __any_sync(0xffffffffu, un);
+                }
+                if (lane == l) alive = found;
+            }
+            if (!alive)
+                atomicAnd(ddir + b * a.dir_stride + (ul >> 5), ~(1u << ((uint32_t)ul & 31u)));
+            ul = ul_n;
+            begin = begin_n;
+            len = len_n;
+        }
+    }
+}
+
 // ------------------------------------------------------------- bottom-up --
 // OR the group bits `bits` (bit q = bitmap bit bit0 + q) into a bitmap.
 template <typename W>
@@ -1479,6 +1590,7 @@ void free_workspace(bfs_graph* g) {
     W.gbits.release();
     W.colfirst.release();
     W.xfmt.release();
+    W.ddir.release();
     for (auto& c : W.sgraph) {
         if (c.exec) cudaGraphExecDestroy(c.exec);
         if (c.graph) cudaGraphDestroy(c.graph);
@@ -1576,6 +1688,12 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     if (adaptive && wbits != 32)
         return set_error(BFS_ERR_INVALID_ARG, "the level-adaptive exchange format needs 32-bit WAH words");
     const bool row_tracing = stats && rowx && stats->row_trace_words && stats->row_trace_counts;
+    // the dynamic cross directory belongs to the sieve (COMPRESS_SIEVE)
+    const bool dynamic = g->dynamic_dir && mode == BFS_MODE_COMPRESS_SIEVE;
+    if (dynamic && !W.ddir.ptr) {
+        // allocated once: captured level loops keep the address
+        BFS_TRY(W.ddir.alloc(sizeof(uint32_t) * (size_t)(p2 * L.dir_stride)));
+    }
     const size_t dyn = win ? window_bytes(W.win_words) : 0;
     // bottom-up levels: degrees (direction choice) and the decoded streams
     const bool bu_kernels = g->direction != BFS_DIRECTION_TOP_DOWN;
@@ -1650,7 +1768,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
 
     EncodeArgs ea;
     memset(&ea, 0, sizeof(ea));
-    ea.dir = (mode == BFS_MODE_COMPRESS_SIEVE) ? L.dir.as<uint32_t>() : nullptr;
+    ea.dir = (mode == BFS_MODE_COMPRESS_SIEVE) ? (dynamic ? W.ddir.as<uint32_t>() : L.dir.as<uint32_t>()) : nullptr;
     ea.dir_stride = L.dir_stride;
     ea.p = p;
     ea.nb = L.nb;
@@ -1709,6 +1827,9 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     ra.skip = &ctl->bu;                      // bottom-up levels have no row exchange
     const int32_t max_levels = (int32_t)std::min<int64_t>(L.n + 1, INT32_MAX);
     const uint32_t* deg = bu_kernels ? L.deg.as<uint32_t>() : nullptr;
+
+    if (dynamic)                     // the search's directories start as V
+        BFS_CUDA_TRY(cudaMemcpyAsync(W.ddir.ptr, L.dir.ptr, W.ddir.bytes, cudaMemcpyDeviceToDevice, st));
     level_first<<<1, 1, 0, st>>>(ctl, L.n, win ? 1 : 0, g->direction, g->alpha, g->beta, deg, root, L.nnz);
     BFS_CUDA_TRY(cudaGetLastError());
 
@@ -1719,6 +1840,11 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         BFS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * C_ERROR, s));
         BFS_CUDA_TRY(cudaMemsetAsync(ctr + C_WAH_WORDS, 0, sizeof(unsigned long long) * (C_NUM - C_WAH_WORDS), s));
         BFS_CUDA_TRY(cudaMemsetAsync(lvl, 0, sizeof(unsigned long long) * (3 * p + 1), s));
+        if (host && timing) cudaEventRecord(W.ev[7], s);
+        if (dynamic) {                  // the frontier's bits of the dynamic directory
+            dyn_sieve<<<sm_count() * 8, kNT, 0, s>>>(a, W.ddir.as<uint32_t>(), W.fsum.as<uint8_t>());
+            BFS_CUDA_TRY(cudaGetLastError());
+        }
         if (host && timing) cudaEventRecord(W.ev[0], s);
         if (mode == BFS_MODE_PLAIN) {
             if (host && timing) { cudaEventRecord(W.ev[1], s); cudaEventRecord(W.ev[2], s); }
@@ -1821,7 +1947,8 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
         SearchGraph* sg = nullptr;
         for (auto& c : W.sgraph)
             if (c.exec && c.mode == mode && c.wbits == wbits && c.rowx == (int)rowx &&
-                c.bottom_up == (int)bu_kernels && c.adaptive == (int)adaptive && c.parent == parent &&
+                c.bottom_up == (int)bu_kernels && c.adaptive == (int)adaptive && c.dynamic == (int)dynamic &&
+                c.parent == parent &&
                 c.level == level)
                 sg = &c;
         if (!sg) {
@@ -1864,6 +1991,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             c.rowx = rowx ? 1 : 0;
             c.bottom_up = bu_kernels ? 1 : 0;
             c.adaptive = adaptive ? 1 : 0;
+            c.dynamic = dynamic ? 1 : 0;
             c.parent = parent;
             c.level = level;
             sg = &c;
@@ -1913,6 +2041,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
                 ls.ms_row_compress = elapsed(W.ev[3], W.ev[5]);
                 ls.ms_row_fold = elapsed(W.ev[5], W.ev[6]);
                 ls.ms_reducing = elapsed(W.ev[6], W.ev[4]);
+                ls.ms_directory_update = dynamic ? elapsed(W.ev[7], W.ev[0]) : 0.0f;
             }
         }
         stats->n_levels = k + 1;

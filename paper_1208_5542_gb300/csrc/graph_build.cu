@@ -698,7 +698,7 @@ bfs_status bfs_graph_footprint(bfs_graph_t g, int64_t* bytes) {
                    W.chunk_base.bytes + W.units.bytes + W.counters.bytes + W.tmp_parent.bytes + W.tmp_level.bytes +
                    W.pieces.bytes + W.level_scratch.bytes + W.row_meta.bytes + W.tblk.bytes + W.rowbuf.bytes +
                    W.rowcount.bytes + W.rowfirst.bytes + W.rowlive.bytes + W.xfmt.bytes + W.enc_sums.bytes + W.enc_bases.bytes + W.enc_flags.bytes +
-                   W.enc_done.bytes + W.gbits.bytes + W.colfirst.bytes);
+                   W.enc_done.bytes + W.gbits.bytes + W.colfirst.bytes + W.ddir.bytes);
     *bytes = b;
     return BFS_OK;
 }
@@ -715,6 +715,7 @@ bfs_status bfs_graph_info(bfs_graph_t g, bfs_graph_info_t* info) {
     info->row_exchange = g->row_exchange;
     info->exchange_format = g->adaptive ? BFS_FORMAT_ADAPTIVE : BFS_FORMAT_WAH;
     info->direction = g->direction;
+    info->dynamic_directory = g->dynamic_dir;
     info->nonempty_columns = g->L.nnzc_total;
     return BFS_OK;
 }
@@ -745,6 +746,15 @@ bfs_status bfs_graph_set_exchange_format(bfs_graph_t g, int32_t format) {
     if (g->busy.load()) return set_error(BFS_ERR_BUSY, "graph is in use");
     std::lock_guard<std::mutex> lk(g->mu);
     g->adaptive = format == BFS_FORMAT_ADAPTIVE ? 1 : 0;
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_set_dynamic_directory(bfs_graph_t g, int32_t enabled) {
+    if (!g) return set_error(BFS_ERR_INVALID_ARG, "graph is NULL");
+    if (enabled != 0 && enabled != 1) return set_error(BFS_ERR_INVALID_ARG, "enabled must be 0 or 1");
+    if (g->busy.load()) return set_error(BFS_ERR_BUSY, "graph is in use");
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->dynamic_dir = enabled;
     return BFS_OK;
 }
 

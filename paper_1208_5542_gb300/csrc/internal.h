@@ -106,7 +106,7 @@ enum Counter : int {
 struct SearchGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int mode = -1, wbits = 0, rowx = 0, bottom_up = 0, adaptive = 0;
+    int mode = -1, wbits = 0, rowx = 0, bottom_up = 0, adaptive = 0, dynamic = 0;
     int32_t* parent = nullptr;
     int32_t* level = nullptr;
 };
@@ -137,6 +137,7 @@ struct Workspace {
     DevBuf gbits;                // exchanged streams decoded into one bitmap (bottom-up levels)
     DevBuf colfirst;             // the column encoder's per-chunk first words (bottom-up decode)
     DevBuf xfmt;                 // per-slot format of the level-adaptive exchange
+    DevBuf ddir;                 // dynamic cross directory: the search's copy D_{i,j} of the directories
     SearchGraph sgraph[2];       // level loops as CUDA graphs, most recent configurations
     int sgraph_next = 0;
     int64_t enc_cps = 0;         // encoder chunks per slot
@@ -162,6 +163,7 @@ struct bfs_graph {
     bool batch_tuned = false;
     int row_exchange = 0;
     int adaptive = 0;            // level-adaptive exchange format (bfs_graph_set_exchange_format)
+    int dynamic_dir = 0;         // dynamic cross directory (bfs_graph_set_dynamic_directory)
     int symmetric = 0;           // built with symmetrize = 1: in-neighbours = out-neighbours
     int direction = BFS_DIRECTION_TOP_DOWN;
     int alpha = 14, beta = 24;   // switch thresholds of the hybrid

@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
 class GraphInfo(ctypes.Structure):
     _fields_ = [("n_vertices", i64), ("n_entries", i64), ("p", i32), ("mode", i32), ("wah_word_bits", i32),
                 ("row_exchange", i32), ("range_size", i64), ("nonempty_columns", i64),
-                ("exchange_format", i32), ("direction", i32)]
+                ("exchange_format", i32), ("direction", i32), ("dynamic_directory", i32), ("reserved", i32)]
 
 
 class LevelStats(ctypes.Structure):
@@ -47,7 +47,7 @@ class LevelStats(ctypes.Structure):
                 ("ms_compress_sieve", ctypes.c_float), ("ms_communication", ctypes.c_float),
                 ("ms_traversing", ctypes.c_float), ("ms_reducing", ctypes.c_float),
                 ("bottom_up", i32), ("ms_row_compress", ctypes.c_float), ("ms_row_fold", ctypes.c_float),
-                ("reserved", i32), ("compress_chunks", i64), ("row_compress_chunks", i64)]
+                ("ms_directory_update", ctypes.c_float), ("compress_chunks", i64), ("row_compress_chunks", i64)]
 
 
 class BatchStats(ctypes.Structure):
@@ -81,6 +81,7 @@ _SIGS = {
     "bfs_graph_set_row_exchange": (ctypes.c_int, [vp, i32]),
     "bfs_graph_set_direction": (ctypes.c_int, [vp, i32, i32, i32]),
     "bfs_graph_set_exchange_format": (ctypes.c_int, [vp, i32]),
+    "bfs_graph_set_dynamic_directory": (ctypes.c_int, [vp, i32]),
     "bfs_graph_directory": (ctypes.c_int, [vp, i32, i32, vp, vp]),
     "bfs_run": (ctypes.c_int, [vp, i32, vp, vp, P(RunStats), vp]),
     "bfs_check_search": (ctypes.c_int, [vp, i32, vp, vp, vp]),
