@@ -8,15 +8,15 @@
 //   COMPRESS (WAH, Alg. 2): f_j is WAH-encoded once per source range j; every
 //                          block-row i decodes stream j and tests its directory.
 //   COMPRESS_SIEVE (DIR-WAH, Alg. 3): for every (j, i) the slice f_j is sieved
-//                          by V_{i,j} and WAH-encoded (lines 9-10); block (i,j)
-//                          decodes its stream (line 13) -- every decoded vertex
-//                          has a nonempty column, so only its rank is looked up.
-//   expansion (line 5):    for every decoded (u, block) item, every entry
+//                          by V_{i,j} and WAH-encoded; block (i,j) decodes its
+//                          stream -- every decoded vertex has a nonempty
+//                          column, so only its rank is looked up.
+//   expansion:             for every decoded (u, block) item, every entry
 //                          u -> v of its column: if v is not in pi, set t[v]
 //                          and lower parent[v] to u (the (select, min) semiring).
-//   reduce (lines 6-7):    t = t & ~pi; pi |= t; level[v] = k + 1 for v in t;
+//   reduce:                t = t & ~pi; pi |= t; level[v] = k + 1 for v in t;
 //                          |t| counted on the device; f <- t.
-// The exchange itself (line 11) is the identity on one GPU: the receive buffer
+// The exchange itself (Alg. 2, 3) is the identity on one GPU: the receive buffer
 // g' is the send buffer in HBM; its sizes are scanned for the statistics and
 // packed into the caller's trace when one is requested.
 //

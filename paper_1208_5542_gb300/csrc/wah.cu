@@ -1,5 +1,5 @@
-// wah.cu -- WAH compress (Sec. IV, Table 3; Alg. 2 line 7, Alg. 3 line 10),
-// fused with the cross-directory sieve (Alg. 3 line 9), and the standalone
+// wah.cu -- WAH compress (Sec. IV, Table 3; the compress steps of Alg. 2 and 3),
+// fused with the cross-directory sieve (Alg. 3, Sec. V-A), and the standalone
 // codec entry points of the C ABI.
 //
 // Encoder: one CTA per exchange slot walks the slot's groups in tiles of
