@@ -532,6 +532,26 @@ def main():
                             ls["ms_row_compress"] + ls["ms_row_fold"] + ls["ms_reducing"])
     timing_modes = {"graph_ms_per_search": round(main_arm["ms_per_step"] / len(roots), 4),
                     "stepwise_phases_ms_per_search": round(stepwise_ms / len(roots), 4)}
+    # the whole search against HBM (the GTEPS roofline): algorithmic bytes per
+    # traversed edge -- adjacency entries 4 B, (vertex, block) columns 12 B (rank
+    # word and column-pointer pair), level, parent and candidate-parent 12 B per
+    # reached vertex, every stream written and read, the directory words the
+    # sieve reads -- and the GTEPS the measured copy rate allows at that rate
+    bpe = []
+    for st, m_r in zip(main_arm["stats"], main_arm["m"]):
+        if not m_r:
+            continue
+        b = sum(4 * ls["edges_scanned"] + 12 * ls["column_hits"] + 2 * ls["wah_bytes"] +
+                (CHUNK_GROUPS * (args.wah_bits - 1) // 8) * ls["compress_chunks"] + 12 * ls["frontier_vertices"]
+                for ls in st.levels)
+        bpe.append(b / m_r)
+    search_roofline = None
+    if bpe:
+        per_edge = sum(bpe) / len(bpe)
+        bound = peak / per_edge
+        search_roofline = {"bound": "hbm", "bytes_per_edge": round(per_edge, 3), "peak_gbs": peak,
+                           "bound_gteps": round(bound, 1), "achieved_gteps": round(value, 4),
+                           "frac": round(value / bound, 4), "peak_source": peak_src}
 
     per_level, per_root_ratio = {}, []
     phases = {"compression_sieve": 0.0, "communication": 0.0, "traversing": 0.0, "row_compression_sieve": 0.0,
@@ -698,6 +718,7 @@ def main():
         "plain_gpu": plain,
         **arms,
         "roofline": roofline,
+        "search_roofline": search_roofline,
         "kernel_rooflines": kr,
         "timing_modes": timing_modes,
         "phases_ms_per_search": phases,

@@ -395,3 +395,24 @@ def test_scale26_grid16_bench_configuration_one_root():
     lv, pa = oracle.bfs(go, r)
     assert (level == lv).all() and (parent == pa).all()
     assert (level0 == lv).all() and (parent0 == pa).all()
+
+
+def test_erdos_renyi_scale26_grid16_control_one_root():
+    """The bench's control workload: Erdos-Renyi scale 26 (uniform endpoints,
+    the Kronecker graph's n and m), 16x16 grid, COMPRESS_SIEVE and PLAIN, the
+    global-memory visiting path.  One seeded root: all levels and parents
+    bit-exact with the oracle."""
+    bfs = _lib()
+    n, src, dst = graphgen.edges(26, 16, kind=graphgen.ERDOS_RENYI)
+    g = bfs.Graph.from_edges(n, src, dst, p=16, mode=2)
+    r = int(graphgen.pick_roots(n, src, dst, 1)[0])
+    parent, level, _ = _run(g, r)
+    g.set_mode(0)
+    parent0, level0, _ = _run(g, r)
+    del g
+    torch.cuda.empty_cache()
+    go = oracle.csr(n, src, dst)
+    del src, dst
+    lv, pa = oracle.bfs(go, r)
+    assert (level == lv).all() and (parent == pa).all()
+    assert (level0 == lv).all() and (parent0 == pa).all()
