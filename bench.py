@@ -740,6 +740,58 @@ def main():
         dist.destroy_process_group()
 
 
+def codec_study(g, bfs, torch, n, p, root):
+    """The bitmap codes on the slices one DIR-WAH search exchanges (Sec. IV names
+    BBC and PLWAH beside WAH; the paper weighs codes by size and time): every
+    slice of every level decoded from its WAH stream on the GPU, then encoded
+    and decoded again with each code through the library (one call per slice,
+    scratch allocation and synchronisation included); bytes per code over the
+    search, mean microseconds per slice, and every round trip checked."""
+    nb = -(-n // p)
+    cap = 1 << 26
+    g.set_mode(2, 32)
+    g.set_row_exchange(False)
+    _, _, st = g.run(int(root), stats=True, trace_capacity=cap)
+    torch.cuda.synchronize()
+    words = st.trace_words[: st.trace_used]
+    counts = st.trace_counts.cpu().numpy()
+    out = {"slices": 0, "bytes": {"wah": 0, "plwah": 0, "bbc": 0, "raw": 0},
+           "us_per_slice": {"wah_decode": 0.0, "plwah_encode": 0.0, "plwah_decode": 0.0, "bbc_encode": 0.0,
+                            "bbc_decode": 0.0}, "round_trips_equal": 0}
+    off = 0
+    for k in range(counts.shape[0]):
+        for s, c in enumerate(counts[k]):
+            c = int(c)
+            j = s % p
+            nbits = max(0, min(n, (j + 1) * nb) - j * nb)
+            w = words[off: off + c]
+            off += c
+            t0 = time.perf_counter()
+            bits = bfs.wah_decode(w, nbits)
+            t1 = time.perf_counter()
+            pl = bfs.plwah_encode(bits, nbits)
+            t2 = time.perf_counter()
+            plb = bfs.plwah_decode(pl, nbits)
+            t3 = time.perf_counter()
+            bb = bfs.bbc_encode(bits, nbits)
+            t4 = time.perf_counter()
+            bbb = bfs.bbc_decode(bb, nbits)
+            t5 = time.perf_counter()
+            for key, dt in (("wah_decode", t1 - t0), ("plwah_encode", t2 - t1), ("plwah_decode", t3 - t2),
+                            ("bbc_encode", t4 - t3), ("bbc_decode", t5 - t4)):
+                out["us_per_slice"][key] += dt * 1e6
+            out["bytes"]["wah"] += 4 * c
+            out["bytes"]["plwah"] += 4 * pl.numel()
+            out["bytes"]["bbc"] += bb.numel()
+            out["bytes"]["raw"] += 4 * ((nbits + 31) // 32)
+            out["round_trips_equal"] += int(torch.equal(plb, bits) and torch.equal(bbb, bits))
+            out["slices"] += 1
+    for key in out["us_per_slice"]:
+        out["us_per_slice"][key] = round(out["us_per_slice"][key] / max(1, out["slices"]), 1)
+    out["over_wah"] = {k: round(v / out["bytes"]["wah"], 4) for k, v in out["bytes"].items()} if out["bytes"]["wah"] else None
+    return out
+
+
 def other_configs(args, bfs, graphgen, torch, dev):
     """The other configurations, each with its own validation: Kronecker scale
     22 on 8 x 8 (DIR-WAH, BIT, and DIR-WAH with the row exchange), the
@@ -795,6 +847,7 @@ def other_configs(args, bfs, graphgen, torch, dev):
             lv_o, pa_o = oracle.bfs(go, r0)
             res["oracle"] = {"root": r0, "bit_exact": bool((glv == lv_o).all() and
                                                            (parent.cpu().numpy() == pa_o).all())}
+            res["codecs"] = codec_study(g, bfs, torch, n, p, r0)
         else:
             lv_o, _ = oracle.bfs_sample(go, r0, ORACLE_SAMPLE_ENTRIES)
             got = lv_o >= 0

@@ -565,6 +565,53 @@ BFS_API bfs_status bfs_plwah_encode(const uint32_t *bits, int64_t nbits, uint32_
 BFS_API bfs_status bfs_plwah_decode(const uint32_t *words, int64_t nwords, int64_t nbits, uint32_t *bits,
                                    void *cuda_stream);
 
+/*
+ * BBC, the byte-aligned bitmap code (Antoshenkov) that Sec. IV names beside
+ * WAH and PLWAH, for one bitmap on the device.  The paper does not define it;
+ * this is the reading used here (four kinds of run, as BBC has):
+ *   the bitmap is cut into bytes, byte k = bits 8k .. 8k+7 with bit 8k the
+ *   most significant (bits past nbits are 0); a gap byte of value b is 0x00
+ *   (b = 0) or 0xFF (b = 1), every other byte a map byte; a map byte is odd
+ *   for b when it differs from the gap byte of value b in exactly one bit, at
+ *   position P (0 = the most significant bit);
+ *   a run is a fill of F >= 0 gap bytes of value b followed by a tail of
+ *   T = 0 .. 15 map bytes (stored as they are) or by one odd byte (stored as
+ *   P in the header); its header byte, most significant bit first:
+ *     1 b F F T T T T    F <= 3, tail
+ *     0 1 b F F P P P    F <= 3, odd byte
+ *     0 0 1 b T T T T    F >= 4, tail       (F follows as a counter)
+ *     0 0 0 1 b P P P    F >= 4, odd byte   (F follows as a counter)
+ *   the counter is base 128, least significant group first, bit 7 set on
+ *   every byte but the last; headers 0x00 .. 0x0F are not used;
+ *   encoding: a unit is a maximal run of equal gap bytes and the maximal run
+ *   of map bytes after it (a unit opening with map bytes, only at byte 0, has
+ *   F = 0, b = 0); its first run carries the fill and up to 15 map bytes, the
+ *   rest follow in runs with F = 0, 15 bytes each; a final one-byte tail that
+ *   is odd for the run's b (for F = 0: b = 0, else b = 1) is an odd-byte run.
+ * The exchange of the search keeps WAH; this code is offered beside it, to
+ * compare the codes on the same frontiers (as the paper weighs WAH against
+ * other codes).
+ *   bits: device, ceil(nbits/32) uint32 words (bit b = bit b%32 of word b/32).
+ *   nbits: 0 .. 2^31 - 1.
+ *   bytes: device output, capacity_bytes >= n + n/15 + 11 for n = ceil(nbits/8).
+ *   nbytes: device int64, receives the stream's length.
+ * Allocates scratch (cudaMalloc) and synchronises `cuda_stream`.
+ */
+BFS_API bfs_status bfs_bbc_encode(const uint32_t *bits, int64_t nbits, uint8_t *bytes, int64_t capacity_bytes,
+                                  int64_t *nbytes, void *cuda_stream);
+
+/*
+ * Decode a BBC stream (the inverse of bfs_bbc_encode; any well-formed stream,
+ * canonical or not) into `bits` (device, ceil(nbits/32) words, written whole:
+ * bits past nbits are 0).  Allocates scratch and synchronises `cuda_stream`.
+ * Errors: BFS_ERR_CORRUPT for a malformed stream (an unused header, a counter
+ * cut short or above 2^56, a record past the stream, bytes past nbits or too
+ * few, padding bits set); BFS_ERR_INVALID_ARG for nbits outside the range or
+ * bad pointers.
+ */
+BFS_API bfs_status bfs_bbc_decode(const uint8_t *bytes, int64_t nbytes, int64_t nbits, uint32_t *bits,
+                                  void *cuda_stream);
+
 /* ------------------------------------------------------------ diagnostics -- */
 
 /* bfs_measure_scatter_reads -- the rate of scattered 4-byte reads of this GPU,

@@ -76,6 +76,8 @@ def _load():
                 "oracle_wah_decode": (_int, [_ptr, _i64, _i64, _int, _int, _ptr]),
                 "oracle_plwah_encode": (_i64, [_ptr, _i64, _ptr]),
                 "oracle_plwah_decode": (_int, [_ptr, _i64, _i64, _ptr]),
+                "oracle_bbc_encode": (_i64, [_ptr, _i64, _ptr]),
+                "oracle_bbc_decode": (_int, [_ptr, _i64, _i64, _ptr]),
                 "oracle_adaptive_encode": (_i64, [_ptr, _i64, _int, _ptr, _ptr]),
                 "oracle_adaptive_decode": (_int, [_int, _ptr, _i64, _i64, _int, _ptr]),
                 "oracle_dist_bfs": (_i64, [_i64, _int, _ptr, _ptr, ctypes.c_int32, _int, _int, _int,
@@ -202,6 +204,26 @@ def plwah_decode(words: np.ndarray, nbits: int):
     words = np.ascontiguousarray(words, dtype=np.uint32)
     bits = np.zeros(max(1, nbits), dtype=np.uint8)
     rc = _load().oracle_plwah_decode(_p(words) if len(words) else 0, len(words), nbits, _p(bits))
+    return None if rc != 0 else bits[:nbits]
+
+
+def bbc_encode(bits: np.ndarray) -> np.ndarray:
+    """BBC bytes (uint8) of a 0/1 byte array (oracle_bbc_encode)."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    nbits = len(bits)
+    nbytes = (nbits + 7) // 8
+    out = np.empty(nbytes + nbytes // 15 + 16, dtype=np.uint8)
+    nb = _load().oracle_bbc_encode(_p(bits) if nbits else 0, nbits, _p(out))
+    if nb < 0:
+        raise MemoryError("oracle_bbc_encode")
+    return out[:nb].copy()
+
+
+def bbc_decode(data: np.ndarray, nbits: int):
+    """0/1 byte array, or ``None`` if the stream is malformed."""
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    bits = np.zeros(max(1, nbits), dtype=np.uint8)
+    rc = _load().oracle_bbc_decode(_p(data) if len(data) else 0, len(data), nbits, _p(bits))
     return None if rc != 0 else bits[:nbits]
 
 

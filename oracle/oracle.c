@@ -25,6 +25,9 @@
  *                            code Sec. IV names beside WAH (Deliege and
  *                            Pedersen): a fill word also carries the one odd
  *                            bit of the group that follows its run.
+ *   oracle_bbc_encode/_decode -- byte-aligned bitmap code, the other bitmap
+ *                            code Sec. IV names (Antoshenkov): runs of gap
+ *                            bytes and map bytes behind one-byte headers.
  *   oracle_adaptive_encode/_decode -- a sieved slice sent as the smallest of
  *                            its WAH stream, its sparse vector (Sec. II,
  *                            Table 2; Sec. V-A) and its raw bitmap (Alg. 1).
@@ -395,6 +398,160 @@ int oracle_plwah_decode(const uint32_t *words, int64_t nwords, int64_t nbits, ui
         for (int64_t b = 0; b < r; ++b) bits[full * 31 + b] = (uint8_t)((word >> (r - 1 - b)) & 1u);
     }
     return k == nwords ? 0 : -1;
+}
+
+/* ------------------------------------------------------------------ BBC -- */
+
+/*
+ * Byte-aligned bitmap code (BBC, Antoshenkov), the other bitmap code Sec. IV
+ * names beside WAH; the paper does not define it, so this is the reading the
+ * build uses (four kinds of run, as BBC has).  The bitmap is cut into bytes:
+ * byte k holds bits 8k .. 8k+7, the first of them the most significant; the
+ * bits past nbits in the last byte are 0.  A gap byte of value b is 0x00
+ * (b = 0) or 0xFF (b = 1); every other byte is a map byte.  A map byte is odd
+ * for b when it differs from the gap byte of value b in exactly one bit, its
+ * odd position (0 = the byte's first, most significant bit).
+ *
+ * The stream is a sequence of runs.  A run is a fill of F >= 0 gap bytes of
+ * value b followed either by a tail of T = 0 .. 15 map bytes, stored as they
+ * are, or by one odd byte, stored as its position in the header:
+ *   1 b F F T T T T            F <= 3, tail          (then the T bytes)
+ *   0 1 b F F P P P            F <= 3, odd byte at P
+ *   0 0 1 b T T T T            F >= 4, tail          (then F, then the T bytes)
+ *   0 0 0 1 b P P P            F >= 4, odd byte at P (then F)
+ * (header bits from the most significant); F >= 4 follows the header as a
+ * base-128 counter, least significant group first, bit 7 set on every byte
+ * but the last.  Headers 0x00 .. 0x0F are not used.
+ *
+ * Encoding, left to right: a unit is a maximal run of equal gap bytes (its
+ * fill; F = 0 and b = 0 when the unit starts with map bytes, which happens
+ * only at byte 0) and the maximal run of map bytes after it (length L >= 0).
+ * The unit's first run carries the fill and the first min(L, 15) map bytes;
+ * the other map bytes follow in runs with F = 0, 15 at a time.  A run whose
+ * tail would be one byte that is also the unit's last map byte is an odd-byte
+ * run when that byte is odd for the run's b (for F = 0: b = 0 if the byte is
+ * odd for 0, else b = 1 if it is odd for 1).  Returns the bytes written (at
+ * most nbytes + nbytes / 15 + 11 for nbytes = ceil(nbits / 8)).
+ */
+static int bbc_gap(uint8_t x) { return x == 0x00 ? 0 : (x == 0xFF ? 1 : -1); }
+
+/* Position of the odd bit of x for fill value b, or -1. */
+static int bbc_odd(uint8_t x, int b)
+{
+    const unsigned d = (unsigned)(x ^ (b ? 0xFFu : 0x00u));
+    if (d == 0 || (d & (d - 1u)) != 0) return -1;
+    int pos = 0;
+    while (!((d >> (7 - pos)) & 1u)) ++pos;
+    return pos;
+}
+
+static int64_t bbc_counter(uint8_t *out, int64_t at, int64_t f)
+{
+    do {
+        uint8_t g = (uint8_t)(f & 0x7F);
+        f >>= 7;
+        if (f) g |= 0x80;
+        out[at++] = g;
+    } while (f);
+    return at;
+}
+
+int64_t oracle_bbc_encode(const uint8_t *bits, int64_t nbits, uint8_t *out)
+{
+    const int64_t nbytes = (nbits + 7) / 8;
+    uint8_t *by = (uint8_t *)calloc((size_t)(nbytes > 0 ? nbytes : 1), 1);
+    if (!by) return -1;
+    for (int64_t i = 0; i < nbits; ++i)
+        if (bits[i] & 1) by[i / 8] |= (uint8_t)(0x80u >> (i % 8));
+    int64_t at = 0, k = 0;
+    while (k < nbytes) {
+        /* the unit: its fill, then its map bytes */
+        int b = 0;
+        int64_t f = 0;
+        if (bbc_gap(by[k]) >= 0) {
+            b = bbc_gap(by[k]);
+            while (k + f < nbytes && bbc_gap(by[k + f]) == b) ++f;
+        }
+        const int64_t m0 = k + f;
+        int64_t l = 0;
+        while (m0 + l < nbytes && bbc_gap(by[m0 + l]) < 0) ++l;
+        /* its runs: the first carries the fill */
+        int64_t done = 0;
+        int first = 1;
+        do {
+            const int64_t fill = first ? f : 0;
+            int rb = first ? b : 0;
+            const int64_t t = (l - done < 15) ? l - done : 15;
+            int pos = -1;
+            if (t == 1 && done + 1 == l) {
+                pos = bbc_odd(by[m0 + done], rb);
+                if (pos < 0 && fill == 0) { rb = 1; pos = bbc_odd(by[m0 + done], 1); }
+                if (pos < 0) rb = first ? b : 0;
+            }
+            if (pos >= 0) {
+                if (fill <= 3) out[at++] = (uint8_t)(0x40 | (rb << 5) | ((int)fill << 3) | pos);
+                else { out[at++] = (uint8_t)(0x10 | (rb << 3) | pos); at = bbc_counter(out, at, fill); }
+            } else {
+                if (fill <= 3) out[at++] = (uint8_t)(0x80 | (rb << 6) | ((int)fill << 4) | (int)t);
+                else { out[at++] = (uint8_t)(0x20 | (rb << 4) | (int)t); at = bbc_counter(out, at, fill); }
+                for (int64_t q = 0; q < t; ++q) out[at++] = by[m0 + done + q];
+            }
+            done += t;
+            first = 0;
+        } while (done < l);
+        k = m0 + l;
+    }
+    free(by);
+    return at;
+}
+
+/* Inverse of oracle_bbc_encode (any well-formed stream).  Returns 0, or -1 if
+ * the stream is malformed: an unused header, a cut counter or tail, a counter
+ * above 2^56, bytes past nbits, padding bits set, or trailing bytes. */
+int oracle_bbc_decode(const uint8_t *in, int64_t nin, int64_t nbits, uint8_t *bits)
+{
+    const int64_t nbytes = (nbits + 7) / 8;
+    uint8_t *by = (uint8_t *)calloc((size_t)(nbytes > 0 ? nbytes : 1), 1);
+    if (!by) return -1;
+    int64_t k = 0, at = 0;
+    int rc = 0;
+    while (at < nin) {
+        const uint8_t h = in[at++];
+        int b, odd = -1;
+        int64_t f, t = 0;
+        if (h & 0x80) { b = (h >> 6) & 1; f = (h >> 4) & 3; t = h & 15; }
+        else if (h & 0x40) { b = (h >> 5) & 1; f = (h >> 3) & 3; odd = h & 7; }
+        else if (h & 0x20) { b = (h >> 4) & 1; f = -1; t = h & 15; }
+        else if (h & 0x10) { b = (h >> 3) & 1; f = -1; odd = h & 7; }
+        else { rc = -1; break; }
+        if (f < 0) {                      /* a counter follows */
+            f = 0;
+            int shift = 0, more = 1;
+            while (more) {
+                if (at >= nin || shift > 49) { rc = -1; break; }
+                const uint8_t g = in[at++];
+                f |= (int64_t)(g & 0x7F) << shift;
+                shift += 7;
+                more = g & 0x80;
+            }
+            if (rc) break;
+        }
+        const int64_t tail = odd >= 0 ? 1 : t;
+        if (f > nbytes - k || tail > nbytes - k - f) { rc = -1; break; }
+        for (int64_t q = 0; q < f; ++q) by[k++] = b ? 0xFF : 0x00;
+        if (odd >= 0) {
+            by[k++] = (uint8_t)((b ? 0xFFu : 0x00u) ^ (0x80u >> odd));
+        } else {
+            if (t > nin - at) { rc = -1; break; }
+            for (int64_t q = 0; q < t; ++q) by[k++] = in[at++];
+        }
+    }
+    if (rc == 0 && k != nbytes) rc = -1;
+    if (rc == 0 && (nbits % 8) && (by[nbytes - 1] & (0xFFu >> (nbits % 8)))) rc = -1;
+    if (rc == 0)
+        for (int64_t i = 0; i < nbits; ++i) bits[i] = (uint8_t)((by[i / 8] >> (7 - i % 8)) & 1u);
+    free(by);
+    return rc;
 }
 
 /* ------------------------------------------------------ adaptive format -- */

@@ -294,6 +294,28 @@ def plwah_decode(words: torch.Tensor, nbits: int, stream=None) -> torch.Tensor:
     return out[: (nbits + 31) // 32]
 
 
+def bbc_encode(bits: torch.Tensor, nbits: int, stream=None) -> torch.Tensor:
+    """BBC bytes (uint8 CUDA tensor) of the first ``nbits`` bits of ``bits`` (int32 CUDA words)."""
+    words_in = (nbits + 31) // 32
+    src = torch.zeros(max(1, words_in), dtype=torch.int32, device="cuda")
+    if words_in:
+        src[:words_in] = bits[:words_in]
+    n = (nbits + 7) // 8
+    cap = n + n // 15 + 11
+    out = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    check(native.lib().bfs_bbc_encode(_ptr(src), int(nbits), _ptr(out), int(cap), _ptr(cnt), _stream_ptr(stream)))
+    return out[: int(cnt.item())]
+
+
+def bbc_decode(data: torch.Tensor, nbits: int, stream=None) -> torch.Tensor:
+    """Decode a BBC stream (uint8 CUDA tensor) into int32 bitmap words; raises on a malformed stream."""
+    out = torch.zeros(max(1, (nbits + 31) // 32), dtype=torch.int32, device="cuda")
+    check(native.lib().bfs_bbc_decode(_ptr(data) if data.numel() else None, int(data.numel()), int(nbits),
+                                      _ptr(out), _stream_ptr(stream)))
+    return out[: (nbits + 31) // 32]
+
+
 class Server:
     """Continuous-batching query server over resident graphs (``bfs_server_*``)."""
 

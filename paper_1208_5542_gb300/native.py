@@ -102,6 +102,8 @@ _SIGS = {
     "bfs_wah_decode_static": (ctypes.c_int, [vp, i64, i64, i32, vp, vp]),
     "bfs_plwah_encode": (ctypes.c_int, [vp, i64, vp, i64, vp, vp]),
     "bfs_plwah_decode": (ctypes.c_int, [vp, i64, i64, vp, vp]),
+    "bfs_bbc_encode": (ctypes.c_int, [vp, i64, vp, i64, vp, vp]),
+    "bfs_bbc_decode": (ctypes.c_int, [vp, i64, i64, vp, vp]),
     "bfs_measure_scatter_reads": (ctypes.c_int, [i64, i32, ctypes.POINTER(ctypes.c_double), vp]),
 }
 
