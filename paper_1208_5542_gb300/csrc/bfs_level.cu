@@ -131,6 +131,7 @@ struct LevelArgs {
     const LevelCtl* ctl;                // this level's values
     // bottom-up levels
     uint32_t* gbits;                    // decoded streams (n bits, OR over the block-rows)
+    int range_aligned;                  // 1: ranges start at word boundaries (n_b a multiple of 32)
     int64_t g_words;                    // its uint32 words (a multiple of 4)
     const int64_t* bu_ptr;              // bottom-up rows: offsets (n + 1)
     const int32_t* bu_adj;              // bottom-up rows: neighbour ids
@@ -862,12 +863,20 @@ __global__ void __launch_bounds__(kFT) fold_slots(LevelArgs a) {
         }
         __syncthreads();
         const int64_t gw0 = (ib + b0) >> 5;
+        // a word inside the chunk (or the bitmap's last, partial word) is this
+        // CTA's alone: stored; a word shared with a neighbouring range is ORed.
+        // With word-aligned ranges every word of the decoded bitmap is some
+        // chunk's alone and is stored even when zero (no clearing pass)
+        const bool store_zero = !ROWS && a.range_aligned;
         for (int k = threadIdx.x; k < nimg; k += kFT) {
             const uint32_t x = img[k];
-            if (!x) continue;
             const int64_t wlo = (gw0 + k) * 32;
-            if (wlo >= ib + b0 && wlo + 32 <= ib + b1) dst[gw0 + k] = x;
-            else atomicOr(dst + gw0 + k, x);
+            const bool own = wlo >= ib + b0 && (wlo + 32 <= ib + b1 || ib + b1 >= a.n);
+            if (own) {
+                if (x || store_zero) dst[gw0 + k] = x;
+            } else if (x) {
+                atomicOr(dst + gw0 + k, x);
+            }
         }
         if (threadIdx.x == 0 && s_err) atomicOr(a.ctr + C_ERROR, 16ull);
         __syncthreads();
@@ -1762,6 +1771,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     a.row_cps = W.enc_cps;
     a.row_bcps = (L.nb + (int64_t)kEncChunkGroups * (wbits - 1) - 1) / ((int64_t)kEncChunkGroups * (wbits - 1));
     a.gbits = W.gbits.as<uint32_t>();
+    a.range_aligned = (L.nb % 32 == 0) ? 1 : 0;
     a.g_words = g_words;
     a.bu_ptr = L.bu_ptr.as<int64_t>();
     a.bu_adj = L.bu_adj.as<int32_t>();
@@ -1862,7 +1872,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             BFS_TRY(launch_wah_encode_parallel(eh, wbits, W.enc_sums.ptr, W.enc_bases.ptr, W.enc_cps,
                                                W.enc_flags.ptr, host ? ctr + C_EXCHANGED : nullptr, sm_count() * 6, s));
             if (bu_kernels) {           // a bottom-up level reads the streams as bitmaps
-                clear_gbits<<<sm_count() * 4, kNT, 0, s>>>(a);
+                if (!a.range_aligned) clear_gbits<<<sm_count() * 4, kNT, 0, s>>>(a);   // shared boundary words
                 const int64_t fitems = (int64_t)p * a.row_bcps;
                 const int fgrid = (int)std::min<int64_t>(std::max<int64_t>(fitems, 1), (int64_t)sm_count() * 4);
                 if (wbits == 32) fold_slots<uint32_t, false><<<fgrid, kFT, 0, s>>>(a);

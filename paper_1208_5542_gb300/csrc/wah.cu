@@ -233,6 +233,8 @@ __global__ void __launch_bounds__(kNT) wah_encode_kernel(EncodeArgs a, unsigned 
 // copies (all in flight together; one round trip per chunk), then every
 // group is two shared-memory words funnel-shifted.
 constexpr int kEW = 128;          // threads per staging encoder CTA (4 warps)
+constexpr int kEWBlocks = 6;      // CTAs per SM the staging passes are compiled for: as many as their shared
+                                  // memory allows (registers capped at 80; uncapped they held 5)
 constexpr int kStageWords = 1060; // >= the words of one chunk (1024 x 31 bits) + alignment and funnel slack,
                                   // and >= the padded output words of a chunk (the frontier buffer is reused)
 
@@ -566,7 +568,7 @@ __device__ __forceinline__ uint32_t lane_popc(const uint32_t (&c)[32], int ng) {
     return cnt;
 }
 
-__global__ void __launch_bounds__(kEW) enc_chunk_sums32(EncodeArgs a, ChunkSum* sums, uint8_t* flags, int64_t cps,
+__global__ void __launch_bounds__(kEW, kEWBlocks) enc_chunk_sums32(EncodeArgs a, ChunkSum* sums, uint8_t* flags, int64_t cps,
                                                         unsigned long long* setbits) {
     if (a.skip && *a.skip) return;
     __shared__ __align__(16) uint32_t s_f[kEW / 32][kStageWords];
@@ -649,7 +651,7 @@ constexpr int kOutWords = kTile + 2;     // the chunk's words, from the one befo
 // bank conflicts.
 __device__ __forceinline__ int opad(int k) { return k + (k >> 5); }
 
-__global__ void __launch_bounds__(kEW) enc_chunk_write32(EncodeArgs a, const ChunkBase* bases, const uint8_t* flags,
+__global__ void __launch_bounds__(kEW, kEWBlocks) enc_chunk_write32(EncodeArgs a, const ChunkBase* bases, const uint8_t* flags,
                                                          int64_t cps) {
     __shared__ __align__(16) uint32_t s_f[kEW / 32][kStageWords];
     __shared__ __align__(16) uint32_t s_d[kEW / 32][kStageWords];
