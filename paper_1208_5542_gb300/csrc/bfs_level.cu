@@ -224,23 +224,27 @@ struct Visitor {
 // they do not push the visited, parent and next-bit lines out of L2 (-21% DRAM
 // bytes at the growing level of a scale-24 search).
 constexpr int kIlp = 4;
+#ifndef BFS_PIECE_ILP
+#define BFS_PIECE_ILP 8
+#endif
+constexpr int kPieceIlp = BFS_PIECE_ILP;   // the piece kernel: long columns only, more entries in flight
 
-// All 32 lanes expand one column: kIlp x 32 consecutive entries per step.
-template <bool WIN, bool DEDUP, bool ROWX>
+// All 32 lanes expand one column: ILP x 32 consecutive entries per step.
+template <bool WIN, bool DEDUP, bool ROWX, int ILP = kIlp>
 __device__ __forceinline__ void warp_column(const LevelArgs& a, const Visitor<WIN, DEDUP, ROWX>& vis, int32_t u, int64_t beg,
                                             uint32_t len) {
     const int32_t* col = a.ir + beg;
-    for (uint32_t e = lane_id(); e < len; e += 32 * kIlp) {
-        int32_t v[kIlp];
-        uint32_t w[kIlp], t[kIlp];
+    for (uint32_t e = lane_id(); e < len; e += 32 * ILP) {
+        int32_t v[ILP];
+        uint32_t w[ILP], t[ILP];
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k) v[k] = (e + 32 * k < len) ? __ldcs(col + e + 32 * k) : -1;
+        for (int k = 0; k < ILP; ++k) v[k] = (e + 32 * k < len) ? __ldcs(col + e + 32 * k) : -1;
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k) w[k] = (v[k] >= 0) ? vis.probe(a, v[k]) : 0u;
+        for (int k = 0; k < ILP; ++k) w[k] = (v[k] >= 0) ? vis.probe(a, v[k]) : 0u;
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k) vis.stage(a, v[k], w[k], t[k]);
+        for (int k = 0; k < ILP; ++k) vis.stage(a, v[k], w[k], t[k]);
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k)
+        for (int k = 0; k < ILP; ++k)
             if (v[k] >= 0) vis.mark(a, v[k], u, w[k], t[k]);
     }
 }
@@ -687,7 +691,7 @@ __global__ void __launch_bounds__(kXT, 1) expand_pieces(LevelArgs a) {
         const Visitor<WIN, DEDUP, ROWX> vis{s_pi, s_t, range_begin(a, row),
                                             ROWX ? a.tblk + ((int64_t)row * a.p + j) * a.dir_stride : nullptr,
                                             (uint32_t)range_begin(a, j)};
-        warp_column<WIN, DEDUP, ROWX>(a, vis, it.u, it.begin, it.len);
+        warp_column<WIN, DEDUP, ROWX, kPieceIlp>(a, vis, it.u, it.begin, it.len);
     };
     row_affine<WIN>(a, a.row_piece_next, 1, units_in_row, do_unit, s_pi, s_t, s_row);
 }
@@ -1290,8 +1294,12 @@ __global__ void __launch_bounds__(kNT) reduce_level(uint32_t* __restrict__ t, ui
 // One thread: the values of the next level, and whether it runs (the
 // frontier is not empty, no invariant failed, fewer than max_levels levels).
 // In a CUDA graph the decision drives the conditional WHILE node.
-__global__ void level_next(LevelCtl* c, const unsigned long long* ctr, int64_t n, int win, int32_t max_levels,
-                           cudaGraphConditionalHandle handle, int use_handle) {
+// In the graph-launched loop (use_handle) it also clears the per-level
+// counters and the row hand-out counters (lvl, nlvl of them) for the next
+// level, in place of memset nodes; the stepwise loop reads them first and
+// clears them itself.
+__global__ void level_next(LevelCtl* c, unsigned long long* ctr, int64_t n, int win, int32_t max_levels,
+                           cudaGraphConditionalHandle handle, int use_handle, unsigned long long* lvl, int nlvl) {
     const int64_t f = (int64_t)ctr[C_NEXT_COUNT];
     const int64_t prev = c->frontier;
     const int64_t mf = (int64_t)ctr[C_NEXT_DEGREE];
@@ -1321,7 +1329,12 @@ __global__ void level_next(LevelCtl* c, const unsigned long long* ctr, int64_t n
     c->dedup = (!win && c->visited * 16 < n) ? 1 : 0;
     const int go = (f > 0 && ctr[C_ERROR] == 0 && c->level < max_levels) ? 1 : 0;
     c->go = go;
-    if (use_handle) cudaGraphSetConditional(handle, go ? 1u : 0u);
+    if (use_handle) {
+        for (int k = 0; k < C_ERROR; ++k) ctr[k] = 0ull;          // the error flag and trace cursors stay
+        for (int k = C_WAH_WORDS; k < C_NUM; ++k) ctr[k] = 0ull;
+        for (int k = 0; k < nlvl; ++k) lvl[k] = 0ull;
+        cudaGraphSetConditional(handle, go ? 1u : 0u);
+    }
 }
 
 __global__ void level_first(LevelCtl* c, int64_t n, int win, int policy, int alpha, int beta,
@@ -1747,6 +1760,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     a.chunks_per_slot = W.chunks_per_slot;
     a.slot_unit_base = W.units.as<int64_t>();
     unsigned long long* lvl = W.level_scratch.as<unsigned long long>();
+    BFS_CUDA_TRY(cudaMemsetAsync(lvl, 0, sizeof(unsigned long long) * (3 * p + 1), st));   // the first level's
     a.row_next = lvl;
     a.row_piece_count = lvl + p;
     a.row_piece_next = lvl + 2 * p;
@@ -1846,10 +1860,14 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
     // One level: the same launch sequence every time.  `host` adds the
     // statistics, the trace and the phase events (and k is known on the host).
     auto level_body = [&](cudaStream_t s, bool host, int32_t k, cudaGraphConditionalHandle handle) -> bfs_status {
-        // per-level counters; the error flag and the trace cursor persist
-        BFS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * C_ERROR, s));
-        BFS_CUDA_TRY(cudaMemsetAsync(ctr + C_WAH_WORDS, 0, sizeof(unsigned long long) * (C_NUM - C_WAH_WORDS), s));
-        BFS_CUDA_TRY(cudaMemsetAsync(lvl, 0, sizeof(unsigned long long) * (3 * p + 1), s));
+        // per-level counters (the error flag and the trace cursor persist): the
+        // stepwise loop clears them here, the graph-launched loop's level_next
+        // at the end of the level before (and the search's setup for the first)
+        if (host) {
+            BFS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * C_ERROR, s));
+            BFS_CUDA_TRY(cudaMemsetAsync(ctr + C_WAH_WORDS, 0, sizeof(unsigned long long) * (C_NUM - C_WAH_WORDS), s));
+            BFS_CUDA_TRY(cudaMemsetAsync(lvl, 0, sizeof(unsigned long long) * (3 * p + 1), s));
+        }
         if (host && timing) cudaEventRecord(W.ev[7], s);
         if (dynamic) {                  // the frontier's bits of the dynamic directory
             dyn_sieve<<<sm_count() * 8, kNT, 0, s>>>(a, W.ddir.as<uint32_t>(), W.fsum.as<uint8_t>());
@@ -1944,7 +1962,7 @@ bfs_status run_search(bfs_graph* g, int32_t root, int32_t* parent, int32_t* leve
             t, W.pi.as<uint32_t>(), f, W.fsum.as<uint8_t>(), W.bm_words, L.n, level, ctl, ctr, deg);
         BFS_CUDA_TRY(cudaGetLastError());
         if (host && timing) cudaEventRecord(W.ev[4], s);
-        level_next<<<1, 1, 0, s>>>(ctl, ctr, L.n, win ? 1 : 0, max_levels, handle, host ? 0 : 1);
+        level_next<<<1, 1, 0, s>>>(ctl, ctr, L.n, win ? 1 : 0, max_levels, handle, host ? 0 : 1, lvl, 3 * p + 1);
         BFS_CUDA_TRY(cudaGetLastError());
         return BFS_OK;
     };
