@@ -55,9 +55,9 @@ namespace {
 constexpr int kNT = 256;            // threads of the small kernels
 constexpr int kXT = 1024;           // threads of the expansion CTAs
 constexpr int kXW = kXT / 32;       // warps of the expansion CTAs
-constexpr uint32_t kCoop = 32;      // columns of at least this many entries take the whole warp
-constexpr uint32_t kHub = 1024;     // columns longer than this are cut into pieces
-constexpr uint32_t kPiece = 1024;   // entries per piece
+constexpr uint32_t kCoop = 64;      // columns of at least this many entries take the whole warp
+constexpr uint32_t kHub = 2048;     // columns longer than this are cut into pieces
+constexpr uint32_t kPiece = 2048;   // entries per piece
 #ifndef BFS_GUIDE
 #define BFS_GUIDE 2
 #endif

@@ -416,3 +416,37 @@ def test_erdos_renyi_scale26_grid16_control_one_root():
     lv, pa = oracle.bfs(go, r)
     assert (level == lv).all() and (parent == pa).all()
     assert (level0 == lv).all() and (parent0 == pa).all()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_long_columns_cut_into_pieces(mode):
+    """Columns around and far above the piece length (2048 entries): stars whose
+    centres have 2047, 2048, 2049, 4097 and 20000 leaves, joined by a path, on
+    1 x 1 and 2 x 2 grids, from a centre and from a leaf; levels, parents and
+    streams equal the oracle's, on the global visiting path too (a range too
+    long for the row window)."""
+    bfs = _lib()
+    src, dst, base = [], [], 0
+    centres = []
+    for leaves in (2047, 2048, 2049, 4097, 20000):
+        centres.append(base)
+        src += [base] * leaves
+        dst += list(range(base + 1, base + 1 + leaves))
+        base += leaves + 1
+    for a, b in zip(centres[:-1], centres[1:]):
+        src.append(a + 1)
+        dst.append(b)
+    n = max(base, 2_000_000)                         # isolated tail: ranges beyond the row window
+    src = np.array(src, np.int32)
+    dst = np.array(dst, np.int32)
+    go = oracle.csr(n, src, dst)
+    for p in (1, 2):
+        g = bfs.Graph.from_edges(n, src, dst, p=p, mode=mode)
+        for r in (centres[0], centres[-1] + 7, centres[2]):
+            lv, pa, tr = oracle.dist_bfs(go, p, r, mode=ORACLE_MODE[mode], trace=True)
+            parent, level, st = _run(g, r, stats=True, trace_capacity=1 << 22 if mode else 0)
+            assert (level == lv).all() and (parent == pa).all()
+            if mode:
+                _check_trace(_unpack_trace(st, 32), tr)
+            parent, level, _ = _run(g, r)
+            assert (level == lv).all() and (parent == pa).all()
