@@ -59,7 +59,7 @@ constexpr uint32_t kCoop = 64;      // columns of at least this many entries tak
 constexpr uint32_t kHub = 2048;     // columns longer than this are cut into pieces
 constexpr uint32_t kPiece = 2048;   // entries per piece
 #ifndef BFS_GUIDE
-#define BFS_GUIDE 2
+#define BFS_GUIDE 1
 #endif
 constexpr int64_t kGuide = BFS_GUIDE;  // a grab takes 1/(kGuide * warps) of the units left in the row
 constexpr int64_t kSmemLimit = 227 * 1024;
