@@ -101,18 +101,26 @@ def parse():
 
 
 # ----------------------------------------------------------------- helpers --
-def kernel_hash():
-    """Hash of the kernel sources' code: comments and blank lines do not count,
-    so that a comment edit does not retire the committed ncu counters."""
+def code_digest(texts):
+    """Hash of C/CUDA sources' code: comments and blank lines do not count."""
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), encoding="utf-8") as fh:
-            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+    for text in texts:
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for line in text.splitlines():
             line = re.sub(r"//.*", "", line).rstrip()
             if line:
                 h.update(line.encode() + b"\n")
     return h.hexdigest()[:16]
+
+
+def kernel_hash():
+    """Hash of the kernel sources' code, so that a comment edit does not retire
+    the committed ncu counters."""
+    texts = []
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as fh:
+            texts.append(fh.read())
+    return code_digest(texts)
 
 
 def measured_peaks():
@@ -343,6 +351,29 @@ def level_rooflines(stats, n, wbits, peak, peak_src, workload):
     return out, entries
 
 
+def search_roofline_of(levels_per_search, m, wbits, peak, value, peak_src):
+    """The whole search against HBM: per search, its algorithmic bytes over its
+    traversed edges m_r -- adjacency entries 4 B, (vertex, block) columns 12 B
+    (rank word and column-pointer pair), level, parent and candidate parent 12 B
+    per reached vertex, every stream written and read, the directory words the
+    sieve reads with each live chunk -- averaged over the searches; the GTEPS the
+    copy rate `peak` (GB/s) allows at that rate, and `value` against it."""
+    bpe = []
+    for levels, m_r in zip(levels_per_search, m):
+        if not m_r:
+            continue
+        b = sum(4 * ls["edges_scanned"] + 12 * ls["column_hits"] + 2 * ls["wah_bytes"] +
+                (CHUNK_GROUPS * (wbits - 1) // 8) * ls["compress_chunks"] + 12 * ls["frontier_vertices"]
+                for ls in levels)
+        bpe.append(b / m_r)
+    if not bpe:
+        return None
+    per_edge = sum(bpe) / len(bpe)
+    bound = peak / per_edge
+    return {"bound": "hbm", "bytes_per_edge": round(per_edge, 3), "peak_gbs": peak, "bound_gteps": round(bound, 1),
+            "achieved_gteps": round(value, 4), "frac": round(value / bound, 4), "peak_source": peak_src}
+
+
 def validate_all(g, roots, parent, level, src_d, dst_d, n, dev, stream, torch):
     """BFS-tree invariants and the smallest-parent rule, every root (torch over
     the edge list): the root is its own parent at level 0; both ends of every
@@ -537,21 +568,8 @@ def main():
     # word and column-pointer pair), level, parent and candidate-parent 12 B per
     # reached vertex, every stream written and read, the directory words the
     # sieve reads -- and the GTEPS the measured copy rate allows at that rate
-    bpe = []
-    for st, m_r in zip(main_arm["stats"], main_arm["m"]):
-        if not m_r:
-            continue
-        b = sum(4 * ls["edges_scanned"] + 12 * ls["column_hits"] + 2 * ls["wah_bytes"] +
-                (CHUNK_GROUPS * (args.wah_bits - 1) // 8) * ls["compress_chunks"] + 12 * ls["frontier_vertices"]
-                for ls in st.levels)
-        bpe.append(b / m_r)
-    search_roofline = None
-    if bpe:
-        per_edge = sum(bpe) / len(bpe)
-        bound = peak / per_edge
-        search_roofline = {"bound": "hbm", "bytes_per_edge": round(per_edge, 3), "peak_gbs": peak,
-                           "bound_gteps": round(bound, 1), "achieved_gteps": round(value, 4),
-                           "frac": round(value / bound, 4), "peak_source": peak_src}
+    search_roofline = search_roofline_of([st.levels for st in main_arm["stats"]], main_arm["m"], args.wah_bits,
+                                         peak, value, peak_src)
 
     per_level, per_root_ratio = {}, []
     phases = {"compression_sieve": 0.0, "communication": 0.0, "traversing": 0.0, "row_compression_sieve": 0.0,

@@ -57,3 +57,31 @@ def test_compression_factor_is_the_mean_of_the_level_ratios():
     assert bench.compression_factor([one], 0) is None
     assert bench.compression_factor([], 2) is None
     assert bench.compression_factor([[None]], 2) is None
+
+
+def test_kernel_hash_ignores_comments_only():
+    """The committed ncu counters stay valid across comment edits of the kernel
+    sources, and no longer once the code changes."""
+    sys.path.insert(0, ROOT)
+    import bench
+    code = "int f(int x) {\n    return x + 1;   // add one\n}\n/* a block\n   comment */\n"
+    same = "// header comment\nint f(int x) {\n\n    return x + 1;   // a different remark\n}\n"
+    other = "int f(int x) {\n    return x + 2;\n}\n"
+    assert bench.code_digest([code]) == bench.code_digest([same])
+    assert bench.code_digest([code]) != bench.code_digest([other])
+    assert len(bench.kernel_hash()) == 16
+
+
+def test_search_roofline_arithmetic():
+    """Bytes per traversed edge from the per-level counters, the GTEPS bound at
+    the copy rate, and the fraction the measured value reaches."""
+    sys.path.insert(0, ROOT)
+    import bench
+    lv = {"edges_scanned": 1000, "column_hits": 100, "wah_bytes": 50, "compress_chunks": 2, "frontier_vertices": 10}
+    chunk = bench.CHUNK_GROUPS * 31 // 8
+    per = (4 * 1000 + 12 * 100 + 2 * 50 + chunk * 2 + 12 * 10) / 500
+    r = bench.search_roofline_of([[lv]], [500], 32, 6000.0, 100.0, "measured")
+    assert r["bytes_per_edge"] == round(per, 3)
+    assert r["bound_gteps"] == round(6000.0 / per, 1)
+    assert r["frac"] == round(100.0 / (6000.0 / per), 4)
+    assert bench.search_roofline_of([[lv]], [0], 32, 6000.0, 100.0, "measured") is None
