@@ -47,6 +47,14 @@ HAND = [
     ([0xFF] * 4 + [0xBF], [0x10 | (1 << 3) | 1, 4]),
     # 0x00 0x80 0x80: the tail has two bytes, so no odd-byte run
     ([0x00, 0x80, 0x80], [0x80 | (1 << 4) | 2, 0x80, 0x80]),
+    # the 128-bit bitmap of Table 3's WAH example (1 one, 20 zeros, 3 ones, 79
+    # zeros, 25 ones; Sec. IV): bytes 80 00 07 00x9 01 FF FF FF ->
+    #   80 alone, odd for 0 at 0          -> 01 0 00 000        = 0x40
+    #   one 00, tail 07 (three bits set)  -> 1 0 01 0001, 07    = 0x91 0x07
+    #   nine 00, then 01 odd for 0 at 7   -> 0001 0 111, 9      = 0x17 0x09
+    #   three FF, nothing after           -> 1 1 11 0000        = 0xF0
+    # six bytes where WAH needs four 32-bit words
+    ([0x80, 0x00, 0x07] + [0x00] * 9 + [0x01, 0xFF, 0xFF, 0xFF], [0x40, 0x91, 0x07, 0x17, 0x09, 0xF0]),
 ]
 
 
