@@ -13,8 +13,12 @@
  * exchanged message is a per-block buffer in HBM.  Beside the paper's three
  * algorithms: the hybrid top-down / bottom-up levels it names as future work
  * (Sec. VIII, IX; bfs_graph_set_direction), bit-parallel batches of up to 64
- * roots and a continuous-batching server (bfs_run_batch, bfs_server_*), and
- * the PLWAH code it names beside WAH (Sec. IV; bfs_plwah_*).
+ * roots and a continuous-batching server (bfs_run_batch, bfs_server_*), the
+ * row exchange of the 2D partition (Sec. VIII; bfs_graph_set_row_exchange),
+ * the level-adaptive exchange format (Sec. II, Table 2;
+ * bfs_graph_set_exchange_format), the dynamic cross directory (Sec. V-B;
+ * bfs_graph_set_dynamic_directory), and the PLWAH and BBC codes it names
+ * beside WAH (Sec. IV; bfs_plwah_*, bfs_bbc_*).
  *
  * Conventions for every entry point:
  *   - Errors are returned as a bfs_status; nothing throws across the ABI and
